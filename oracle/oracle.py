@@ -1,0 +1,221 @@
+"""ctypes front end of the FP64 CPU oracle in ``bqcd_oracle.c``.
+
+TEST INFRASTRUCTURE.  Each function names the part of arXiv:1711.03836 it
+follows; the arithmetic lives in the C file and is written from the
+definitions (Eq. 1 hopping term with chemical potential, Eq. 2 clover term,
+Eq. 5 U(1) phases, the even-odd Schur complement of M = A - kappa D_hop,
+textbook CG).  Fields use the canonical host layouts:
+
+  links   U[V][4][3][3] complex128, site lex = x + Lx*(y + Ly*(z + Lz*t))
+  U(1)    A[V][4] float64 (or None)
+  spinor  half lattice [V/2][4][3] complex128, indexed by lex/2
+
+Nothing here imports the CUDA library, and the CUDA library imports nothing
+from here.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bqcd_oracle.c")
+_LIB = os.path.join(_HERE, "libbqcd_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``or_params`` in the C file."""
+
+    _fields_ = [
+        ("L", ctypes.c_int * 4),
+        ("kappa", ctypes.c_double),
+        ("csw", ctypes.c_double),
+        ("mu", ctypes.c_double),
+        ("t_bc", ctypes.c_double),
+        ("charge", ctypes.c_double),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``libbqcd_oracle.so`` (gcc, -O2, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.POINTER(Params)
+            dp = ctypes.c_void_p
+            L = ctypes.c_long
+            i = ctypes.c_int
+            d = ctypes.c_double
+            sig = {
+                "or_gamma": (None, [i, dp]),
+                "or_dhop": (None, [P, dp, dp, dp, i, i, dp]),
+                "or_dhop_sites": (None, [P, dp, dp, dp, i, i, L, dp, dp]),
+                "or_clover_field": (None, [P, dp, i, dp]),
+                "or_clover_invert": (L, [L, dp, dp]),
+                "or_clover_apply": (None, [L, dp, dp, i, dp]),
+                "or_clover_sites": (i, [P, dp, i, i, L, dp, dp, dp]),
+                "or_mhat": (None, [P, dp, dp, dp, dp, dp, i, dp]),
+                "or_mdagm": (None, [P, dp, dp, dp, dp, dp, d, dp]),
+                "or_mhat_sites": (i, [P, dp, dp, dp, i, L, dp, dp]),
+                "or_cg": (i, [P, dp, dp, dp, dp, dp, d, d, i, dp]),
+                "or_num_threads": (i, []),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def params(dims, kappa=0.125, csw=0.0, mu=0.0, t_bc=-1.0, charge=0.0) -> Params:
+    p = Params()
+    for k in range(4):
+        p.L[k] = int(dims[k])
+    p.kappa, p.csw, p.mu, p.t_bc, p.charge = float(kappa), float(csw), float(mu), float(t_bc), float(charge)
+    return p
+
+
+def half_volume(p: Params) -> int:
+    return p.L[0] * p.L[1] * p.L[2] * p.L[3] // 2
+
+
+def num_threads() -> int:
+    return _load().or_num_threads()
+
+
+def gamma(k: int) -> np.ndarray:
+    """The oracle's gamma_{k+1} (k=0..3) or gamma_5 (k=4), chiral basis."""
+    out = np.zeros((4, 4), np.complex128)
+    _load().or_gamma(k, _ptr(out))
+    return out
+
+
+def dhop(p, U, A, psi, out_parity, dagger=False):
+    """D_hop (Eq. 1, Eq. 5) from the opposite parity onto ``out_parity``."""
+    U, psi = _c128(U), _c128(psi)
+    A = None if A is None else np.ascontiguousarray(A, np.float64)
+    out = np.empty((half_volume(p), 4, 3), np.complex128)
+    _load().or_dhop(ctypes.byref(p), _ptr(U), _ptr(A), _ptr(psi), out_parity, int(dagger), _ptr(out))
+    return out
+
+
+def dhop_sites(p, U, A, psi, out_parity, sites, dagger=False):
+    U, psi = _c128(U), _c128(psi)
+    A = None if A is None else np.ascontiguousarray(A, np.float64)
+    sites = np.ascontiguousarray(sites, np.int64)
+    out = np.empty((len(sites), 4, 3), np.complex128)
+    _load().or_dhop_sites(ctypes.byref(p), _ptr(U), _ptr(A), _ptr(psi), out_parity, int(dagger),
+                          len(sites), _ptr(sites), _ptr(out))
+    return out
+
+
+def clover_field(p, U, parity):
+    """A(x) = 1 + i kappa c_SW sum_{mu<nu} sigma F (Eq. 2) as [V/2][12][12]."""
+    U = _c128(U)
+    out = np.empty((half_volume(p), 12, 12), np.complex128)
+    _load().or_clover_field(ctypes.byref(p), _ptr(U), parity, _ptr(out))
+    return out
+
+
+def clover_invert(Am):
+    Am = _c128(Am)
+    out = np.empty_like(Am)
+    bad = _load().or_clover_invert(Am.shape[0], _ptr(Am), _ptr(out))
+    if bad:
+        raise np.linalg.LinAlgError(f"{bad} singular clover sites")
+    return out
+
+
+def clover_apply(Am, psi, dagger=False):
+    Am, psi = _c128(Am), _c128(psi)
+    out = np.empty(psi.shape, np.complex128)
+    _load().or_clover_apply(Am.shape[0], _ptr(Am), _ptr(psi), int(dagger), _ptr(out))
+    return out
+
+
+def clover_sites(p, U, parity, psi, sites, inverse=False):
+    U, psi = _c128(U), _c128(psi)
+    sites = np.ascontiguousarray(sites, np.int64)
+    out = np.empty((len(sites), 4, 3), np.complex128)
+    bad = _load().or_clover_sites(ctypes.byref(p), _ptr(U), parity, int(inverse), len(sites),
+                                  _ptr(sites), _ptr(psi), _ptr(out))
+    if bad:
+        raise np.linalg.LinAlgError(f"{bad} singular clover sites")
+    return out
+
+
+class Operator:
+    """The even-odd operator of one gauge field: clover blocks built once."""
+
+    def __init__(self, p: Params, U, A=None):
+        self.p = p
+        self.U = _c128(U)
+        self.A = None if A is None else np.ascontiguousarray(A, np.float64)
+        self.Aee = clover_field(p, self.U, 0)
+        self.Aoo_inv = clover_invert(clover_field(p, self.U, 1))
+
+    def mhat(self, psi, dagger=False):
+        """Mhat psi = A_ee psi - kappa^2 D_eo A_oo^{-1} D_oe psi (or its adjoint)."""
+        psi = _c128(psi)
+        out = np.empty_like(psi)
+        _load().or_mhat(ctypes.byref(self.p), _ptr(self.U), _ptr(self.A), _ptr(self.Aee),
+                        _ptr(self.Aoo_inv), _ptr(psi), int(dagger), _ptr(out))
+        return out
+
+    def mdagm(self, psi, sigma=0.0):
+        psi = _c128(psi)
+        out = np.empty_like(psi)
+        _load().or_mdagm(ctypes.byref(self.p), _ptr(self.U), _ptr(self.A), _ptr(self.Aee),
+                         _ptr(self.Aoo_inv), _ptr(psi), float(sigma), _ptr(out))
+        return out
+
+    def cg(self, b, sigma=0.0, tol=1e-10, maxiter=10000):
+        """Textbook CG on (Mhat^dagger Mhat + sigma) x = b from x = 0."""
+        b = _c128(b)
+        x = np.empty_like(b)
+        it = _load().or_cg(ctypes.byref(self.p), _ptr(self.U), _ptr(self.A), _ptr(self.Aee),
+                           _ptr(self.Aoo_inv), _ptr(b), float(sigma), float(tol), int(maxiter), _ptr(x))
+        return x, it
+
+    def multishift(self, b, shifts, tol=1e-10, maxiter=10000):
+        """Multishift reference: one independent CG per shift."""
+        return [self.cg(b, s, tol, maxiter)[0] for s in shifts]
+
+
+def mhat_sites(p, U, A, psi, sites, dagger=False):
+    """Mhat psi (or Mhat^dagger psi) at listed even half sites, built on the fly."""
+    U, psi = _c128(U), _c128(psi)
+    A = None if A is None else np.ascontiguousarray(A, np.float64)
+    sites = np.ascontiguousarray(sites, np.int64)
+    out = np.empty((len(sites), 4, 3), np.complex128)
+    bad = _load().or_mhat_sites(ctypes.byref(p), _ptr(U), _ptr(A), _ptr(psi), int(dagger), len(sites),
+                                _ptr(sites), _ptr(out))
+    if bad:
+        raise np.linalg.LinAlgError(f"{bad} singular clover sites")
+    return out
