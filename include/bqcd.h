@@ -1,0 +1,161 @@
+/*
+ * bqcd.h -- C ABI of the GB300-native even-odd clover-Wilson library.
+ *
+ * The library applies the fermion matrix of the BQCD update paper
+ * (arXiv:1711.03836, Section 2 "Actions"): the hopping term of Eq. 1 with the
+ * chemical potential e^{+-mu} on time links, the clover term of Eq. 2, and the
+ * QCD+QED U(1) phases of Eq. 5, in even-odd preconditioned form
+ *     Mhat = A_ee - kappa^2 D_eo A_oo^{-1} D_oe,
+ * and solves with it by CG and multishift CG (Section 4, "solvers").
+ *
+ * Conventions.
+ *   Lattice extents dims = {Lx, Ly, Lz, Lt}, all even and >= 2; V = Lx*Ly*Lz*Lt.
+ *   Site lex = x + Lx*(y + Ly*(z + Lz*t)); parity = (x+y+z+t) mod 2; a field on
+ *   one parity ("half lattice", V/2 sites) is indexed by lex/2.
+ *   Chiral Dirac basis: gamma_k = [[0,-i s_k],[i s_k,0]], gamma_4 = [[0,1],[1,0]],
+ *   gamma_5 = diag(1,1,-1,-1).
+ *   Canonical host/device layouts (all FP64, complex = two doubles re,im):
+ *     links   U[V][4][3][3]   (mu = 0..3 for x,y,z,t; U[a][b] row a, column b)
+ *     U(1)    A[V][4]         real angles A_mu(x)
+ *     spinor  psi[V/2][4][3]  (spin, colour) on one parity
+ *   Native spinor buffers hold one half-lattice spinor in the library's
+ *   structure-of-arrays layout at one precision; their size is
+ *   bq_spinor_bytes(). They are allocated by the caller on the device.
+ *
+ * Errors. Every call returns BQ_OK (0) or a BQ_ERR_* code; bq_last_error()
+ * gives a one-line message for the calling thread. No call aborts or traps.
+ * Ownership. The caller owns every pointer it passes; set_* calls copy into
+ * library-owned device storage. All device work is queued on the stream given
+ * to bq_create (NULL = legacy default stream); calls that return host values
+ * synchronise that stream.
+ */
+#ifndef BQCD_H
+#define BQCD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    BQ_OK = 0,
+    BQ_ERR_ARG = 1,             /* invalid argument (null pointer, bad size, bad enum) */
+    BQ_ERR_CUDA = 2,            /* a CUDA runtime call failed */
+    BQ_ERR_NOT_CONVERGED = 3,   /* solver hit max_iter; stats are still filled */
+    BQ_ERR_TIMEOUT = 4,         /* a bounded device-side wait gave up */
+    BQ_ERR_CLOVER_SINGULAR = 5, /* a 6x6 clover block could not be inverted */
+    BQ_ERR_STATE = 6,           /* call made before the fields it needs were set */
+    BQ_ERR_NOMEM = 7            /* device allocation failed */
+};
+
+enum { BQ_PREC_DOUBLE = 0, BQ_PREC_SINGLE = 1, BQ_PREC_HALF = 2 };
+enum { BQ_RECON_18 = 18, BQ_RECON_12 = 12 };
+enum { BQ_HOST = 0, BQ_DEVICE = 1 };
+
+typedef struct bq_ctx bq_ctx;
+
+/* Action parameters (Eq. 1, Eq. 2, Eq. 5). */
+typedef struct {
+    double kappa;   /* hopping parameter */
+    double csw;     /* clover coefficient c_SW */
+    double mu;      /* chemical potential: forward time hop x e^{+mu}, backward x e^{-mu} (Eq. 1) */
+    double t_bc;    /* +1 periodic, -1 antiperiodic fermion boundary in t */
+    double charge;  /* Q_q of Eq. 5: links become e^{-i Q A_mu(x)} U_mu(x) when a U(1) field is set */
+} bq_params;
+
+/* Solver controls. */
+typedef struct {
+    double tol;       /* stop when the TRUE FP64 residual |b - (Mhat^dag Mhat + shift) x| <= tol |b| */
+    int max_iter;     /* iteration cap (inner iterations for mixed precision) */
+    int precision;    /* BQ_PREC_DOUBLE: plain FP64 CG. SINGLE/HALF: reliable-update mixed CG
+                         with that inner (sloppy) precision and FP64 outer residuals */
+    double delta;     /* reliable-update trigger: recompute the FP64 residual when the
+                         iterated residual fell by this factor since the last update (mixed only) */
+    int check_every;  /* iterations between host-side convergence checks (>= 1) */
+    double shift;     /* sigma >= 0: solve (Mhat^dag Mhat + sigma) x = b */
+} bq_solver_params;
+
+typedef struct {
+    int iterations;          /* Krylov iterations performed */
+    int reliable_updates;    /* FP64 residual recomputations (mixed precision) */
+    int converged;           /* 1 if the true residual met tol */
+    double true_residual;    /* |b - (Mhat^dag Mhat + shift) x| / |b| recomputed in FP64 at exit */
+    double seconds;          /* device time of the solve (CUDA events on the library stream) */
+    double dslash_calls;     /* hopping-term launches, each over V/2 sites */
+} bq_solver_stats;
+
+/* ---- context ------------------------------------------------------------- */
+
+/* Create a context for a lattice of extents dims on the current CUDA device,
+ * queueing all work on `cuda_stream` (a cudaStream_t, may be NULL).
+ * BQ_ERR_ARG if an extent is odd or < 2 or V/2 >= 2^31. */
+int bq_create(bq_ctx **ctx, const int dims[4], void *cuda_stream);
+int bq_destroy(bq_ctx *ctx);
+const char *bq_strerror(int status);
+const char *bq_last_error(void);
+
+/* Set kappa, c_SW, mu, the t boundary sign and the U(1) charge. Changing kappa,
+ * c_SW or the charge invalidates derived fields (rebuilt lazily). */
+int bq_set_params(bq_ctx *ctx, const bq_params *p);
+
+/* Link storage for one precision: BQ_RECON_18 (all 18 reals) or BQ_RECON_12
+ * (first two rows; the third is rebuilt as conj(row1 x row2), valid for SU(3)
+ * links only, so it is refused while a U(1) field is set). */
+int bq_set_recon(bq_ctx *ctx, int precision, int recon);
+
+/* Gauge links in canonical layout U[V][4][3][3] complex FP64, from host or
+ * device memory (where = BQ_HOST / BQ_DEVICE). Copied; derived fields rebuilt lazily. */
+int bq_set_gauge(bq_ctx *ctx, const double *U, int where);
+
+/* U(1) angles A[V][4] (Eq. 5), or NULL to remove the U(1) field. */
+int bq_set_u1(bq_ctx *ctx, const double *A, int where);
+
+/* Build the clover term A(x) = 1 + i kappa c_SW sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x)
+ * (Eq. 2; sigma = (i/2)[gamma_mu,gamma_nu], F = traceless part of (Q - Q^dag)/8,
+ * Q = sum of the four plaquette leaves) on the GPU from the SU(3) links, and
+ * its inverse on odd sites (FP64, two 6x6 Hermitian blocks per site).
+ * Called implicitly by the first operator application after a change.
+ * BQ_ERR_CLOVER_SINGULAR if a block has no inverse. */
+int bq_build_clover(bq_ctx *ctx);
+
+/* ---- spinor buffers -------------------------------------------------------- */
+
+/* Bytes of one native half-lattice spinor at `precision` (device buffer). */
+size_t bq_spinor_bytes(const bq_ctx *ctx, int precision);
+
+/* Convert a canonical FP64 half-lattice spinor psi[V/2][4][3] (host or device)
+ * into a native device buffer at `precision`, and back. */
+int bq_spinor_pack(bq_ctx *ctx, void *native, const double *canonical, int precision, int where);
+int bq_spinor_unpack(bq_ctx *ctx, double *canonical, const void *native, int precision, int where);
+
+/* ---- operator (native buffers, device) ---------------------------------- */
+
+/* out = D_hop in restricted to output parity out_parity (Eq. 1 / Eq. 5);
+ * dagger != 0 applies D_hop^dagger. in holds the opposite parity. */
+int bq_apply_dhop(bq_ctx *ctx, void *out, const void *in, int out_parity, int dagger, int precision);
+
+/* out = A_p in, or A_p^{-1} in (inverse != 0), on parity p (Eq. 2). A is Hermitian. */
+int bq_apply_clover(bq_ctx *ctx, void *out, const void *in, int parity, int inverse, int precision);
+
+/* out = Mhat in = A_ee in - kappa^2 D_eo A_oo^{-1} D_oe in, or Mhat^dagger in.
+ * Both spinors are even-parity. out must not alias in. */
+int bq_apply_mhat(bq_ctx *ctx, void *out, const void *in, int dagger, int precision);
+
+/* out = Mhat^dagger Mhat in. out must not alias in. */
+int bq_apply_mdagm(bq_ctx *ctx, void *out, const void *in, int precision);
+
+/* ---- solvers (canonical FP64 spinors, host or device) --------------------- */
+
+/* Solve (Mhat^dagger Mhat + shift) x = b for even-parity x, b in canonical layout.
+ * Plain FP64 CG or reliable-update mixed-precision CG (params->precision).
+ * x is both the output and ignored on input (the solve starts from x = 0).
+ * BQ_ERR_NOT_CONVERGED if max_iter is reached first (x and stats still written). */
+int bq_solve_cg(bq_ctx *ctx, double *x, const double *b, int where,
+                const bq_solver_params *params, bq_solver_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BQCD_H */

@@ -1,0 +1,253 @@
+"""Thin ctypes binding of ``libbqcd_gb300.so`` (C ABI in ``include/bqcd.h``).
+
+Argument marshalling only: every step of the operator and the solvers runs in
+the CUDA library.  Functions keep the C names.  Device buffers are torch CUDA
+tensors (``torch`` supplies device memory and the stream); host arrays are
+numpy arrays or CPU tensors.  A missing or unloadable library raises at import
+time of the first call: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbqcd_gb300.so")
+
+BQ_OK, BQ_ERR_ARG, BQ_ERR_CUDA, BQ_ERR_NOT_CONVERGED, BQ_ERR_TIMEOUT, BQ_ERR_CLOVER_SINGULAR, BQ_ERR_STATE, \
+    BQ_ERR_NOMEM = range(8)
+BQ_PREC_DOUBLE, BQ_PREC_SINGLE, BQ_PREC_HALF = 0, 1, 2
+BQ_RECON_18, BQ_RECON_12 = 18, 12
+BQ_HOST, BQ_DEVICE = 0, 1
+PREC_NAMES = {"double": 0, "single": 1, "half": 2, 0: 0, 1: 1, 2: 2}
+
+
+class bq_params(ctypes.Structure):
+    _fields_ = [("kappa", ctypes.c_double), ("csw", ctypes.c_double), ("mu", ctypes.c_double),
+                ("t_bc", ctypes.c_double), ("charge", ctypes.c_double)]
+
+
+class bq_solver_params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
+                ("delta", ctypes.c_double), ("check_every", ctypes.c_int), ("shift", ctypes.c_double)]
+
+
+class bq_solver_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("converged", ctypes.c_int),
+                ("true_residual", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("dslash_calls", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BqError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        lib = _lib_handle()
+        msg = lib.bq_strerror(status).decode() + ": " + lib.bq_last_error().decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+_SIGS = {
+    "bq_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
+    "bq_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "bq_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "bq_last_error": (ctypes.c_char_p, []),
+    "bq_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(bq_params)]),
+    "bq_set_recon": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "bq_set_gauge": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "bq_set_u1": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "bq_build_clover": (ctypes.c_int, [ctypes.c_void_p]),
+    "bq_spinor_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int]),
+    "bq_spinor_pack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "bq_spinor_unpack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "bq_apply_dhop": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int]),
+    "bq_apply_clover": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int]),
+    "bq_apply_mhat": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "bq_apply_mdagm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "bq_solve_cg": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                   ctypes.POINTER(bq_solver_params), ctypes.POINTER(bq_solver_stats)]),
+}
+
+
+def _lib_handle():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"CUDA library {LIB_PATH} is not built; run __graft_entry__.build()")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status, where):
+    if status != BQ_OK:
+        raise BqError(status, where)
+
+
+def _ptr_where(a):
+    """(pointer, BQ_HOST/BQ_DEVICE) of a numpy array or torch tensor (contiguous)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, BQ_HOST
+    import torch
+
+    if isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), (BQ_DEVICE if a.is_cuda else BQ_HOST)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _dev_ptr(t):
+    p, w = _ptr_where(t)
+    if w != BQ_DEVICE:
+        raise ValueError("native spinor buffers must be CUDA tensors")
+    return p
+
+
+# ---------------------------------------------------------------- the C functions
+
+def bq_create(dims, stream=None):
+    ctx = ctypes.c_void_p()
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(_lib_handle().bq_create(ctypes.byref(ctx), d, ctypes.c_void_p(stream)), "bq_create")
+    return ctx
+
+
+def bq_destroy(ctx):
+    _check(_lib_handle().bq_destroy(ctx), "bq_destroy")
+
+
+def bq_set_params(ctx, kappa, csw=0.0, mu=0.0, t_bc=-1.0, charge=0.0):
+    p = bq_params(kappa, csw, mu, t_bc, charge)
+    _check(_lib_handle().bq_set_params(ctx, ctypes.byref(p)), "bq_set_params")
+
+
+def bq_set_recon(ctx, precision, recon):
+    _check(_lib_handle().bq_set_recon(ctx, PREC_NAMES[precision], int(recon)), "bq_set_recon")
+
+
+def bq_set_gauge(ctx, U):
+    p, w = _ptr_where(U)
+    _check(_lib_handle().bq_set_gauge(ctx, p, w), "bq_set_gauge")
+
+
+def bq_set_u1(ctx, A):
+    if A is None:
+        _check(_lib_handle().bq_set_u1(ctx, None, BQ_HOST), "bq_set_u1")
+        return
+    p, w = _ptr_where(A)
+    _check(_lib_handle().bq_set_u1(ctx, p, w), "bq_set_u1")
+
+
+def bq_build_clover(ctx):
+    _check(_lib_handle().bq_build_clover(ctx), "bq_build_clover")
+
+
+def bq_spinor_bytes(ctx, precision):
+    return int(_lib_handle().bq_spinor_bytes(ctx, PREC_NAMES[precision]))
+
+
+def bq_spinor_pack(ctx, native, canonical, precision):
+    p, w = _ptr_where(canonical)
+    _check(_lib_handle().bq_spinor_pack(ctx, _dev_ptr(native), p, PREC_NAMES[precision], w), "bq_spinor_pack")
+
+
+def bq_spinor_unpack(ctx, canonical, native, precision):
+    p, w = _ptr_where(canonical)
+    _check(_lib_handle().bq_spinor_unpack(ctx, p, _dev_ptr(native), PREC_NAMES[precision], w), "bq_spinor_unpack")
+
+
+def bq_apply_dhop(ctx, out, inp, out_parity, dagger, precision):
+    _check(_lib_handle().bq_apply_dhop(ctx, _dev_ptr(out), _dev_ptr(inp), int(out_parity), int(bool(dagger)),
+                                       PREC_NAMES[precision]), "bq_apply_dhop")
+
+
+def bq_apply_clover(ctx, out, inp, parity, inverse, precision):
+    _check(_lib_handle().bq_apply_clover(ctx, _dev_ptr(out), _dev_ptr(inp), int(parity), int(bool(inverse)),
+                                         PREC_NAMES[precision]), "bq_apply_clover")
+
+
+def bq_apply_mhat(ctx, out, inp, dagger, precision):
+    _check(_lib_handle().bq_apply_mhat(ctx, _dev_ptr(out), _dev_ptr(inp), int(bool(dagger)), PREC_NAMES[precision]),
+           "bq_apply_mhat")
+
+
+def bq_apply_mdagm(ctx, out, inp, precision):
+    _check(_lib_handle().bq_apply_mdagm(ctx, _dev_ptr(out), _dev_ptr(inp), PREC_NAMES[precision]), "bq_apply_mdagm")
+
+
+def bq_solve_cg(ctx, x, b, tol=1e-10, max_iter=10000, precision="double", delta=1e-3, check_every=8, shift=0.0,
+                raise_on_nonconvergence=True):
+    """Solve (Mhat^dag Mhat + shift) x = b; x, b canonical [V/2][4][3] complex128 (host or device)."""
+    px, wx = _ptr_where(x)
+    pb, wb = _ptr_where(b)
+    if wx != wb:
+        raise ValueError("x and b must both be host or both be device buffers")
+    sp = bq_solver_params(tol, int(max_iter), PREC_NAMES[precision], delta, int(check_every), shift)
+    st = bq_solver_stats()
+    s = _lib_handle().bq_solve_cg(ctx, px, pb, wx, ctypes.byref(sp), ctypes.byref(st))
+    if s != BQ_OK and (raise_on_nonconvergence or s != BQ_ERR_NOT_CONVERGED):
+        raise BqError(s, "bq_solve_cg")
+    return st.as_dict()
+
+
+# ---------------------------------------------------------------- convenience
+
+class Lattice:
+    """A context plus torch-allocated native buffers (device memory only)."""
+
+    def __init__(self, dims, kappa, csw=0.0, mu=0.0, t_bc=-1.0, charge=0.0, stream=None):
+        import torch
+
+        self.torch = torch
+        self.dims = tuple(int(d) for d in dims)
+        self.Vh = int(np.prod(self.dims)) // 2
+        self.ctx = bq_create(self.dims, stream)
+        bq_set_params(self.ctx, kappa, csw, mu, t_bc, charge)
+
+    def close(self):
+        if self.ctx is not None:
+            bq_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def spinor(self, precision="double"):
+        n = bq_spinor_bytes(self.ctx, precision)
+        return self.torch.empty(n, dtype=self.torch.uint8, device="cuda")
+
+    def pack(self, canonical, precision="double"):
+        buf = self.spinor(precision)
+        bq_spinor_pack(self.ctx, buf, np.ascontiguousarray(canonical, np.complex128)
+                       if isinstance(canonical, np.ndarray) else canonical, precision)
+        return buf
+
+    def unpack(self, native, precision="double"):
+        out = np.empty((self.Vh, 4, 3), np.complex128)
+        bq_spinor_unpack(self.ctx, out, native, precision)
+        return out

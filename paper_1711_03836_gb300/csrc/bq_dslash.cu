@@ -1,0 +1,330 @@
+// bq_dslash.cu -- the even-odd hopping term D_hop (Eq. 1 / Eq. 5) with fused
+// clover epilogues, and the operators built from it:
+//   D_oe + A_oo^{-1}          (EPI_CLOVINV)
+//   A_ee x - k D_eo in        (EPI_XPAY)
+//   Mhat, Mhat^dagger, Mhat^dagger Mhat.
+//
+// One thread per output site. Each of the eight hops loads the neighbour
+// spinor, projects it with (1 +- gamma_mu) to two spin components (chiral
+// basis), multiplies the two colour vectors by U or U^dagger, and adds the
+// reconstructed four-spinor. The chemical potential factor e^{+-mu} and the
+// time boundary sign multiply the time hops as scalars; U(1) phases are
+// already folded into the links.
+#include "bq_internal.cuh"
+
+struct DslashArgs {
+    void *out;
+    const void *in;
+    const char *links;
+    size_t lblk;  // bytes of one (parity, mu) link block
+    const void *clov;
+    const void *xin;
+    int L0, L1, L2, L3, Lxh, Vh, parity;
+    double cf, cb;  // time-hop factors forward / backward (e^{+mu}, e^{-mu}; swapped for the adjoint)
+    double bc;      // time boundary sign
+    double k;       // xpay coefficient
+};
+
+// (1 + S gamma_mu) psi = (h0, h1, ...) in the chiral basis: the projection ...
+template <int MU, int S, typename T>
+__device__ __forceinline__ void project(const cplx<T> p[12], cplx<T> h0[3], cplx<T> h1[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const cplx<T> p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
+        if (MU == 0) {  // h0 = p0 - i S p3, h1 = p1 - i S p2
+            h0[c] = csub(p0, cimul<S>(p3));
+            h1[c] = csub(p1, cimul<S>(p2));
+        } else if (MU == 1) {  // h0 = p0 - S p3, h1 = p1 + S p2
+            h0[c] = (S > 0) ? csub(p0, p3) : cadd(p0, p3);
+            h1[c] = (S > 0) ? cadd(p1, p2) : csub(p1, p2);
+        } else if (MU == 2) {  // h0 = p0 - i S p2, h1 = p1 + i S p3
+            h0[c] = csub(p0, cimul<S>(p2));
+            h1[c] = cadd(p1, cimul<S>(p3));
+        } else {  // h0 = p0 + S p2, h1 = p1 + S p3
+            h0[c] = (S > 0) ? cadd(p0, p2) : csub(p0, p2);
+            h1[c] = (S > 0) ? cadd(p1, p3) : csub(p1, p3);
+        }
+    }
+}
+
+// ... and the reconstruction of the lower two spin components from (u0, u1)
+template <int MU, int S, typename T>
+__device__ __forceinline__ void accumulate(cplx<T> acc[12], const cplx<T> u0[3], const cplx<T> u1[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        acc[c] = cadd(acc[c], u0[c]);
+        acc[3 + c] = cadd(acc[3 + c], u1[c]);
+        if (MU == 0) {  // (i S u1, i S u0)
+            acc[6 + c] = cadd(acc[6 + c], cimul<S>(u1[c]));
+            acc[9 + c] = cadd(acc[9 + c], cimul<S>(u0[c]));
+        } else if (MU == 1) {  // (S u1, -S u0)
+            acc[6 + c] = (S > 0) ? cadd(acc[6 + c], u1[c]) : csub(acc[6 + c], u1[c]);
+            acc[9 + c] = (S > 0) ? csub(acc[9 + c], u0[c]) : cadd(acc[9 + c], u0[c]);
+        } else if (MU == 2) {  // (i S u0, -i S u1)
+            acc[6 + c] = cadd(acc[6 + c], cimul<S>(u0[c]));
+            acc[9 + c] = csub(acc[9 + c], cimul<S>(u1[c]));
+        } else {  // (S u0, S u1)
+            acc[6 + c] = (S > 0) ? cadd(acc[6 + c], u0[c]) : csub(acc[6 + c], u0[c]);
+            acc[9 + c] = (S > 0) ? cadd(acc[9 + c], u1[c]) : csub(acc[9 + c], u1[c]);
+        }
+    }
+}
+
+template <int PREC, int RECON, int MU, int S, bool BACK, bool SCALE>
+__device__ __forceinline__ void hop(cplx<typename Traits<PREC>::real> acc[12], const void *in, int hn,
+                                    const char *lblk, int hl, int Vh, typename Traits<PREC>::real coef) {
+    using T = typename Traits<PREC>::real;
+    cplx<T> psi[12];
+    SpinorIO<PREC>::load(psi, in, hn, Vh);
+    cplx<T> h0[3], h1[3];
+    project<MU, S>(psi, h0, h1);
+    cplx<T> U[9];
+    LinkIO<PREC, RECON>::load(U, lblk, hl, Vh);
+    cplx<T> u0[3], u1[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        u0[a] = {T(0), T(0)};
+        u1[a] = {T(0), T(0)};
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            if (BACK) {  // U^dagger: [a][b] = conj(U[b][a])
+                u0[a] = cfmac(U[b * 3 + a], h0[b], u0[a]);
+                u1[a] = cfmac(U[b * 3 + a], h1[b], u1[a]);
+            } else {
+                u0[a] = cfma(U[a * 3 + b], h0[b], u0[a]);
+                u1[a] = cfma(U[a * 3 + b], h1[b], u1[a]);
+            }
+        }
+        if (SCALE) {
+            u0[a] = cscale(coef, u0[a]);
+            u1[a] = cscale(coef, u1[a]);
+        }
+    }
+    accumulate<MU, S>(acc, u0, u1);
+}
+
+template <int PREC, int RECON, bool DAG, int EPI>
+__global__ void __launch_bounds__(128) k_dslash(const DslashArgs a) {
+    using T = typename Traits<PREC>::real;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= a.Vh) return;
+    const int Lxh = a.Lxh, Vh = a.Vh;
+    const int xh = h % Lxh;
+    int r = h / Lxh;
+    const int y = r % a.L1;
+    r /= a.L1;
+    const int z = r % a.L2;
+    const int t = r / a.L2;
+    const int x = 2 * xh + ((a.parity + y + z + t) & 1);
+    const char *Lo = a.links + (size_t)a.parity * 4 * a.lblk;        // links U_mu(x), x of the output parity
+    const char *Li = a.links + (size_t)(1 - a.parity) * 4 * a.lblk;  // links U_mu(x - mu)
+    constexpr int SF = DAG ? +1 : -1;  // forward hop: (1 - gamma) for D, (1 + gamma) for D^dagger
+    constexpr int SB = -SF;
+    const int sy = Lxh, sz = Lxh * a.L1, st = sz * a.L2;
+
+    cplx<T> acc[12];
+#pragma unroll
+    for (int c = 0; c < 12; c++) acc[c] = {T(0), T(0)};
+
+    {
+        const int xn = (x + 1 == a.L0) ? 0 : x + 1;
+        hop<PREC, RECON, 0, SF, false, false>(acc, a.in, h - xh + (xn >> 1), Lo, h, Vh, T(1));
+    }
+    {
+        const int xn = (x == 0) ? a.L0 - 1 : x - 1;
+        const int hn = h - xh + (xn >> 1);
+        hop<PREC, RECON, 0, SB, true, false>(acc, a.in, hn, Li, hn, Vh, T(1));
+    }
+    {
+        const int hn = (y + 1 == a.L1) ? h - (a.L1 - 1) * sy : h + sy;
+        hop<PREC, RECON, 1, SF, false, false>(acc, a.in, hn, Lo + a.lblk, h, Vh, T(1));
+    }
+    {
+        const int hn = (y == 0) ? h + (a.L1 - 1) * sy : h - sy;
+        hop<PREC, RECON, 1, SB, true, false>(acc, a.in, hn, Li + a.lblk, hn, Vh, T(1));
+    }
+    {
+        const int hn = (z + 1 == a.L2) ? h - (a.L2 - 1) * sz : h + sz;
+        hop<PREC, RECON, 2, SF, false, false>(acc, a.in, hn, Lo + 2 * a.lblk, h, Vh, T(1));
+    }
+    {
+        const int hn = (z == 0) ? h + (a.L2 - 1) * sz : h - sz;
+        hop<PREC, RECON, 2, SB, true, false>(acc, a.in, hn, Li + 2 * a.lblk, hn, Vh, T(1));
+    }
+    {
+        const bool wrap = (t + 1 == a.L3);
+        const int hn = wrap ? h - (a.L3 - 1) * st : h + st;
+        const T coef = (T)(wrap ? a.cf * a.bc : a.cf);
+        hop<PREC, RECON, 3, SF, false, true>(acc, a.in, hn, Lo + 3 * a.lblk, h, Vh, coef);
+    }
+    {
+        const bool wrap = (t == 0);
+        const int hn = wrap ? h + (a.L3 - 1) * st : h - st;
+        const T coef = (T)(wrap ? a.cb * a.bc : a.cb);
+        hop<PREC, RECON, 3, SB, true, true>(acc, a.in, hn, Li + 3 * a.lblk, hn, Vh, coef);
+    }
+
+    if (EPI == EPI_PLAIN) {
+        SpinorIO<PREC>::store(a.out, h, Vh, acc);
+    } else if (EPI == EPI_CLOVINV) {
+        cplx<T> o[12];
+        clover_apply_site<PREC>(o, acc, a.clov, h, Vh);
+        SpinorIO<PREC>::store(a.out, h, Vh, o);
+    } else {
+        cplx<T> xv[12], o[12];
+        SpinorIO<PREC>::load(xv, a.xin, h, Vh);
+        clover_apply_site<PREC>(o, xv, a.clov, h, Vh);
+        const T k = (T)a.k;
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            o[c].re = fma(-k, acc[c].re, o[c].re);
+            o[c].im = fma(-k, acc[c].im, o[c].im);
+        }
+        SpinorIO<PREC>::store(a.out, h, Vh, o);
+    }
+}
+
+template <int PREC>
+__global__ void k_clover(void *out, const void *in, const void *clov, int Vh) {
+    using T = typename Traits<PREC>::real;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= Vh) return;
+    cplx<T> s[12], o[12];
+    SpinorIO<PREC>::load(s, in, h, Vh);
+    clover_apply_site<PREC>(o, s, clov, h, Vh);
+    SpinorIO<PREC>::store(out, h, Vh, o);
+}
+
+// --------------------------------------------------------------------------
+// dispatch
+
+template <int PREC, int RECON>
+static void launch_dslash_pr(const DslashArgs &a, bool dag, int epi, unsigned grid, cudaStream_t s) {
+    if (dag) {
+        if (epi == EPI_PLAIN) k_dslash<PREC, RECON, true, EPI_PLAIN><<<grid, 128, 0, s>>>(a);
+        else if (epi == EPI_CLOVINV) k_dslash<PREC, RECON, true, EPI_CLOVINV><<<grid, 128, 0, s>>>(a);
+        else k_dslash<PREC, RECON, true, EPI_XPAY><<<grid, 128, 0, s>>>(a);
+    } else {
+        if (epi == EPI_PLAIN) k_dslash<PREC, RECON, false, EPI_PLAIN><<<grid, 128, 0, s>>>(a);
+        else if (epi == EPI_CLOVINV) k_dslash<PREC, RECON, false, EPI_CLOVINV><<<grid, 128, 0, s>>>(a);
+        else k_dslash<PREC, RECON, false, EPI_XPAY><<<grid, 128, 0, s>>>(a);
+    }
+}
+
+int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_parity, int dagger, int epi,
+                     const void *xin, double k) {
+    BQ_TRY(bq_prepare_links(c, prec));
+    if (epi != EPI_PLAIN) BQ_TRY(bq_prepare_clover(c, prec));
+    DslashArgs a;
+    a.out = out;
+    a.in = in;
+    a.links = links_ptr(c, prec);
+    a.lblk = links_block_bytes(c, prec);
+    a.clov = (epi == EPI_CLOVINV) ? clover_ptr(c, prec, out_parity, 1)
+           : (epi == EPI_XPAY)    ? clover_ptr(c, prec, out_parity, 0)
+                                  : nullptr;
+    a.xin = xin;
+    a.L0 = c->L[0];
+    a.L1 = c->L[1];
+    a.L2 = c->L[2];
+    a.L3 = c->L[3];
+    a.Lxh = c->L[0] / 2;
+    a.Vh = c->Vh;
+    a.parity = out_parity;
+    double ef = exp(c->params.mu), eb = exp(-c->params.mu);
+    a.cf = dagger ? eb : ef;
+    a.cb = dagger ? ef : eb;
+    a.bc = c->params.t_bc;
+    a.k = k;
+    unsigned grid = (unsigned)((c->Vh + 127) / 128);
+    int recon = c->links_recon[prec];
+    if (prec == BQ_PREC_DOUBLE) {
+        if (recon == 12) launch_dslash_pr<BQ_PREC_DOUBLE, 12>(a, dagger, epi, grid, c->stream);
+        else launch_dslash_pr<BQ_PREC_DOUBLE, 18>(a, dagger, epi, grid, c->stream);
+    } else if (prec == BQ_PREC_SINGLE) {
+        if (recon == 12) launch_dslash_pr<BQ_PREC_SINGLE, 12>(a, dagger, epi, grid, c->stream);
+        else launch_dslash_pr<BQ_PREC_SINGLE, 18>(a, dagger, epi, grid, c->stream);
+    } else {
+        if (recon == 12) launch_dslash_pr<BQ_PREC_HALF, 12>(a, dagger, epi, grid, c->stream);
+        else launch_dslash_pr<BQ_PREC_HALF, 18>(a, dagger, epi, grid, c->stream);
+    }
+    BQ_LAUNCH_CHECK();
+    return BQ_OK;
+}
+
+int bq_clover_launch(bq_ctx *c, int prec, void *out, const void *in, int parity, int inverse) {
+    BQ_TRY(bq_prepare_clover(c, prec));
+    const void *cl = clover_ptr(c, prec, parity, inverse);
+    unsigned grid = (unsigned)((c->Vh + 127) / 128);
+    if (prec == BQ_PREC_DOUBLE) k_clover<BQ_PREC_DOUBLE><<<grid, 128, 0, c->stream>>>(out, in, cl, c->Vh);
+    else if (prec == BQ_PREC_SINGLE) k_clover<BQ_PREC_SINGLE><<<grid, 128, 0, c->stream>>>(out, in, cl, c->Vh);
+    else k_clover<BQ_PREC_HALF><<<grid, 128, 0, c->stream>>>(out, in, cl, c->Vh);
+    BQ_LAUNCH_CHECK();
+    return BQ_OK;
+}
+
+// Mhat in = A_ee in - kappa^2 D_eo A_oo^{-1} D_oe in (adjoint: D -> D^dagger, A Hermitian)
+int bq_mhat_launch(bq_ctx *c, int prec, void *out, const void *in, int dagger, void *tmp_odd) {
+    BQ_TRY(bq_dslash_launch(c, prec, tmp_odd, in, 1, dagger, EPI_CLOVINV, nullptr, 0.0));
+    double k2 = c->params.kappa * c->params.kappa;
+    return bq_dslash_launch(c, prec, out, tmp_odd, 0, dagger, EPI_XPAY, in, k2);
+}
+
+int bq_mdagm_launch(bq_ctx *c, int prec, void *out, const void *in, void *tmp_odd, void *tmp_even) {
+    BQ_TRY(bq_mhat_launch(c, prec, tmp_even, in, 0, tmp_odd));
+    return bq_mhat_launch(c, prec, out, tmp_even, 1, tmp_odd);
+}
+
+int bq_workspace(bq_ctx *c, int prec) {
+    size_t b = spinor_bytes_per_site(prec) * (size_t)c->Vh;
+    BQ_TRY(bq_alloc((void **)&c->tmp_odd[prec], b));
+    BQ_TRY(bq_alloc((void **)&c->tmp_even[prec], b));
+    return BQ_OK;
+}
+
+// --------------------------------------------------------------------------
+// C ABI
+
+static int check_apply(bq_ctx *c, const void *out, const void *in, int prec) {
+    if (!c || !out || !in || !(prec == BQ_PREC_DOUBLE || prec == BQ_PREC_SINGLE || prec == BQ_PREC_HALF)) {
+        bq_set_error("bad arguments to an apply call");
+        return BQ_ERR_ARG;
+    }
+    if (!c->have_gauge) {
+        bq_set_error("gauge field not set");
+        return BQ_ERR_STATE;
+    }
+    return BQ_OK;
+}
+
+extern "C" int bq_apply_dhop(bq_ctx *c, void *out, const void *in, int out_parity, int dagger, int prec) {
+    BQ_TRY(check_apply(c, out, in, prec));
+    if (out_parity != 0 && out_parity != 1) return BQ_ERR_ARG;
+    return bq_dslash_launch(c, prec, out, in, out_parity, dagger ? 1 : 0, EPI_PLAIN, nullptr, 0.0);
+}
+
+extern "C" int bq_apply_clover(bq_ctx *c, void *out, const void *in, int parity, int inverse, int prec) {
+    BQ_TRY(check_apply(c, out, in, prec));
+    if (parity != 0 && parity != 1) return BQ_ERR_ARG;
+    return bq_clover_launch(c, prec, out, in, parity, inverse ? 1 : 0);
+}
+
+extern "C" int bq_apply_mhat(bq_ctx *c, void *out, const void *in, int dagger, int prec) {
+    BQ_TRY(check_apply(c, out, in, prec));
+    if (out == in) {
+        bq_set_error("bq_apply_mhat: out aliases in");
+        return BQ_ERR_ARG;
+    }
+    BQ_TRY(bq_workspace(c, prec));
+    return bq_mhat_launch(c, prec, out, in, dagger ? 1 : 0, c->tmp_odd[prec]);
+}
+
+extern "C" int bq_apply_mdagm(bq_ctx *c, void *out, const void *in, int prec) {
+    BQ_TRY(check_apply(c, out, in, prec));
+    if (out == in) {
+        bq_set_error("bq_apply_mdagm: out aliases in");
+        return BQ_ERR_ARG;
+    }
+    BQ_TRY(bq_workspace(c, prec));
+    return bq_mdagm_launch(c, prec, out, in, c->tmp_odd[prec], c->tmp_even[prec]);
+}

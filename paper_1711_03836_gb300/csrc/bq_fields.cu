@@ -1,0 +1,627 @@
+// bq_fields.cu -- context, field upload and derived-field preparation.
+//
+//  * links: canonical FP64 U[V][4][3][3] -> native per-precision layout, with
+//    the QCD+QED phase e^{-i Q A_mu(x)} of Eq. 5 folded into U_mu(x);
+//  * clover: A(x) = 1 + i kappa c_SW sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x) of Eq. 2,
+//    built on the GPU in FP64 from the four plaquette leaves, written as two
+//    packed Hermitian 6x6 chiral blocks, inverted per block in FP64 (Gauss-Jordan,
+//    partial pivoting), then stored at each solve precision;
+//  * spinors: canonical FP64 [Vh][4][3] <-> native SoA at each precision.
+#include <stdarg.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "bq_internal.cuh"
+
+// --------------------------------------------------------------------------
+// errors
+
+static thread_local char g_err[512] = "";
+
+void bq_set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+extern "C" const char *bq_last_error(void) { return g_err; }
+
+extern "C" const char *bq_strerror(int s) {
+    switch (s) {
+        case BQ_OK: return "ok";
+        case BQ_ERR_ARG: return "invalid argument";
+        case BQ_ERR_CUDA: return "CUDA error";
+        case BQ_ERR_NOT_CONVERGED: return "solver did not converge";
+        case BQ_ERR_TIMEOUT: return "device-side wait timed out";
+        case BQ_ERR_CLOVER_SINGULAR: return "singular clover block";
+        case BQ_ERR_STATE: return "required field not set";
+        case BQ_ERR_NOMEM: return "device allocation failed";
+        default: return "unknown status";
+    }
+}
+
+int bq_alloc(void **p, size_t bytes) {
+    if (*p) return BQ_OK;
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        bq_set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        return BQ_ERR_NOMEM;
+    }
+    return BQ_OK;
+}
+
+static int valid_prec(int p) { return p == BQ_PREC_DOUBLE || p == BQ_PREC_SINGLE || p == BQ_PREC_HALF; }
+
+static void invalidate_derived(bq_ctx *c, int links, int clover) {
+    for (int p = 0; p < BQ_NPREC; p++) {
+        if (links) c->links_valid[p] = 0;
+        if (clover) c->clov_valid[p] = 0;
+    }
+    if (clover) c->clov_master_valid = 0;
+}
+
+// --------------------------------------------------------------------------
+// context
+
+extern "C" int bq_create(bq_ctx **out, const int dims[4], void *stream) {
+    if (!out || !dims) {
+        bq_set_error("bq_create: null pointer");
+        return BQ_ERR_ARG;
+    }
+    *out = nullptr;
+    long long V = 1;
+    for (int k = 0; k < 4; k++) {
+        if (dims[k] < 2 || dims[k] % 2) {
+            bq_set_error("bq_create: extent %d of direction %d must be even and >= 2", dims[k], k);
+            return BQ_ERR_ARG;
+        }
+        V *= dims[k];
+    }
+    if (V / 2 >= (1LL << 31) / 8) {
+        bq_set_error("bq_create: volume %lld too large", V);
+        return BQ_ERR_ARG;
+    }
+    bq_ctx *c = (bq_ctx *)calloc(1, sizeof(bq_ctx));
+    if (!c) return BQ_ERR_NOMEM;
+    for (int k = 0; k < 4; k++) c->L[k] = dims[k];
+    c->V = V;
+    c->Vh = (int)(V / 2);
+    c->stream = (cudaStream_t)stream;
+    cudaGetDevice(&c->device);
+    c->params.kappa = 0.125;
+    c->params.csw = 0.0;
+    c->params.mu = 0.0;
+    c->params.t_bc = -1.0;
+    c->params.charge = 0.0;
+    for (int p = 0; p < BQ_NPREC; p++) c->recon[p] = BQ_RECON_18;
+    int s = bq_alloc((void **)&c->red_partials, sizeof(double) * 8 * 4096);
+    if (s == BQ_OK) s = bq_alloc((void **)&c->red_ticket, sizeof(unsigned int) * 16);
+    if (s == BQ_OK) s = bq_alloc((void **)&c->dev_flag, sizeof(int) * 16);
+    if (s == BQ_OK && cudaMemsetAsync(c->red_ticket, 0, sizeof(unsigned int) * 16, c->stream) != cudaSuccess)
+        s = BQ_ERR_CUDA;
+    if (s == BQ_OK && cudaMemsetAsync(c->dev_flag, 0, sizeof(int) * 16, c->stream) != cudaSuccess) s = BQ_ERR_CUDA;
+    if (s != BQ_OK) {
+        bq_destroy(c);
+        return s;
+    }
+    *out = c;
+    return BQ_OK;
+}
+
+void bq_solver_free(bq_ctx *c);  // bq_solvers.cu
+
+extern "C" int bq_destroy(bq_ctx *c) {
+    if (!c) return BQ_OK;
+    cudaStreamSynchronize(c->stream);
+    bq_solver_free(c);
+    cudaFree(c->U_canon);
+    cudaFree(c->A_u1);
+    for (int p = 0; p < BQ_NPREC; p++) {
+        cudaFree(c->links[p]);
+        if (p != BQ_PREC_DOUBLE) cudaFree(c->clov[p]);
+        cudaFree(c->tmp_odd[p]);
+        cudaFree(c->tmp_even[p]);
+    }
+    cudaFree(c->clov_master);
+    cudaFree(c->canon_stage);
+    cudaFree(c->red_partials);
+    cudaFree(c->red_ticket);
+    cudaFree(c->dev_flag);
+    free(c);
+    return BQ_OK;
+}
+
+extern "C" int bq_set_params(bq_ctx *c, const bq_params *p) {
+    if (!c || !p) {
+        bq_set_error("bq_set_params: null pointer");
+        return BQ_ERR_ARG;
+    }
+    if (!(p->t_bc == 1.0 || p->t_bc == -1.0)) {
+        bq_set_error("bq_set_params: t_bc must be +1 or -1");
+        return BQ_ERR_ARG;
+    }
+    int clover_changed = p->kappa != c->params.kappa || p->csw != c->params.csw;
+    int links_changed = p->charge != c->params.charge && c->A_u1;
+    c->params = *p;
+    invalidate_derived(c, links_changed, clover_changed);
+    return BQ_OK;
+}
+
+extern "C" int bq_set_recon(bq_ctx *c, int prec, int recon) {
+    if (!c || !valid_prec(prec) || !(recon == BQ_RECON_18 || recon == BQ_RECON_12)) {
+        bq_set_error("bq_set_recon: bad arguments");
+        return BQ_ERR_ARG;
+    }
+    if (recon == BQ_RECON_12 && c->A_u1) {
+        bq_set_error("bq_set_recon: 12-real links need SU(3) links; a U(1) field is set");
+        return BQ_ERR_ARG;
+    }
+    if (c->recon[prec] != recon) {
+        c->recon[prec] = recon;
+        c->links_valid[prec] = 0;
+    }
+    return BQ_OK;
+}
+
+extern "C" int bq_set_gauge(bq_ctx *c, const double *U, int where) {
+    if (!c || !U || !(where == BQ_HOST || where == BQ_DEVICE)) {
+        bq_set_error("bq_set_gauge: bad arguments");
+        return BQ_ERR_ARG;
+    }
+    size_t bytes = (size_t)c->V * 4 * 9 * sizeof(double2);
+    BQ_TRY(bq_alloc((void **)&c->U_canon, bytes));
+    BQ_CUDA_TRY(cudaMemcpyAsync(c->U_canon, U, bytes,
+                                where == BQ_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+    if (where == BQ_HOST) BQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->have_gauge = 1;
+    invalidate_derived(c, 1, 1);
+    return BQ_OK;
+}
+
+extern "C" int bq_set_u1(bq_ctx *c, const double *A, int where) {
+    if (!c || !(where == BQ_HOST || where == BQ_DEVICE)) {
+        bq_set_error("bq_set_u1: bad arguments");
+        return BQ_ERR_ARG;
+    }
+    if (!A) {
+        cudaFree(c->A_u1);
+        c->A_u1 = nullptr;
+        invalidate_derived(c, 1, 0);
+        return BQ_OK;
+    }
+    for (int p = 0; p < BQ_NPREC; p++)
+        if (c->recon[p] == BQ_RECON_12) {
+            bq_set_error("bq_set_u1: precision %d uses 12-real links, which need SU(3) links", p);
+            return BQ_ERR_ARG;
+        }
+    size_t bytes = (size_t)c->V * 4 * sizeof(double);
+    BQ_TRY(bq_alloc((void **)&c->A_u1, bytes));
+    BQ_CUDA_TRY(cudaMemcpyAsync(c->A_u1, A, bytes,
+                                where == BQ_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+    if (where == BQ_HOST) BQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    invalidate_derived(c, 1, 0);
+    return BQ_OK;
+}
+
+// --------------------------------------------------------------------------
+// geometry helper for setup kernels (full-lattice lex index)
+
+struct Geo {
+    int L0, L1, L2, L3;
+    long long V;
+    int Vh;
+};
+
+__device__ __forceinline__ void lex_coords(const Geo &g, long long lex, int c[4]) {
+    c[0] = (int)(lex % g.L0);
+    lex /= g.L0;
+    c[1] = (int)(lex % g.L1);
+    lex /= g.L1;
+    c[2] = (int)(lex % g.L2);
+    c[3] = (int)(lex / g.L2);
+}
+__device__ __forceinline__ long long lex_of(const Geo &g, const int c[4]) {
+    return c[0] + (long long)g.L0 * (c[1] + (long long)g.L1 * (c[2] + (long long)g.L2 * c[3]));
+}
+__device__ __forceinline__ long long lex_step(const Geo &g, long long lex, int mu, int dir) {
+    int c[4];
+    lex_coords(g, lex, c);
+    const int Ls[4] = {g.L0, g.L1, g.L2, g.L3};
+    c[mu] += dir;
+    if (c[mu] < 0) c[mu] += Ls[mu];
+    if (c[mu] >= Ls[mu]) c[mu] -= Ls[mu];
+    return lex_of(g, c);
+}
+
+static Geo geo_of(const bq_ctx *c) { return Geo{c->L[0], c->L[1], c->L[2], c->L[3], c->V, c->Vh}; }
+
+static unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// --------------------------------------------------------------------------
+// links
+
+template <int PREC, int RECON>
+__global__ void k_pack_links(char *dst, size_t blk, const double2 *U, const double *A, double charge, Geo g) {
+    long long lex = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (lex >= g.V) return;
+    int c[4];
+    lex_coords(g, lex, c);
+    int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+    int h = (int)(lex >> 1);
+    for (int mu = 0; mu < 4; mu++) {
+        double2 u[9];
+        const double2 *src = U + (lex * 4 + mu) * 9;
+        for (int k = 0; k < 9; k++) u[k] = src[k];
+        if (A) {
+            double s, co;
+            sincos(-charge * A[lex * 4 + mu], &s, &co);
+            for (int k = 0; k < 9; k++) u[k] = make_double2(co * u[k].x - s * u[k].y, co * u[k].y + s * u[k].x);
+        }
+        LinkIO<PREC, RECON>::store(dst + (size_t)(par * 4 + mu) * blk, h, g.Vh, u);
+    }
+}
+
+int bq_prepare_links(bq_ctx *c, int prec) {
+    if (!c->have_gauge) {
+        bq_set_error("gauge field not set");
+        return BQ_ERR_STATE;
+    }
+    if (c->links_valid[prec] && c->links_recon[prec] == c->recon[prec]) return BQ_OK;
+    int recon = c->recon[prec];
+    size_t blk = link_bytes_per_link(prec, recon) * (size_t)c->Vh;
+    if (c->links[prec] && c->links_recon[prec] != recon) {
+        cudaFree(c->links[prec]);
+        c->links[prec] = nullptr;
+    }
+    BQ_TRY(bq_alloc((void **)&c->links[prec], blk * 8));
+    c->links_recon[prec] = recon;
+    Geo g = geo_of(c);
+    unsigned grid = grid_for(c->V, 128);
+    double q = c->params.charge;
+#define PACK(P, R) k_pack_links<P, R><<<grid, 128, 0, c->stream>>>(c->links[prec], blk, c->U_canon, c->A_u1, q, g)
+    if (prec == BQ_PREC_DOUBLE) {
+        if (recon == 12) PACK(BQ_PREC_DOUBLE, 12); else PACK(BQ_PREC_DOUBLE, 18);
+    } else if (prec == BQ_PREC_SINGLE) {
+        if (recon == 12) PACK(BQ_PREC_SINGLE, 12); else PACK(BQ_PREC_SINGLE, 18);
+    } else {
+        if (recon == 12) PACK(BQ_PREC_HALF, 12); else PACK(BQ_PREC_HALF, 18);
+    }
+#undef PACK
+    BQ_LAUNCH_CHECK();
+    c->links_valid[prec] = 1;
+    return BQ_OK;
+}
+
+// --------------------------------------------------------------------------
+// clover term
+
+struct M3 {
+    cplx<double> a[9];
+};
+
+__device__ __forceinline__ M3 load_link(const double2 *U, long long lex, int mu) {
+    M3 m;
+    const double2 *p = U + (lex * 4 + mu) * 9;
+    for (int k = 0; k < 9; k++) m.a[k] = {p[k].x, p[k].y};
+    return m;
+}
+__device__ __forceinline__ M3 mdag(const M3 &x) {
+    M3 m;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) m.a[i * 3 + j] = cconj(x.a[j * 3 + i]);
+    return m;
+}
+__device__ __forceinline__ M3 mmul(const M3 &x, const M3 &y) {
+    M3 m;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            cplx<double> s = {0, 0};
+            for (int k = 0; k < 3; k++) s = cfma(x.a[i * 3 + k], y.a[k * 3 + j], s);
+            m.a[i * 3 + j] = s;
+        }
+    return m;
+}
+
+// traceless anti-Hermitian part of the clover-leaf sum in the mu-nu plane: (Q - Q^dag)/8 - trace/3
+__device__ void field_strength(const double2 *U, const Geo &g, long long x, int mu, int nu, M3 &F) {
+    long long xpm = lex_step(g, x, mu, +1), xpn = lex_step(g, x, nu, +1);
+    long long xmm = lex_step(g, x, mu, -1), xmn = lex_step(g, x, nu, -1);
+    long long xmm_pn = lex_step(g, xmm, nu, +1), xmm_mn = lex_step(g, xmm, nu, -1);
+    long long xmn_pm = lex_step(g, xmn, mu, +1);
+    M3 Q;
+    // leaf 1: x -> x+mu -> x+mu+nu -> x+nu -> x
+    Q = mmul(mmul(load_link(U, x, mu), load_link(U, xpm, nu)), mmul(mdag(load_link(U, xpn, mu)), mdag(load_link(U, x, nu))));
+    // leaf 2: x -> x+nu -> x+nu-mu -> x-mu -> x
+    M3 t = mmul(mmul(load_link(U, x, nu), mdag(load_link(U, xmm_pn, mu))),
+                mmul(mdag(load_link(U, xmm, nu)), load_link(U, xmm, mu)));
+    for (int k = 0; k < 9; k++) Q.a[k] = cadd(Q.a[k], t.a[k]);
+    // leaf 3: x -> x-mu -> x-mu-nu -> x-nu -> x
+    t = mmul(mmul(mdag(load_link(U, xmm, mu)), mdag(load_link(U, xmm_mn, nu))),
+             mmul(load_link(U, xmm_mn, mu), load_link(U, xmn, nu)));
+    for (int k = 0; k < 9; k++) Q.a[k] = cadd(Q.a[k], t.a[k]);
+    // leaf 4: x -> x-nu -> x-nu+mu -> x+mu -> x
+    t = mmul(mmul(mdag(load_link(U, xmn, nu)), load_link(U, xmn, mu)),
+             mmul(load_link(U, xmn_pm, nu), mdag(load_link(U, x, mu))));
+    for (int k = 0; k < 9; k++) Q.a[k] = cadd(Q.a[k], t.a[k]);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            cplx<double> q = Q.a[i * 3 + j], qt = cconj(Q.a[j * 3 + i]);
+            F.a[i * 3 + j] = cscale(0.125, csub(q, qt));
+        }
+    cplx<double> tr = cscale(1.0 / 3.0, cadd(cadd(F.a[0], F.a[4]), F.a[8]));
+    F.a[0] = csub(F.a[0], tr);
+    F.a[4] = csub(F.a[4], tr);
+    F.a[8] = csub(F.a[8], tr);
+}
+
+// write a Hermitian 6x6 (given as full matrix) into packed FP64 storage of one block
+__device__ __forceinline__ void store_herm6(double2 *blk, int b, int h, int Vh, const cplx<double> B[36]) {
+    double2 *p = blk + (size_t)(18 * b) * Vh + h;
+    for (int k = 0; k < 3; k++) p[(size_t)k * Vh] = make_double2(B[(2 * k) * 7].re, B[(2 * k + 1) * 7].re);
+    int k = 0;
+    for (int i = 0; i < 6; i++)
+        for (int j = i + 1; j < 6; j++) {
+            p[(size_t)(3 + k) * Vh] = make_double2(B[i * 6 + j].re, B[i * 6 + j].im);
+            k++;
+        }
+}
+__device__ __forceinline__ void load_herm6(const double2 *blk, int b, int h, int Vh, cplx<double> B[36]) {
+    const double2 *p = blk + (size_t)(18 * b) * Vh + h;
+    for (int k = 0; k < 3; k++) {
+        double2 v = p[(size_t)k * Vh];
+        B[(2 * k) * 7] = {v.x, 0.0};
+        B[(2 * k + 1) * 7] = {v.y, 0.0};
+    }
+    int k = 0;
+    for (int i = 0; i < 6; i++)
+        for (int j = i + 1; j < 6; j++) {
+            double2 v = p[(size_t)(3 + k) * Vh];
+            B[i * 6 + j] = {v.x, v.y};
+            B[j * 6 + i] = {v.x, -v.y};
+            k++;
+        }
+}
+
+// A(x) per site. In the chiral basis sigma_{mu nu} is block diagonal; with
+// E1 = F14 -+ F23 ... the chirality block is 1 + i kc [[E3, E1 - iE2], [E1 + iE2, -E3]]
+// (upper block: E1 = F14 - F23, E2 = F24 + F13, E3 = F34 - F12;
+//  lower block: E1 = -F14 - F23, E2 = -F24 + F13, E3 = -F34 - F12).
+__global__ void k_build_clover(double2 *master, size_t pblk, const double2 *U, Geo g, double kc) {
+    long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.V) return;
+    int c[4];
+    lex_coords(g, x, c);
+    int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+    int h = (int)(x >> 1);
+    // planes: 0:(0,1) 1:(0,2) 2:(0,3) 3:(1,2) 4:(1,3) 5:(2,3)
+    M3 F[6];
+    int pl = 0;
+    for (int mu = 0; mu < 4; mu++)
+        for (int nu = mu + 1; nu < 4; nu++) field_strength(U, g, x, mu, nu, F[pl++]);
+    double2 *dst = master + (size_t)(par * 2 + 0) * pblk;
+    for (int b = 0; b < 2; b++) {
+        double sg = b == 0 ? 1.0 : -1.0;
+        M3 E1, E2, E3;
+        for (int k = 0; k < 9; k++) {
+            E1.a[k] = csub(cscale(sg, F[2].a[k]), F[3].a[k]);  // +-F14 - F23
+            E2.a[k] = cadd(cscale(sg, F[4].a[k]), F[1].a[k]);  // +-F24 + F13
+            E3.a[k] = csub(cscale(sg, F[5].a[k]), F[0].a[k]);  // +-F34 - F12
+        }
+        cplx<double> B[36];
+        for (int a = 0; a < 3; a++)
+            for (int bb = 0; bb < 3; bb++) {
+                cplx<double> e1 = E1.a[a * 3 + bb], e2 = E2.a[a * 3 + bb], e3 = E3.a[a * 3 + bb];
+                double d = (a == bb) ? 1.0 : 0.0;
+                // i kc E3, i kc (E1 - i E2) = i kc E1 + kc E2, i kc (E1 + i E2) = i kc E1 - kc E2, -i kc E3
+                B[(0 + a) * 6 + (0 + bb)] = {d - kc * e3.im, kc * e3.re};
+                B[(0 + a) * 6 + (3 + bb)] = {-kc * e1.im + kc * e2.re, kc * e1.re + kc * e2.im};
+                B[(3 + a) * 6 + (0 + bb)] = {-kc * e1.im - kc * e2.re, kc * e1.re - kc * e2.im};
+                B[(3 + a) * 6 + (3 + bb)] = {d + kc * e3.im, -kc * e3.re};
+            }
+        store_herm6(dst, b, h, g.Vh, B);
+    }
+}
+
+// inverse of each 6x6 block (Gauss-Jordan with partial pivoting, FP64)
+__global__ void k_invert_clover(double2 *master, size_t pblk, int Vh, int *flag) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 4 * Vh) return;
+    int h = idx % Vh;
+    int b = (idx / Vh) & 1;
+    int par = idx / (2 * Vh);
+    const double2 *src = master + (size_t)(par * 2 + 0) * pblk;
+    double2 *dst = master + (size_t)(par * 2 + 1) * pblk;
+    cplx<double> a[6][12];
+    cplx<double> B[36];
+    load_herm6(src, b, h, Vh, B);
+    for (int i = 0; i < 6; i++)
+        for (int j = 0; j < 6; j++) {
+            a[i][j] = B[i * 6 + j];
+            a[i][6 + j] = {i == j ? 1.0 : 0.0, 0.0};
+        }
+    for (int col = 0; col < 6; col++) {
+        int piv = col;
+        double best = hypot(a[col][col].re, a[col][col].im);
+        for (int r = col + 1; r < 6; r++) {
+            double m = hypot(a[r][col].re, a[r][col].im);
+            if (m > best) {
+                best = m;
+                piv = r;
+            }
+        }
+        if (!(best > 1e-300)) {
+            atomicExch(flag, 1);
+            return;
+        }
+        if (piv != col)
+            for (int j = 0; j < 12; j++) {
+                cplx<double> t = a[col][j];
+                a[col][j] = a[piv][j];
+                a[piv][j] = t;
+            }
+        cplx<double> p = a[col][col];
+        double n2 = p.re * p.re + p.im * p.im;
+        cplx<double> inv = {p.re / n2, -p.im / n2};
+        for (int j = 0; j < 12; j++) a[col][j] = cmul(inv, a[col][j]);
+        for (int r = 0; r < 6; r++) {
+            if (r == col) continue;
+            cplx<double> f = a[r][col];
+            for (int j = 0; j < 12; j++) a[r][j] = csub(a[r][j], cmul(f, a[col][j]));
+        }
+    }
+    // the inverse of a Hermitian matrix is Hermitian: keep the diagonal's real part and the upper triangle
+    for (int i = 0; i < 6; i++)
+        for (int j = 0; j < 6; j++) B[i * 6 + j] = a[i][6 + j];
+    store_herm6(dst, b, h, Vh, B);
+}
+
+template <int PREC>
+__global__ void k_convert_clover(char *dst, const double2 *src, int Vh, int nblk) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nblk * Vh) return;
+    int h = idx % Vh, blk = idx / Vh;
+    const double2 *s = src + (size_t)blk * 36 * Vh + h;
+    double r[72];
+    for (int k = 0; k < 36; k++) {
+        double2 v = s[(size_t)k * Vh];
+        r[2 * k] = v.x;
+        r[2 * k + 1] = v.y;
+    }
+    if (PREC == BQ_PREC_SINGLE) {
+        float4 *d = reinterpret_cast<float4 *>(dst) + (size_t)blk * 18 * Vh + h;
+        for (int k = 0; k < 18; k++)
+            d[(size_t)k * Vh] = make_float4((float)r[4 * k], (float)r[4 * k + 1], (float)r[4 * k + 2], (float)r[4 * k + 3]);
+    } else {
+        uint2 *d = reinterpret_cast<uint2 *>(dst) + (size_t)blk * 18 * Vh + h;
+        for (int k = 0; k < 18; k++) {
+            uint2 v;
+            v.x = f2h((float)r[4 * k], (float)r[4 * k + 1]);
+            v.y = f2h((float)r[4 * k + 2], (float)r[4 * k + 3]);
+            d[(size_t)k * Vh] = v;
+        }
+    }
+}
+
+extern "C" int bq_build_clover(bq_ctx *c) {
+    if (!c) return BQ_ERR_ARG;
+    if (!c->have_gauge) {
+        bq_set_error("gauge field not set");
+        return BQ_ERR_STATE;
+    }
+    size_t pblk = (size_t)36 * c->Vh;  // double2 per (parity, inverse) block
+    BQ_TRY(bq_alloc((void **)&c->clov_master, sizeof(double2) * pblk * 4));
+    Geo g = geo_of(c);
+    BQ_CUDA_TRY(cudaMemsetAsync(c->dev_flag, 0, sizeof(int), c->stream));
+    k_build_clover<<<grid_for(c->V, 64), 64, 0, c->stream>>>((double2 *)c->clov_master, pblk, c->U_canon, g,
+                                                               c->params.kappa * c->params.csw);
+    BQ_LAUNCH_CHECK();
+    k_invert_clover<<<grid_for(4LL * c->Vh, 64), 64, 0, c->stream>>>((double2 *)c->clov_master, pblk, c->Vh,
+                                                                     c->dev_flag);
+    BQ_LAUNCH_CHECK();
+    int flag = 0;
+    BQ_CUDA_TRY(cudaMemcpyAsync(&flag, c->dev_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    BQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (flag) {
+        bq_set_error("clover block without inverse");
+        return BQ_ERR_CLOVER_SINGULAR;
+    }
+    c->clov_master_valid = 1;
+    c->clov[BQ_PREC_DOUBLE] = (char *)c->clov_master;
+    c->clov_valid[BQ_PREC_DOUBLE] = 1;
+    c->clov_valid[BQ_PREC_SINGLE] = c->clov_valid[BQ_PREC_HALF] = 0;
+    return BQ_OK;
+}
+
+int bq_prepare_clover(bq_ctx *c, int prec) {
+    if (!c->clov_master_valid) BQ_TRY(bq_build_clover(c));
+    if (c->clov_valid[prec]) return BQ_OK;
+    BQ_TRY(bq_alloc((void **)&c->clov[prec], clover_bytes_per_site(prec) * (size_t)c->Vh * 4));
+    unsigned grid = grid_for(4LL * c->Vh, 128);
+    if (prec == BQ_PREC_SINGLE)
+        k_convert_clover<BQ_PREC_SINGLE><<<grid, 128, 0, c->stream>>>(c->clov[prec], (const double2 *)c->clov_master, c->Vh, 4);
+    else
+        k_convert_clover<BQ_PREC_HALF><<<grid, 128, 0, c->stream>>>(c->clov[prec], (const double2 *)c->clov_master, c->Vh, 4);
+    BQ_LAUNCH_CHECK();
+    c->clov_valid[prec] = 1;
+    return BQ_OK;
+}
+
+// --------------------------------------------------------------------------
+// spinor pack / unpack
+
+template <int PREC>
+__global__ void k_pack_spinor(void *dst, const double2 *src, int Vh) {
+    using T = typename Traits<PREC>::real;
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= Vh) return;
+    cplx<T> s[12];
+    for (int k = 0; k < 12; k++) {
+        double2 v = src[(size_t)h * 12 + k];
+        s[k] = {(T)v.x, (T)v.y};
+    }
+    SpinorIO<PREC>::store(dst, h, Vh, s);
+}
+
+template <int PREC>
+__global__ void k_unpack_spinor(double2 *dst, const void *src, int Vh) {
+    using T = typename Traits<PREC>::real;
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= Vh) return;
+    cplx<T> s[12];
+    SpinorIO<PREC>::load(s, src, h, Vh);
+    for (int k = 0; k < 12; k++) dst[(size_t)h * 12 + k] = make_double2((double)s[k].re, (double)s[k].im);
+}
+
+int bq_pack(bq_ctx *c, void *native, const double *canon_dev, int prec) {
+    unsigned grid = grid_for(c->Vh, 128);
+    const double2 *src = (const double2 *)canon_dev;
+    if (prec == BQ_PREC_DOUBLE) k_pack_spinor<BQ_PREC_DOUBLE><<<grid, 128, 0, c->stream>>>(native, src, c->Vh);
+    else if (prec == BQ_PREC_SINGLE) k_pack_spinor<BQ_PREC_SINGLE><<<grid, 128, 0, c->stream>>>(native, src, c->Vh);
+    else k_pack_spinor<BQ_PREC_HALF><<<grid, 128, 0, c->stream>>>(native, src, c->Vh);
+    BQ_LAUNCH_CHECK();
+    return BQ_OK;
+}
+
+int bq_unpack(bq_ctx *c, double *canon_dev, const void *native, int prec) {
+    unsigned grid = grid_for(c->Vh, 128);
+    double2 *dst = (double2 *)canon_dev;
+    if (prec == BQ_PREC_DOUBLE) k_unpack_spinor<BQ_PREC_DOUBLE><<<grid, 128, 0, c->stream>>>(dst, native, c->Vh);
+    else if (prec == BQ_PREC_SINGLE) k_unpack_spinor<BQ_PREC_SINGLE><<<grid, 128, 0, c->stream>>>(dst, native, c->Vh);
+    else k_unpack_spinor<BQ_PREC_HALF><<<grid, 128, 0, c->stream>>>(dst, native, c->Vh);
+    BQ_LAUNCH_CHECK();
+    return BQ_OK;
+}
+
+extern "C" size_t bq_spinor_bytes(const bq_ctx *c, int prec) {
+    if (!c || !valid_prec(prec)) return 0;
+    return spinor_bytes_per_site(prec) * (size_t)c->Vh;
+}
+
+extern "C" int bq_spinor_pack(bq_ctx *c, void *native, const double *canon, int prec, int where) {
+    if (!c || !native || !canon || !valid_prec(prec) || !(where == BQ_HOST || where == BQ_DEVICE)) {
+        bq_set_error("bq_spinor_pack: bad arguments");
+        return BQ_ERR_ARG;
+    }
+    const double *src = canon;
+    if (where == BQ_HOST) {
+        BQ_TRY(bq_alloc((void **)&c->canon_stage, (size_t)c->Vh * 192));
+        BQ_CUDA_TRY(cudaMemcpyAsync(c->canon_stage, canon, (size_t)c->Vh * 192, cudaMemcpyHostToDevice, c->stream));
+        src = c->canon_stage;
+    }
+    return bq_pack(c, native, src, prec);
+}
+
+extern "C" int bq_spinor_unpack(bq_ctx *c, double *canon, const void *native, int prec, int where) {
+    if (!c || !native || !canon || !valid_prec(prec) || !(where == BQ_HOST || where == BQ_DEVICE)) {
+        bq_set_error("bq_spinor_unpack: bad arguments");
+        return BQ_ERR_ARG;
+    }
+    if (where == BQ_DEVICE) return bq_unpack(c, canon, native, prec);
+    BQ_TRY(bq_alloc((void **)&c->canon_stage, (size_t)c->Vh * 192));
+    BQ_TRY(bq_unpack(c, c->canon_stage, native, prec));
+    BQ_CUDA_TRY(cudaMemcpyAsync(canon, c->canon_stage, (size_t)c->Vh * 192, cudaMemcpyDeviceToHost, c->stream));
+    BQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return BQ_OK;
+}

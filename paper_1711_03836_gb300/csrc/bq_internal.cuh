@@ -1,0 +1,494 @@
+// bq_internal.cuh -- shared device types, storage policies and the context of
+// the GB300 even-odd clover-Wilson library.
+//
+// Native layouts (structure of arrays, site index innermost, so that the 32
+// threads of a warp, one output site each, read consecutive addresses):
+//
+//   spinor FP64 : double2 [12][Vh]                 (component c = spin*3+colour)
+//   spinor FP32 : float4  [6][Vh]                  (components 2k, 2k+1)
+//   spinor HALF : uint4   [3][Vh] of 8 fp16 each,  then float [Vh] per-site scale
+//   links       : per (parity, mu) block, [chunks][Vh] (see LinkIO), U(1) phase folded in
+//   clover      : per (parity, inverse) block, 72 reals per site = two packed
+//                 Hermitian 6x6 blocks (6 real diagonal + 15 complex upper
+//                 entries, row-major), stored as double2 [36][Vh], float4 [18][Vh]
+//                 or uint2 [18][Vh] of fp16
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/bqcd.h"
+
+// --------------------------------------------------------------------------
+// error reporting (thread-local message, status codes; nothing aborts)
+
+void bq_set_error(const char *fmt, ...);
+
+#define BQ_CUDA_TRY(call)                                                              \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            bq_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+            return BQ_ERR_CUDA;                                                        \
+        }                                                                              \
+    } while (0)
+
+#define BQ_TRY(call)              \
+    do {                          \
+        int s_ = (call);          \
+        if (s_ != BQ_OK) return s_; \
+    } while (0)
+
+#define BQ_LAUNCH_CHECK() BQ_CUDA_TRY(cudaGetLastError())
+
+// --------------------------------------------------------------------------
+// complex arithmetic
+
+template <typename T>
+struct cplx {
+    T re, im;
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> cmk(T r, T i) { return cplx<T>{r, i}; }
+template <typename T>
+__device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T>
+__device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// conj(a) * b
+template <typename T>
+__device__ __forceinline__ cplx<T> cmulc(cplx<T> a, cplx<T> b) {
+    return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cconj(cplx<T> a) { return {a.re, -a.im}; }
+template <typename T>
+__device__ __forceinline__ cplx<T> cscale(T s, cplx<T> a) { return {s * a.re, s * a.im}; }
+// c + a*b
+template <typename T>
+__device__ __forceinline__ cplx<T> cfma(cplx<T> a, cplx<T> b, cplx<T> c) {
+    c.re = fma(a.re, b.re, c.re);
+    c.re = fma(-a.im, b.im, c.re);
+    c.im = fma(a.re, b.im, c.im);
+    c.im = fma(a.im, b.re, c.im);
+    return c;
+}
+// c + conj(a)*b
+template <typename T>
+__device__ __forceinline__ cplx<T> cfmac(cplx<T> a, cplx<T> b, cplx<T> c) {
+    c.re = fma(a.re, b.re, c.re);
+    c.re = fma(a.im, b.im, c.re);
+    c.im = fma(a.re, b.im, c.im);
+    c.im = fma(-a.im, b.re, c.im);
+    return c;
+}
+// i*s*a for s = +1 / -1
+template <int S, typename T>
+__device__ __forceinline__ cplx<T> cimul(cplx<T> a) {
+    return (S > 0) ? cplx<T>{-a.im, a.re} : cplx<T>{a.im, -a.re};
+}
+
+// --------------------------------------------------------------------------
+// precision traits
+
+template <int PREC>
+struct Traits;
+template <>
+struct Traits<BQ_PREC_DOUBLE> {
+    using real = double;
+    static constexpr size_t spinor_bytes = 192;
+};
+template <>
+struct Traits<BQ_PREC_SINGLE> {
+    using real = float;
+    static constexpr size_t spinor_bytes = 96;
+};
+template <>
+struct Traits<BQ_PREC_HALF> {
+    using real = float;
+    static constexpr size_t spinor_bytes = 52;  // 48 B of fp16 + 4 B scale
+};
+
+__host__ __device__ inline size_t spinor_bytes_per_site(int prec) {
+    return prec == BQ_PREC_DOUBLE ? 192 : prec == BQ_PREC_SINGLE ? 96 : 52;
+}
+__host__ __device__ inline size_t link_bytes_per_link(int prec, int recon) {
+    size_t reals = (recon == BQ_RECON_12) ? 12 : 18;
+    return reals * (prec == BQ_PREC_DOUBLE ? 8 : prec == BQ_PREC_SINGLE ? 4 : 2);
+}
+__host__ __device__ inline size_t clover_bytes_per_site(int prec) {
+    return 72 * (prec == BQ_PREC_DOUBLE ? 8 : prec == BQ_PREC_SINGLE ? 4 : 2);
+}
+
+// --------------------------------------------------------------------------
+// read-only / streaming loads
+
+template <typename V>
+__device__ __forceinline__ V ldg(const V *p) { return __ldg(p); }
+
+__device__ __forceinline__ float2 h2f(uint32_t u) {
+    __half2 h = *reinterpret_cast<__half2 *>(&u);
+    return __half22float2(h);
+}
+__device__ __forceinline__ uint32_t f2h(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// --------------------------------------------------------------------------
+// spinor I/O: 12 complex per site
+
+template <int PREC>
+struct SpinorIO;
+
+template <>
+struct SpinorIO<BQ_PREC_DOUBLE> {
+    using T = double;
+    __device__ static __forceinline__ void load(cplx<T> s[12], const void *base, int h, int Vh) {
+        const double2 *p = static_cast<const double2 *>(base);
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            double2 v = ldg(p + (size_t)c * Vh + h);
+            s[c] = {v.x, v.y};
+        }
+    }
+    __device__ static __forceinline__ void store(void *base, int h, int Vh, const cplx<T> s[12]) {
+        double2 *p = static_cast<double2 *>(base);
+#pragma unroll
+        for (int c = 0; c < 12; c++) p[(size_t)c * Vh + h] = make_double2(s[c].re, s[c].im);
+    }
+};
+
+template <>
+struct SpinorIO<BQ_PREC_SINGLE> {
+    using T = float;
+    __device__ static __forceinline__ void load(cplx<T> s[12], const void *base, int h, int Vh) {
+        const float4 *p = static_cast<const float4 *>(base);
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            float4 v = ldg(p + (size_t)k * Vh + h);
+            s[2 * k] = {v.x, v.y};
+            s[2 * k + 1] = {v.z, v.w};
+        }
+    }
+    __device__ static __forceinline__ void store(void *base, int h, int Vh, const cplx<T> s[12]) {
+        float4 *p = static_cast<float4 *>(base);
+#pragma unroll
+        for (int k = 0; k < 6; k++)
+            p[(size_t)k * Vh + h] = make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
+    }
+};
+
+template <>
+struct SpinorIO<BQ_PREC_HALF> {
+    using T = float;
+    __device__ static __forceinline__ void load(cplx<T> s[12], const void *base, int h, int Vh) {
+        const uint4 *p = static_cast<const uint4 *>(base);
+        const float *nrm = reinterpret_cast<const float *>(p + (size_t)3 * Vh);
+        float n = ldg(nrm + h);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            uint4 v = ldg(p + (size_t)k * Vh + h);
+            float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
+            s[4 * k + 0] = {a.x * n, a.y * n};
+            s[4 * k + 1] = {b.x * n, b.y * n};
+            s[4 * k + 2] = {c.x * n, c.y * n};
+            s[4 * k + 3] = {d.x * n, d.y * n};
+        }
+    }
+    __device__ static __forceinline__ void store(void *base, int h, int Vh, const cplx<T> s[12]) {
+        uint4 *p = static_cast<uint4 *>(base);
+        float *nrm = reinterpret_cast<float *>(p + (size_t)3 * Vh);
+        float m = 0.f;
+#pragma unroll
+        for (int c = 0; c < 12; c++) m = fmaxf(m, fmaxf(fabsf(s[c].re), fabsf(s[c].im)));
+        float inv = (m > 0.f) ? 1.0f / m : 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            uint4 v;
+            v.x = f2h(s[4 * k + 0].re * inv, s[4 * k + 0].im * inv);
+            v.y = f2h(s[4 * k + 1].re * inv, s[4 * k + 1].im * inv);
+            v.z = f2h(s[4 * k + 2].re * inv, s[4 * k + 2].im * inv);
+            v.w = f2h(s[4 * k + 3].re * inv, s[4 * k + 3].im * inv);
+            p[(size_t)k * Vh + h] = v;
+        }
+        nrm[h] = m;
+    }
+};
+
+// --------------------------------------------------------------------------
+// link I/O: 3x3 complex, row-major; RECON 12 stores rows 0 and 1 only
+
+template <typename T>
+__device__ __forceinline__ void reconstruct_row2(cplx<T> U[9]) {
+    // row 2 = conj(row0 x row1), exact for SU(3)
+    U[6] = cconj(csub(cmul(U[1], U[5]), cmul(U[2], U[4])));
+    U[7] = cconj(csub(cmul(U[2], U[3]), cmul(U[0], U[5])));
+    U[8] = cconj(csub(cmul(U[0], U[4]), cmul(U[1], U[3])));
+}
+
+template <int PREC, int RECON>
+struct LinkIO;
+
+template <int RECON>
+struct LinkIO<BQ_PREC_DOUBLE, RECON> {
+    using T = double;
+    static constexpr int NC = (RECON == 12) ? 6 : 9;
+    __device__ static __forceinline__ void load(cplx<T> U[9], const char *blk, int h, int Vh) {
+        const double2 *p = reinterpret_cast<const double2 *>(blk);
+#pragma unroll
+        for (int c = 0; c < NC; c++) {
+            double2 v = ldg(p + (size_t)c * Vh + h);
+            U[c] = {v.x, v.y};
+        }
+        if (RECON == 12) reconstruct_row2(U);
+    }
+    __device__ static __forceinline__ void store(char *blk, int h, int Vh, const double2 U[9]) {
+        double2 *p = reinterpret_cast<double2 *>(blk);
+#pragma unroll
+        for (int c = 0; c < NC; c++) p[(size_t)c * Vh + h] = U[c];
+    }
+};
+
+template <int RECON>
+struct LinkIO<BQ_PREC_SINGLE, RECON> {
+    using T = float;
+    static constexpr int NF4 = (RECON == 12) ? 3 : 4;  // float4 chunks (2 complex each)
+    __device__ static __forceinline__ void load(cplx<T> U[9], const char *blk, int h, int Vh) {
+        const float4 *p = reinterpret_cast<const float4 *>(blk);
+#pragma unroll
+        for (int k = 0; k < NF4; k++) {
+            float4 v = ldg(p + (size_t)k * Vh + h);
+            U[2 * k] = {v.x, v.y};
+            U[2 * k + 1] = {v.z, v.w};
+        }
+        if (RECON == 12) {
+            reconstruct_row2(U);
+        } else {
+            const float2 *t = reinterpret_cast<const float2 *>(p + (size_t)4 * Vh);
+            float2 v = ldg(t + h);
+            U[8] = {v.x, v.y};
+        }
+    }
+    __device__ static __forceinline__ void store(char *blk, int h, int Vh, const double2 U[9]) {
+        float4 *p = reinterpret_cast<float4 *>(blk);
+#pragma unroll
+        for (int k = 0; k < NF4; k++)
+            p[(size_t)k * Vh + h] = make_float4((float)U[2 * k].x, (float)U[2 * k].y, (float)U[2 * k + 1].x,
+                                                (float)U[2 * k + 1].y);
+        if (RECON != 12) {
+            float2 *t = reinterpret_cast<float2 *>(p + (size_t)4 * Vh);
+            t[h] = make_float2((float)U[8].x, (float)U[8].y);
+        }
+    }
+};
+
+template <int RECON>
+struct LinkIO<BQ_PREC_HALF, RECON> {
+    using T = float;
+    static constexpr int NU2 = (RECON == 12) ? 3 : 4;  // uint2 chunks (2 complex each)
+    __device__ static __forceinline__ void load(cplx<T> U[9], const char *blk, int h, int Vh) {
+        const uint2 *p = reinterpret_cast<const uint2 *>(blk);
+#pragma unroll
+        for (int k = 0; k < NU2; k++) {
+            uint2 v = ldg(p + (size_t)k * Vh + h);
+            float2 a = h2f(v.x), b = h2f(v.y);
+            U[2 * k] = {a.x, a.y};
+            U[2 * k + 1] = {b.x, b.y};
+        }
+        if (RECON == 12) {
+            reconstruct_row2(U);
+        } else {
+            const uint32_t *t = reinterpret_cast<const uint32_t *>(p + (size_t)4 * Vh);
+            float2 a = h2f(ldg(t + h));
+            U[8] = {a.x, a.y};
+        }
+    }
+    __device__ static __forceinline__ void store(char *blk, int h, int Vh, const double2 U[9]) {
+        uint2 *p = reinterpret_cast<uint2 *>(blk);
+#pragma unroll
+        for (int k = 0; k < NU2; k++) {
+            uint2 v;
+            v.x = f2h((float)U[2 * k].x, (float)U[2 * k].y);
+            v.y = f2h((float)U[2 * k + 1].x, (float)U[2 * k + 1].y);
+            p[(size_t)k * Vh + h] = v;
+        }
+        if (RECON != 12) {
+            uint32_t *t = reinterpret_cast<uint32_t *>(p + (size_t)4 * Vh);
+            t[h] = f2h((float)U[8].x, (float)U[8].y);
+        }
+    }
+};
+
+// --------------------------------------------------------------------------
+// clover I/O: 72 reals per site, R[0..35] block 0 (spins 0,1), R[36..71] block 1
+
+template <int PREC>
+struct CloverIO;
+
+template <>
+struct CloverIO<BQ_PREC_DOUBLE> {
+    using T = double;
+    // block b: 6 diagonal reals, 15 complex upper-triangle entries
+    __device__ static __forceinline__ void load_block(T d[6], cplx<T> o[15], const void *base, int b, int h,
+                                                      int Vh) {
+        const double2 *p = static_cast<const double2 *>(base) + (size_t)(18 * b) * Vh + h;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            double2 v = ldg(p + (size_t)k * Vh);
+            d[2 * k] = v.x;
+            d[2 * k + 1] = v.y;
+        }
+#pragma unroll
+        for (int k = 0; k < 15; k++) {
+            double2 v = ldg(p + (size_t)(3 + k) * Vh);
+            o[k] = {v.x, v.y};
+        }
+    }
+};
+
+template <>
+struct CloverIO<BQ_PREC_SINGLE> {
+    using T = float;
+    __device__ static __forceinline__ void load_block(T d[6], cplx<T> o[15], const void *base, int b, int h,
+                                                      int Vh) {
+        const float4 *p = static_cast<const float4 *>(base) + (size_t)(9 * b) * Vh + h;
+        float r[36];
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            float4 v = ldg(p + (size_t)k * Vh);
+            r[4 * k] = v.x;
+            r[4 * k + 1] = v.y;
+            r[4 * k + 2] = v.z;
+            r[4 * k + 3] = v.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 6; k++) d[k] = r[k];
+#pragma unroll
+        for (int k = 0; k < 15; k++) o[k] = {r[6 + 2 * k], r[7 + 2 * k]};
+    }
+};
+
+template <>
+struct CloverIO<BQ_PREC_HALF> {
+    using T = float;
+    // 36 fp16 per block = 9 uint2; the block pair is stored as uint2 [18][Vh]
+    __device__ static __forceinline__ void load_block(T d[6], cplx<T> o[15], const void *base, int b, int h,
+                                                      int Vh) {
+        const uint2 *p = static_cast<const uint2 *>(base) + (size_t)(9 * b) * Vh + h;
+        float r[36];
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            uint2 v = ldg(p + (size_t)k * Vh);
+            float2 a = h2f(v.x), c = h2f(v.y);
+            r[4 * k] = a.x;
+            r[4 * k + 1] = a.y;
+            r[4 * k + 2] = c.x;
+            r[4 * k + 3] = c.y;
+        }
+#pragma unroll
+        for (int k = 0; k < 6; k++) d[k] = r[k];
+#pragma unroll
+        for (int k = 0; k < 15; k++) o[k] = {r[6 + 2 * k], r[7 + 2 * k]};
+    }
+};
+
+// y = B x for one packed Hermitian 6x6 block
+template <typename T>
+__device__ __forceinline__ void herm6_apply(const T d[6], const cplx<T> o[15], const cplx<T> x[6], cplx<T> y[6]) {
+#pragma unroll
+    for (int i = 0; i < 6; i++) y[i] = cscale(d[i], x[i]);
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+#pragma unroll
+        for (int j = i + 1; j < 6; j++) {
+            y[i] = cfma(o[k], x[j], y[i]);   // B[i][j] x[j]
+            y[j] = cfmac(o[k], x[i], y[j]);  // B[j][i] = conj(B[i][j])
+            k++;
+        }
+    }
+}
+
+template <int PREC, typename T>
+__device__ __forceinline__ void clover_apply_site(cplx<T> out[12], const cplx<T> in[12], const void *clov, int h,
+                                                  int Vh) {
+#pragma unroll
+    for (int b = 0; b < 2; b++) {
+        T d[6];
+        cplx<T> o[15];
+        CloverIO<PREC>::load_block(d, o, clov, b, h, Vh);
+        herm6_apply(d, o, in + 6 * b, out + 6 * b);
+    }
+}
+
+// --------------------------------------------------------------------------
+// context
+
+enum { BQ_NPREC = 3 };
+
+struct SolverWork;  // defined in the solver translation unit
+
+struct bq_ctx {
+    int L[4];
+    int Vh;
+    long long V;
+    int device;
+    cudaStream_t stream;
+    bq_params params;
+    int recon[BQ_NPREC];
+
+    // master fields (FP64, device)
+    double2 *U_canon;  // [V][4][9]
+    double *A_u1;      // [V][4] or null
+    int have_gauge;
+
+    // derived native fields, rebuilt lazily
+    char *links[BQ_NPREC];
+    int links_recon[BQ_NPREC];
+    int links_valid[BQ_NPREC];
+    double *clov_master;           // FP64 packed, [parity][inverse] blocks of 72*Vh reals
+    int clov_master_valid;
+    char *clov[BQ_NPREC];          // [parity][inverse] blocks at each precision
+    int clov_valid[BQ_NPREC];
+
+    // scratch
+    char *tmp_odd[BQ_NPREC];
+    char *tmp_even[BQ_NPREC];
+    double *canon_stage;           // [Vh][12] complex staging for pack/unpack of host data
+    double *red_partials;          // block partial sums of reductions
+    unsigned int *red_ticket;      // last-block ticket
+    int *dev_flag;                 // device error flag (singular clover etc.)
+    SolverWork *solver;
+};
+
+// field preparation (bq_fields.cu)
+int bq_prepare_links(bq_ctx *c, int prec);
+int bq_prepare_clover(bq_ctx *c, int prec);
+int bq_alloc(void **p, size_t bytes);
+int bq_pack(bq_ctx *c, void *native, const double *canon_dev, int prec);
+int bq_unpack(bq_ctx *c, double *canon_dev, const void *native, int prec);
+
+// clover block pointer for (parity, inverse) at precision prec
+inline const char *clover_ptr(const bq_ctx *c, int prec, int parity, int inverse) {
+    return c->clov[prec] + (size_t)(parity * 2 + inverse) * clover_bytes_per_site(prec) * c->Vh;
+}
+inline const char *links_ptr(const bq_ctx *c, int prec) { return c->links[prec]; }
+inline size_t links_block_bytes(const bq_ctx *c, int prec) {
+    return link_bytes_per_link(prec, c->links_recon[prec]) * (size_t)c->Vh;
+}
+
+// operator launches (bq_dslash.cu)
+enum { EPI_PLAIN = 0, EPI_CLOVINV = 1, EPI_XPAY = 2 };
+int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_parity, int dagger, int epi,
+                     const void *xin, double k);
+int bq_clover_launch(bq_ctx *c, int prec, void *out, const void *in, int parity, int inverse);
+int bq_mhat_launch(bq_ctx *c, int prec, void *out, const void *in, int dagger, void *tmp_odd);
+int bq_mdagm_launch(bq_ctx *c, int prec, void *out, const void *in, void *tmp_odd, void *tmp_even);
+int bq_workspace(bq_ctx *c, int prec);

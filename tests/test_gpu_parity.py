@@ -1,0 +1,216 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative 2-norm error per apply against the FP64 oracle):
+FP64 1e-13, FP32 1e-6, FP16 storage with per-site scale 5e-3.
+Small lattices are compared element by element on every site; they span
+several 128-thread blocks and leave a ragged tail (V/2 = 720).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_03836_gb300 import synth
+
+TOL = {"double": 1e-13, "single": 1e-6, "half": 5e-3}
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bq():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1711_03836_gb300 import bqcd
+
+    return bqcd
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+def make(bq, dims, kappa=0.1355, csw=1.9, mu=0.0, charge=0.0, eps=0.2, seed=1, recon=18, precision="double"):
+    U = synth.gauge_field(dims, eps, seed)
+    A = synth.u1_field(dims, 0.1, seed + 5) if charge else None
+    lat = bq.Lattice(dims, kappa, csw, mu, -1.0, charge)
+    bq.bq_set_gauge(lat.ctx, U)
+    if A is not None:
+        bq.bq_set_u1(lat.ctx, A)
+    bq.bq_set_recon(lat.ctx, precision, recon)
+    p = oracle.params(dims, kappa=kappa, csw=csw, mu=mu, t_bc=-1.0, charge=charge)
+    return lat, U, A, p
+
+
+CASES = [
+    # (precision, recon, mu, charge)
+    ("double", 18, 0.0, 0.0),
+    ("double", 12, 0.1, 0.0),
+    ("double", 18, 0.1, 2.0 / 3.0),
+    ("single", 18, 0.0, -1.0 / 3.0),
+    ("single", 12, 0.1, 0.0),
+    ("half", 12, 0.0, 0.0),
+    ("half", 18, 0.1, 2.0 / 3.0),
+]
+
+
+@pytest.mark.parametrize("prec,recon,mu,charge", CASES)
+@pytest.mark.parametrize("dims", [(6, 4, 6, 10), (8, 8, 8, 8)])
+def test_dhop_parity(bq, dims, prec, recon, mu, charge):
+    lat, U, A, p = make(bq, dims, mu=mu, charge=charge, recon=recon, precision=prec)
+    psi = synth.gaussian_spinor(lat.Vh, 3)
+    src = lat.pack(psi, prec)
+    out = lat.spinor(prec)
+    for par in (0, 1):
+        for dag in (False, True):
+            bq.bq_apply_dhop(lat.ctx, out, src, par, dag, prec)
+            got = lat.unpack(out, prec)
+            ref = oracle.dhop(p, U, A, psi, par, dag)
+            assert rel(got, ref) < TOL[prec], (par, dag)
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", ["double", "single", "half"])
+def test_clover_parity(bq, prec):
+    dims = (6, 4, 6, 10)
+    lat, U, A, p = make(bq, dims)
+    psi = synth.gaussian_spinor(lat.Vh, 4)
+    src = lat.pack(psi, prec)
+    out = lat.spinor(prec)
+    for par in (0, 1):
+        Am = oracle.clover_field(p, U, par)
+        for inv in (False, True):
+            bq.bq_apply_clover(lat.ctx, out, src, par, inv, prec)
+            ref = oracle.clover_apply(oracle.clover_invert(Am) if inv else Am, psi)
+            assert rel(lat.unpack(out, prec), ref) < TOL[prec], (par, inv)
+    lat.close()
+
+
+@pytest.mark.parametrize("prec,recon,mu,charge", CASES)
+def test_mhat_parity(bq, prec, recon, mu, charge):
+    dims = (6, 4, 6, 10)
+    lat, U, A, p = make(bq, dims, mu=mu, charge=charge, recon=recon, precision=prec)
+    op = oracle.Operator(p, U, A)
+    psi = synth.gaussian_spinor(lat.Vh, 5)
+    src = lat.pack(psi, prec)
+    out = lat.spinor(prec)
+    for dag in (False, True):
+        bq.bq_apply_mhat(lat.ctx, out, src, dag, prec)
+        assert rel(lat.unpack(out, prec), op.mhat(psi, dag)) < TOL[prec], dag
+    bq.bq_apply_mdagm(lat.ctx, out, src, prec)
+    assert rel(lat.unpack(out, prec), op.mdagm(psi)) < TOL[prec]
+    lat.close()
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 4, 2, 6), (4, 2, 6, 2)])
+def test_tiny_and_degenerate_extents(bq, dims):
+    """Extent-2 directions: the forward and backward neighbour coincide."""
+    lat, U, A, p = make(bq, dims, mu=0.1, charge=2.0 / 3.0, eps=0.5)
+    op = oracle.Operator(p, U, A)
+    psi = synth.gaussian_spinor(lat.Vh, 6)
+    out = lat.spinor("double")
+    bq.bq_apply_mhat(lat.ctx, out, lat.pack(psi), 0, "double")
+    assert rel(lat.unpack(out), op.mhat(psi)) < 1e-13
+    lat.close()
+
+
+def test_zero_and_point_sources(bq):
+    dims = (4, 4, 4, 4)
+    lat, U, A, p = make(bq, dims, precision="half", recon=12)
+    op = oracle.Operator(p, U, A)
+    for prec in ("double", "single", "half"):
+        out = lat.spinor(prec)
+        z = np.zeros((lat.Vh, 4, 3), np.complex128)
+        bq.bq_apply_mhat(lat.ctx, out, lat.pack(z, prec), 0, prec)
+        assert np.all(lat.unpack(out, prec) == 0)
+        b = synth.point_source(lat.Vh, 0, 2, 1)
+        bq.bq_apply_mhat(lat.ctx, out, lat.pack(b, prec), 0, prec)
+        assert rel(lat.unpack(out, prec), op.mhat(b)) < TOL[prec]
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", ["double", "single", "half"])
+def test_cg_config1(bq, prec):
+    """8^4, eps 0.3, kappa 0.125, c_SW 1.0, antiperiodic t: true FP64 residual <= 1e-10."""
+    dims = (8, 8, 8, 8)
+    lat, U, A, p = make(bq, dims, kappa=0.125, csw=1.0, eps=0.3, seed=1, recon=12 if prec != "double" else 18,
+                        precision=prec)
+    op = oracle.Operator(p, U)
+    b = synth.gaussian_spinor(lat.Vh, 1001)
+    x = np.empty_like(b)
+    st = bq.bq_solve_cg(lat.ctx, x, b, tol=1e-10, precision=prec, delta=1e-3 if prec == "single" else 1e-1)
+    assert st["converged"] == 1
+    res = np.linalg.norm(op.mdagm(x) - b) / np.linalg.norm(b)
+    assert res <= 1e-10, res
+    assert abs(st["true_residual"] - res) < 1e-11
+    xo, _ = op.cg(b, tol=1e-12)
+    assert rel(x, xo) < 1e-8
+    lat.close()
+
+
+def test_cg_shift_and_device_buffers(bq):
+    import torch
+
+    dims = (6, 4, 6, 10)
+    lat, U, A, p = make(bq, dims, kappa=0.13, csw=1.7, mu=0.0)
+    op = oracle.Operator(p, U)
+    b = synth.gaussian_spinor(lat.Vh, 77)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.empty_like(bd)
+    st = bq.bq_solve_cg(lat.ctx, xd, bd, tol=1e-10, precision="single", shift=0.05)
+    x = xd.cpu().numpy()
+    res = np.linalg.norm(op.mdagm(x, 0.05) - b) / np.linalg.norm(b)
+    assert res <= 1e-10 and st["converged"]
+    lat.close()
+
+
+def test_error_codes(bq):
+    with pytest.raises(bq.BqError) as e:
+        bq.bq_create((4, 4, 5, 4))
+    assert e.value.status == bq.BQ_ERR_ARG
+    lat = bq.Lattice((4, 4, 4, 4), 0.12)
+    out, inp = lat.spinor(), lat.spinor()
+    with pytest.raises(bq.BqError) as e:
+        bq.bq_apply_mhat(lat.ctx, out, inp, 0, "double")
+    assert e.value.status == bq.BQ_ERR_STATE
+    bq.bq_set_gauge(lat.ctx, synth.gauge_field((4, 4, 4, 4), 0.2, 3))
+    bq.bq_set_u1(lat.ctx, synth.u1_field((4, 4, 4, 4), 0.1, 4))
+    with pytest.raises(bq.BqError) as e:
+        bq.bq_set_recon(lat.ctx, "single", 12)
+    assert e.value.status == bq.BQ_ERR_ARG
+    with pytest.raises(bq.BqError) as e:
+        bq.bq_apply_mhat(lat.ctx, out, out, 0, "double")
+    assert e.value.status == bq.BQ_ERR_ARG
+    b = synth.gaussian_spinor(lat.Vh, 1)
+    x = np.empty_like(b)
+    with pytest.raises(bq.BqError) as e:
+        bq.bq_solve_cg(lat.ctx, x, b, tol=1e-10, max_iter=2)
+    assert e.value.status == bq.BQ_ERR_NOT_CONVERGED
+    lat.close()
+
+
+@pytest.mark.parametrize("cfg", ["16^3x32 mu=0.1", "32^3x64"])
+def test_full_size_sampled(bq, cfg):
+    """Full-size lattices: the GPU applies Mhat on every site, the oracle
+    recomputes 48 sampled even sites one by one."""
+    if cfg.startswith("16"):
+        dims, eps, kappa, csw, mu = (16, 16, 16, 32), 0.2, 0.1350, 1.7, 0.1
+    else:
+        dims, eps, kappa, csw, mu = (32, 32, 32, 64), 0.15, 0.1355, 1.9, 0.0
+    U = synth.gauge_field(dims, eps, 1)
+    lat = bq.Lattice(dims, kappa, csw, mu, -1.0)
+    bq.bq_set_gauge(lat.ctx, U)
+    bq.bq_set_recon(lat.ctx, "single", 12)
+    bq.bq_set_recon(lat.ctx, "half", 12)
+    p = oracle.params(dims, kappa=kappa, csw=csw, mu=mu, t_bc=-1.0)
+    psi = synth.gaussian_spinor(lat.Vh, 9)
+    rng = np.random.default_rng(0)
+    sites = np.unique(np.concatenate([[0, lat.Vh - 1], rng.integers(0, lat.Vh, 46)]))
+    for dag in (False, True):
+        ref = oracle.mhat_sites(p, U, None, psi, sites, dag)
+        for prec in ("double", "single", "half"):
+            out = lat.spinor(prec)
+            bq.bq_apply_mhat(lat.ctx, out, lat.pack(psi, prec), dag, prec)
+            got = lat.unpack(out, prec)[sites]
+            assert rel(got, ref) < TOL[prec], (prec, dag)
+    lat.close()
