@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark of the even-odd clover-Wilson hot path on GB300.
+
+One step = one reliable-update mixed-precision CG solve of
+(Mhat^dag Mhat) x = b to a TRUE FP64 residual <= 1e-10 |b| on a 32^3x64
+lattice (kappa 0.1355, c_SW 1.9, links exp(i 0.15 A) reunitarised, antiperiodic
+t), with the inner Krylov iteration in FP32 (12-real links) and FP64 residual
+recomputation: every row of the hot path (hopping term, clover and inverse
+epilogues, Mhat, Mhat^dag Mhat, BLAS-1 and reductions, FP64 CG outer updates)
+runs inside it.
+
+value = algorithmic hopping-term bytes of all launches in the timed solves
+(8 links + in + out spinor per site, plus the clover blocks / x spinor the
+fused epilogues read) / the timed wall time on the device, in GB/s. The line
+also carries the plain FP64 CG time on the same system (the mixed/FP64
+speed-up), a Dslash bandwidth sweep per precision, the roofline of the
+dominant kernel, the CPU oracle baseline and the end-to-end figure through
+the C ABI with host buffers.
+
+--impl reference times the FP64 CPU oracle (the only reference there is: the
+paper ships no code) on the same lattice, one Mhat^dag Mhat apply per step.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Dslash GB/s vs HBM peak; mixed/batched vs FP64 CG time to |r|/|b|<1e-10"
+
+WORKLOADS = {
+    "32^3x64": dict(dims=(32, 32, 32, 64), eps=0.15, kappa=0.1355, csw=1.9, mu=0.0, seed=1),
+    "24^3x48": dict(dims=(24, 24, 24, 48), eps=0.2, kappa=0.1350, csw=1.7, mu=0.0, seed=1),
+    "16^3x32": dict(dims=(16, 16, 16, 32), eps=0.2, kappa=0.1350, csw=1.7, mu=0.0, seed=1),
+    "8^4": dict(dims=(8, 8, 8, 8), eps=0.3, kappa=0.125, csw=1.0, mu=0.0, seed=1),
+}
+PREC_ID = {"double": 0, "single": 1, "half": 2}
+SPINOR_B = {0: 192, 1: 96, 2: 52}
+CLOVER_B = {0: 576, 1: 288, 2: 144}
+EPI_NAMES = ["dhop", "dhop_clovinv", "dhop_xpay"]
+
+
+def link_b(prec, recon):
+    return (12 if recon == 12 else 18) * {0: 8, 1: 4, 2: 2}[prec]
+
+
+def mdagm_bytes(prec, recon, Vh):
+    """Algorithmic bytes of one Mhat^dag Mhat: 2 D_oe+A^-1 and 2 A x - k D_eo launches."""
+    clovinv = 8 * link_b(prec, recon) + 2 * SPINOR_B[prec] + CLOVER_B[prec]
+    xpay = clovinv + SPINOR_B[prec]
+    return 2.0 * (clovinv + xpay) * Vh
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="32^3x64", choices=sorted(WORKLOADS))
+    ap.add_argument("--inner", default="single", choices=["single", "half"])
+    ap.add_argument("--delta", type=float, default=None)
+    ap.add_argument("--no-extras", action="store_true", help="skip FP64 CG, sweep, e2e and CPU baseline")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, device_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        self.idx = device_index
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={CLOCK_Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if device_index is not None:
+                cmd += ["-i", str(device_index)]
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ traffic from the committed ncu summary
+
+KERNEL_SOURCES = ("bq_dslash.cu", "bq_internal.cuh")  # the files that define k_dslash
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1711_03836_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel_tag, workload):
+    """bytes per launch from a 'bench-traffic:' line of profiles/*.md, if the kernels are unchanged."""
+    src = kernel_source_hash()
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        with open(path) as f:
+            for line in f:
+                if line.startswith("bench-traffic:"):
+                    parts = dict(kv.split("=", 1) for kv in line.split()[1:] if "=" in kv)
+                    if (parts.get("kernel") == kernel_tag and parts.get("workload") == workload
+                            and parts.get("src") == src):
+                        return float(parts["bytes_per_launch"])
+    return None
+
+
+# ------------------------------------------------------------------ reference arm: the FP64 CPU oracle
+
+def oracle_setup(wl):
+    import oracle
+    from paper_1711_03836_gb300 import synth
+
+    U = synth.gauge_field(wl["dims"], wl["eps"], wl["seed"])
+    p = oracle.params(wl["dims"], kappa=wl["kappa"], csw=wl["csw"], mu=wl["mu"], t_bc=-1.0)
+    op = oracle.Operator(p, U)
+    Vh = oracle.half_volume(p)
+    b = synth.gaussian_spinor(Vh, wl["seed"] + 1000)
+    return op, b, Vh
+
+
+def oracle_gbs(op, b, Vh, steps, warmup):
+    for _ in range(warmup):
+        op.mdagm(b)
+    ts = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        op.mdagm(b)
+        ts.append(time.perf_counter() - t0)
+    total = sum(ts)
+    return mdagm_bytes(0, 18, Vh) * steps / total / 1e9, total / steps
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    wl = WORKLOADS[args.workload]
+    op, b, Vh = oracle_setup(wl)
+    gbs, t_step = oracle_gbs(op, b, Vh, args.steps, max(args.warmup, 0))
+    cores = oracle.num_threads()
+    sample = f"one FP64 Mhat^dag Mhat apply per step on the full {args.workload} lattice (no solve)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args), "lattice": list(wl["dims"])},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_name(args):
+    wl = WORKLOADS[args.workload]
+    d = "x".join(str(x) for x in wl["dims"])
+    return (f"{args.workload} ({d}) even-odd clover-Wilson, kappa {wl['kappa']}, c_SW {wl['csw']}, "
+            f"links exp(i {wl['eps']} A) reunitarised, antiperiodic t; mixed-precision CG "
+            f"({args.inner} inner, 12-real links, FP64 reliable updates) to true residual 1e-10")
+
+
+# ------------------------------------------------------------------ our arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1711_03836_gb300 import bqcd, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = WORKLOADS[args.workload]
+    dims = wl["dims"]
+    U = synth.gauge_field(dims, wl["eps"], wl["seed"])
+    lat = bqcd.Lattice(dims, wl["kappa"], wl["csw"], wl["mu"], -1.0)
+    ctx = lat.ctx
+    bqcd.bq_set_gauge(ctx, U)
+    del U
+    bqcd.bq_set_recon(ctx, "single", 12)
+    bqcd.bq_set_recon(ctx, "half", 12)
+    bqcd.bq_build_clover(ctx)
+    Vh = lat.Vh
+    b = synth.gaussian_spinor(Vh, wl["seed"] + 1000 + rank)
+    b_dev = torch.from_numpy(b).cuda()
+    x_dev = torch.empty_like(b_dev)
+    delta = args.delta if args.delta is not None else (1e-3 if args.inner == "single" else 1e-1)
+    solve_kw = dict(tol=1e-10, precision=args.inner, delta=delta, check_every=8, max_iter=20000)
+
+    for _ in range(max(args.warmup, 0)):
+        bqcd.bq_solve_cg(ctx, x_dev, b_dev, **solve_kw)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K solves, inputs resident in HBM
+    sampler = ClockSampler(None if world == 1 else local)
+    barrier()
+    torch.cuda.synchronize()
+    bqcd.bq_reset_counters(ctx, timing=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    e0.record()
+    for _ in range(args.steps):
+        stats.append(bqcd.bq_solve_cg(ctx, x_dev, b_dev, **solve_kw))
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    cnt = bqcd.bq_get_counters(ctx)
+    total_bytes = sum(sum(r) for r in cnt["dslash_bytes"])
+    ms_max, bytes_all = ms, total_bytes
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        bt = torch.tensor([total_bytes], device="cuda", dtype=torch.float64)
+        dist.all_reduce(bt, op=dist.ReduceOp.SUM)
+        bytes_all = float(bt.item())
+    value = bytes_all / (ms_max * 1e-3) / 1e9
+
+    # dominant hopping-term kernel over the timed region (CUDA events around each launch)
+    best = max(((p, e) for p in range(3) for e in range(3)), key=lambda pe: cnt["dslash_ms"][pe[0]][pe[1]])
+    bp, be = best
+    n_l = cnt["dslash_launches"][bp][be]
+    per_launch_bytes = cnt["dslash_bytes"][bp][be] / max(n_l, 1)
+    per_launch_ms = cnt["dslash_ms"][bp][be] / max(n_l, 1)
+    peak, peak_kind = measured_peaks()
+    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+    tag = f"k_dslash<{['double', 'single', 'half'][bp]},{EPI_NAMES[be]}>"
+    traffic = committed_traffic(tag, args.workload)
+    all_ms = sum(sum(r) for r in cnt["dslash_ms"])
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": tag, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": per_launch_bytes, "launches": n_l,
+                "avg_launch_us": per_launch_ms * 1e3, "share_of_dslash_time": cnt["dslash_ms"][bp][be] / all_ms}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": f"{'f32' if args.inner == 'single' else 'f16-storage/f32'}+f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(args), "lattice": list(dims), "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (FP32 links 0.4 GB + clover 1.2 GB + FP64 links 1.2 GB)"},
+        "roofline": roofline,
+        "gpu_launches": cnt["launches"],
+        "clocks": clocks,
+        "solve": {"iterations": stats[-1]["iterations"], "reliable_updates": stats[-1]["reliable_updates"],
+                  "true_residual": stats[-1]["true_residual"], "converged": stats[-1]["converged"]},
+    }
+
+    if not args.no_extras and rank == 0:
+        line.update(extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, ms_max / args.steps, torch, bqcd))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, mixed_ms, torch, bqcd):
+    out = {}
+    Vh = lat.Vh
+    # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    b_host = torch.from_numpy(b).pin_memory()
+    x_host = torch.empty_like(b_host).pin_memory()
+    bqcd.bq_reset_counters(ctx, timing=False)
+    n_e2e = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        bqcd.bq_solve_cg(ctx, x_host, b_host, **solve_kw)
+    t1 = time.perf_counter()
+    cnt = bqcd.bq_get_counters(ctx)
+    e2e_bytes = sum(sum(r) for r in cnt["dslash_bytes"])
+    out["e2e"] = {"value": e2e_bytes / (t1 - t0) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": Vh * 192,
+                  "d2h_bytes_per_step": Vh * 192, "ms_per_step": (t1 - t0) / n_e2e * 1e3}
+
+    # ---- plain FP64 CG on the same system
+    st64 = bqcd.bq_solve_cg(ctx, x_dev, b_dev, tol=1e-10, precision="double", check_every=8, max_iter=20000)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st64 = bqcd.bq_solve_cg(ctx, x_dev, b_dev, tol=1e-10, precision="double", check_every=8, max_iter=20000)
+    e1.record()
+    torch.cuda.synchronize()
+    fp64_ms = e0.elapsed_time(e1)
+    out["cg"] = {"fp64_ms": fp64_ms, "mixed_ms": mixed_ms, "speedup_mixed_vs_fp64": fp64_ms / mixed_ms,
+                 "fp64_iterations": st64["iterations"], "fp64_true_residual": st64["true_residual"]}
+
+    # ---- hopping-term bandwidth sweep (plain D_hop, inputs larger than L2)
+    sweep = {}
+    for prec, recon in (("double", 18), ("double", 12), ("single", 18), ("single", 12), ("half", 18), ("half", 12)):
+        bqcd.bq_set_recon(ctx, prec, recon)
+        src = lat.pack(b, prec)
+        dst = lat.spinor(prec)
+        for _ in range(3):
+            bqcd.bq_apply_dhop(ctx, dst, src, 1, 0, prec)
+        n = 20
+        e0.record()
+        for i in range(n):
+            bqcd.bq_apply_dhop(ctx, dst, src, i & 1, 0, prec)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / n * 1e-3
+        pid = PREC_ID[prec]
+        byts = (8 * link_b(pid, recon) + 2 * SPINOR_B[pid]) * Vh
+        sweep[f"{prec}_r{recon}"] = {"GB/s": byts / t / 1e9, "GFLOP/s": 1320.0 * Vh / t / 1e9, "us": t * 1e6}
+    bqcd.bq_set_recon(ctx, "single", 12)
+    bqcd.bq_set_recon(ctx, "half", 12)
+    out["dslash_sweep"] = sweep
+
+    # ---- CPU oracle on the host cores (bounded sample: 2 Mhat^dag Mhat applies)
+    import oracle
+
+    wl = WORKLOADS[args.workload]
+    op, bb, Vh_o = oracle_setup(wl)
+    gbs, t_step = oracle_gbs(op, bb, Vh_o, 2, 1)
+    out["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": oracle.num_threads(), "kind": "oracle",
+                           "sample": f"2 FP64 Mhat^dag Mhat applies on the full {args.workload} lattice, "
+                                     f"{t_step:.2f} s each"}
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

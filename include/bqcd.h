@@ -85,6 +85,21 @@ typedef struct {
     double dslash_calls;     /* hopping-term launches, each over V/2 sites */
 } bq_solver_stats;
 
+/* Launch counters and optional device timing of the hopping-term kernels.
+ * Buckets [precision][epilogue]: epilogue 0 = plain D_hop, 1 = D_hop followed
+ * by A^{-1} (D_oe A_oo^{-1} step), 2 = A x - k D_hop in (D_eo step of Mhat).
+ * Bytes and flops are ALGORITHMIC per launch: 8 links + 1 input + 1 output
+ * spinor per output site, plus the clover blocks (and the x spinor) the fused
+ * epilogue reads; 1320 flops per site for D_hop, +504 per clover apply,
+ * +48 for the xpay. */
+typedef struct {
+    long long launches;            /* every kernel the library launched since the last reset */
+    long long dslash_launches[3][3];
+    double dslash_bytes[3][3];
+    double dslash_flops[3][3];
+    double dslash_ms[3][3];        /* summed CUDA-event time per launch; 0 unless timing is on */
+} bq_counters;
+
 /* ---- context ------------------------------------------------------------- */
 
 /* Create a context for a lattice of extents dims on the current CUDA device,
@@ -119,6 +134,13 @@ int bq_set_u1(bq_ctx *ctx, const double *A, int where);
  * BQ_ERR_CLOVER_SINGULAR if a block has no inverse. */
 int bq_build_clover(bq_ctx *ctx);
 
+/* Reset the counters; timing != 0 also brackets every hopping-term launch with
+ * CUDA events on the library stream (adds a few microseconds per launch). */
+int bq_reset_counters(bq_ctx *ctx, int timing);
+
+/* Copy the counters; synchronises the library stream when timing is on. */
+int bq_get_counters(bq_ctx *ctx, bq_counters *out);
+
 /* ---- spinor buffers -------------------------------------------------------- */
 
 /* Bytes of one native half-lattice spinor at `precision` (device buffer). */
@@ -128,6 +150,13 @@ size_t bq_spinor_bytes(const bq_ctx *ctx, int precision);
  * into a native device buffer at `precision`, and back. */
 int bq_spinor_pack(bq_ctx *ctx, void *native, const double *canonical, int precision, int where);
 int bq_spinor_unpack(bq_ctx *ctx, double *canonical, const void *native, int precision, int where);
+
+/* result[0] + i result[1] = <a, b> = sum_x sum_{s,c} conj(a) b over the half
+ * lattice, for two native device buffers at `precision`; per-site products in
+ * the storage's arithmetic, global sum in FP64 with a fixed-order grid
+ * reduction (same value on every call). result is host memory; the call
+ * synchronises the library stream. Uses the context's reduction scratch. */
+int bq_spinor_dot(bq_ctx *ctx, const void *a, const void *b, int precision, double *result);
 
 /* ---- operator (native buffers, device) ---------------------------------- */
 
@@ -153,6 +182,20 @@ int bq_apply_mdagm(bq_ctx *ctx, void *out, const void *in, int precision);
  * BQ_ERR_NOT_CONVERGED if max_iter is reached first (x and stats still written). */
 int bq_solve_cg(bq_ctx *ctx, double *x, const double *b, int where,
                 const bq_solver_params *params, bq_solver_stats *stats);
+
+/* Multishift CG (Section 4 lists multishift cg; the shifted systems of an
+ * RHMC rational approximation): solve (Mhat^dag Mhat + shifts[k]) x[k] = b for
+ * k < nshift (1..32, shifts >= 0) in ONE Krylov space of the smallest shift,
+ * run in params->precision to what that precision resolves (FP64: tol,
+ * FP32: 1e-6, FP16: 1e-3 relative iterated residual), with per-shift
+ * zeta/alpha/beta recurrences and per-shift freezing; then every shift is
+ * refined by (mixed-precision) CG from that solution to a TRUE FP64 residual
+ * <= tol |b|.  x[k] are canonical even spinors (host or device, as b); stats
+ * sum iterations and Dslash calls over both phases and report the worst true
+ * residual; residuals[k] (may be NULL) receives each shift's true residual. */
+int bq_solve_multishift_cg(bq_ctx *ctx, double *const *x, const double *b, int where, int nshift,
+                           const double *shifts, const bq_solver_params *params, bq_solver_stats *stats,
+                           double *residuals);
 
 #ifdef __cplusplus
 }

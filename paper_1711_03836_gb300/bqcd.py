@@ -44,6 +44,21 @@ class bq_solver_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class bq_counters(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("dslash_launches", (ctypes.c_longlong * 3) * 3),
+                ("dslash_bytes", (ctypes.c_double * 3) * 3), ("dslash_flops", (ctypes.c_double * 3) * 3),
+                ("dslash_ms", (ctypes.c_double * 3) * 3)]
+
+    def as_dict(self):
+        return {
+            "launches": int(self.launches),
+            "dslash_launches": [[int(v) for v in row] for row in self.dslash_launches],
+            "dslash_bytes": [list(row) for row in self.dslash_bytes],
+            "dslash_flops": [list(row) for row in self.dslash_flops],
+            "dslash_ms": [list(row) for row in self.dslash_ms],
+        }
+
+
 class BqError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -61,6 +76,8 @@ _SIGS = {
     "bq_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "bq_last_error": (ctypes.c_char_p, []),
     "bq_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(bq_params)]),
+    "bq_reset_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "bq_get_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(bq_counters)]),
     "bq_set_recon": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "bq_set_gauge": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "bq_set_u1": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -68,6 +85,8 @@ _SIGS = {
     "bq_spinor_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int]),
     "bq_spinor_pack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "bq_spinor_unpack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "bq_spinor_dot": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_double)]),
     "bq_apply_dhop": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int]),
     "bq_apply_clover": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -76,6 +95,10 @@ _SIGS = {
     "bq_apply_mdagm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "bq_solve_cg": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                    ctypes.POINTER(bq_solver_params), ctypes.POINTER(bq_solver_stats)]),
+    "bq_solve_multishift_cg": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
+                                              ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(bq_solver_params), ctypes.POINTER(bq_solver_stats),
+                                              ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -143,6 +166,16 @@ def bq_set_params(ctx, kappa, csw=0.0, mu=0.0, t_bc=-1.0, charge=0.0):
     _check(_lib_handle().bq_set_params(ctx, ctypes.byref(p)), "bq_set_params")
 
 
+def bq_reset_counters(ctx, timing=False):
+    _check(_lib_handle().bq_reset_counters(ctx, int(bool(timing))), "bq_reset_counters")
+
+
+def bq_get_counters(ctx):
+    c = bq_counters()
+    _check(_lib_handle().bq_get_counters(ctx, ctypes.byref(c)), "bq_get_counters")
+    return c.as_dict()
+
+
 def bq_set_recon(ctx, precision, recon):
     _check(_lib_handle().bq_set_recon(ctx, PREC_NAMES[precision], int(recon)), "bq_set_recon")
 
@@ -178,6 +211,13 @@ def bq_spinor_unpack(ctx, canonical, native, precision):
     _check(_lib_handle().bq_spinor_unpack(ctx, p, _dev_ptr(native), PREC_NAMES[precision], w), "bq_spinor_unpack")
 
 
+def bq_spinor_dot(ctx, a, b, precision):
+    """<a, b> over the half lattice (complex), FP64 accumulation."""
+    r = (ctypes.c_double * 2)()
+    _check(_lib_handle().bq_spinor_dot(ctx, _dev_ptr(a), _dev_ptr(b), PREC_NAMES[precision], r), "bq_spinor_dot")
+    return complex(r[0], r[1])
+
+
 def bq_apply_dhop(ctx, out, inp, out_parity, dagger, precision):
     _check(_lib_handle().bq_apply_dhop(ctx, _dev_ptr(out), _dev_ptr(inp), int(out_parity), int(bool(dagger)),
                                        PREC_NAMES[precision]), "bq_apply_dhop")
@@ -210,6 +250,32 @@ def bq_solve_cg(ctx, x, b, tol=1e-10, max_iter=10000, precision="double", delta=
     if s != BQ_OK and (raise_on_nonconvergence or s != BQ_ERR_NOT_CONVERGED):
         raise BqError(s, "bq_solve_cg")
     return st.as_dict()
+
+
+def bq_solve_multishift_cg(ctx, xs, b, shifts, tol=1e-10, max_iter=20000, precision="double", delta=1e-3,
+                           check_every=8, raise_on_nonconvergence=True):
+    """Solve (Mhat^dag Mhat + shifts[k]) xs[k] = b for all k; xs, b canonical, all host or all device."""
+    n = len(shifts)
+    if len(xs) != n:
+        raise ValueError("one solution buffer per shift")
+    pb, wb = _ptr_where(b)
+    ptrs = []
+    for x in xs:
+        px, wx = _ptr_where(x)
+        if wx != wb:
+            raise ValueError("solutions and b must all be host or all be device buffers")
+        ptrs.append(px)
+    parr = (ctypes.c_void_p * n)(*ptrs)
+    sarr = (ctypes.c_double * n)(*[float(v) for v in shifts])
+    res = (ctypes.c_double * n)()
+    sp = bq_solver_params(tol, int(max_iter), PREC_NAMES[precision], delta, int(check_every), 0.0)
+    st = bq_solver_stats()
+    s = _lib_handle().bq_solve_multishift_cg(ctx, parr, pb, wb, n, sarr, ctypes.byref(sp), ctypes.byref(st), res)
+    if s != BQ_OK and (raise_on_nonconvergence or s != BQ_ERR_NOT_CONVERGED):
+        raise BqError(s, "bq_solve_multishift_cg")
+    d = st.as_dict()
+    d["residuals"] = list(res)
+    return d
 
 
 # ---------------------------------------------------------------- convenience

@@ -10,6 +10,9 @@
 // reconstructed four-spinor. The chemical potential factor e^{+-mu} and the
 // time boundary sign multiply the time hops as scalars; U(1) phases are
 // already folded into the links.
+#include <stdlib.h>
+#include <string.h>
+
 #include "bq_internal.cuh"
 
 struct DslashArgs {
@@ -238,6 +241,13 @@ int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_par
     a.k = k;
     unsigned grid = (unsigned)((c->Vh + 127) / 128);
     int recon = c->links_recon[prec];
+    int slot = -1;
+    if (c->timing) {
+        if (c->ev_used == BQ_EV_PAIRS) BQ_TRY(bq_fold_events(c));
+        slot = c->ev_used++;
+        c->ev_bucket[slot] = prec * 3 + epi;
+        BQ_CUDA_TRY(cudaEventRecord(c->ev[2 * slot], c->stream));
+    }
     if (prec == BQ_PREC_DOUBLE) {
         if (recon == 12) launch_dslash_pr<BQ_PREC_DOUBLE, 12>(a, dagger, epi, grid, c->stream);
         else launch_dslash_pr<BQ_PREC_DOUBLE, 18>(a, dagger, epi, grid, c->stream);
@@ -249,6 +259,56 @@ int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_par
         else launch_dslash_pr<BQ_PREC_HALF, 18>(a, dagger, epi, grid, c->stream);
     }
     BQ_LAUNCH_CHECK();
+    if (slot >= 0) BQ_CUDA_TRY(cudaEventRecord(c->ev[2 * slot + 1], c->stream));
+    // algorithmic traffic and work of this launch
+    double site_bytes = 8.0 * link_bytes_per_link(prec, recon) + 2.0 * spinor_bytes_per_site(prec);
+    double site_flops = 1320.0;
+    if (epi != EPI_PLAIN) {
+        site_bytes += clover_bytes_per_site(prec);
+        site_flops += 504.0;
+    }
+    if (epi == EPI_XPAY) {
+        site_bytes += spinor_bytes_per_site(prec);
+        site_flops += 48.0;
+    }
+    BQ_COUNT(c);
+    c->counters.dslash_launches[prec][epi]++;
+    c->counters.dslash_bytes[prec][epi] += site_bytes * c->Vh;
+    c->counters.dslash_flops[prec][epi] += site_flops * c->Vh;
+    return BQ_OK;
+}
+
+int bq_fold_events(bq_ctx *c) {
+    if (!c->ev_used) return BQ_OK;
+    BQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < c->ev_used; i++) {
+        float ms = 0.f;
+        BQ_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]));
+        int b = c->ev_bucket[i];
+        c->counters.dslash_ms[b / 3][b % 3] += ms;
+    }
+    c->ev_used = 0;
+    return BQ_OK;
+}
+
+extern "C" int bq_reset_counters(bq_ctx *c, int timing) {
+    if (!c) return BQ_ERR_ARG;
+    if (c->ev_used) BQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->ev_used = 0;
+    memset(&c->counters, 0, sizeof c->counters);
+    if (timing && !c->ev) {
+        c->ev = (cudaEvent_t *)calloc(2 * BQ_EV_PAIRS, sizeof(cudaEvent_t));
+        if (!c->ev) return BQ_ERR_NOMEM;
+        for (int i = 0; i < 2 * BQ_EV_PAIRS; i++) BQ_CUDA_TRY(cudaEventCreate(&c->ev[i]));
+    }
+    c->timing = timing ? 1 : 0;
+    return BQ_OK;
+}
+
+extern "C" int bq_get_counters(bq_ctx *c, bq_counters *out) {
+    if (!c || !out) return BQ_ERR_ARG;
+    if (c->timing) BQ_TRY(bq_fold_events(c));
+    *out = c->counters;
     return BQ_OK;
 }
 
@@ -260,6 +320,7 @@ int bq_clover_launch(bq_ctx *c, int prec, void *out, const void *in, int parity,
     else if (prec == BQ_PREC_SINGLE) k_clover<BQ_PREC_SINGLE><<<grid, 128, 0, c->stream>>>(out, in, cl, c->Vh);
     else k_clover<BQ_PREC_HALF><<<grid, 128, 0, c->stream>>>(out, in, cl, c->Vh);
     BQ_LAUNCH_CHECK();
+    BQ_COUNT(c);
     return BQ_OK;
 }
 

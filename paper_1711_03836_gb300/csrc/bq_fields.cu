@@ -129,6 +129,10 @@ extern "C" int bq_destroy(bq_ctx *c) {
     cudaFree(c->red_partials);
     cudaFree(c->red_ticket);
     cudaFree(c->dev_flag);
+    if (c->ev) {
+        for (int i = 0; i < 2 * BQ_EV_PAIRS; i++) cudaEventDestroy(c->ev[i]);
+        free(c->ev);
+    }
     free(c);
     return BQ_OK;
 }
@@ -290,6 +294,7 @@ int bq_prepare_links(bq_ctx *c, int prec) {
     }
 #undef PACK
     BQ_LAUNCH_CHECK();
+    BQ_COUNT(c);
     c->links_valid[prec] = 1;
     return BQ_OK;
 }
@@ -517,9 +522,11 @@ extern "C" int bq_build_clover(bq_ctx *c) {
     k_build_clover<<<grid_for(c->V, 64), 64, 0, c->stream>>>((double2 *)c->clov_master, pblk, c->U_canon, g,
                                                                c->params.kappa * c->params.csw);
     BQ_LAUNCH_CHECK();
+    BQ_COUNT(c);
     k_invert_clover<<<grid_for(4LL * c->Vh, 64), 64, 0, c->stream>>>((double2 *)c->clov_master, pblk, c->Vh,
                                                                      c->dev_flag);
     BQ_LAUNCH_CHECK();
+    BQ_COUNT(c);
     int flag = 0;
     BQ_CUDA_TRY(cudaMemcpyAsync(&flag, c->dev_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     BQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -544,6 +551,7 @@ int bq_prepare_clover(bq_ctx *c, int prec) {
     else
         k_convert_clover<BQ_PREC_HALF><<<grid, 128, 0, c->stream>>>(c->clov[prec], (const double2 *)c->clov_master, c->Vh, 4);
     BQ_LAUNCH_CHECK();
+    BQ_COUNT(c);
     c->clov_valid[prec] = 1;
     return BQ_OK;
 }
@@ -581,6 +589,7 @@ int bq_pack(bq_ctx *c, void *native, const double *canon_dev, int prec) {
     else if (prec == BQ_PREC_SINGLE) k_pack_spinor<BQ_PREC_SINGLE><<<grid, 128, 0, c->stream>>>(native, src, c->Vh);
     else k_pack_spinor<BQ_PREC_HALF><<<grid, 128, 0, c->stream>>>(native, src, c->Vh);
     BQ_LAUNCH_CHECK();
+    BQ_COUNT(c);
     return BQ_OK;
 }
 
@@ -591,6 +600,7 @@ int bq_unpack(bq_ctx *c, double *canon_dev, const void *native, int prec) {
     else if (prec == BQ_PREC_SINGLE) k_unpack_spinor<BQ_PREC_SINGLE><<<grid, 128, 0, c->stream>>>(dst, native, c->Vh);
     else k_unpack_spinor<BQ_PREC_HALF><<<grid, 128, 0, c->stream>>>(dst, native, c->Vh);
     BQ_LAUNCH_CHECK();
+    BQ_COUNT(c);
     return BQ_OK;
 }
 

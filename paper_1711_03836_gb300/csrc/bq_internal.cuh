@@ -466,7 +466,18 @@ struct bq_ctx {
     unsigned int *red_ticket;      // last-block ticket
     int *dev_flag;                 // device error flag (singular clover etc.)
     SolverWork *solver;
+
+    // counters and optional per-launch event timing of the hopping term
+    bq_counters counters;
+    int timing;
+    cudaEvent_t *ev;               // 2 * BQ_EV_PAIRS events, created on first use
+    int ev_bucket[4096];
+    int ev_used;
 };
+
+enum { BQ_EV_PAIRS = 4096 };
+#define BQ_COUNT(c) ((c)->counters.launches++)
+int bq_fold_events(bq_ctx *c);
 
 // field preparation (bq_fields.cu)
 int bq_prepare_links(bq_ctx *c, int prec);

@@ -13,6 +13,7 @@
 // host reads the residual every `check_every` iterations.
 #include <math.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include "bq_internal.cuh"
 
@@ -21,8 +22,16 @@ enum { S_RR = 0, S_BB, S_PAP, S_ALPHA, S_BETA, S_RRPREV, S_RRTRUE, S_SIGMA, S_NS
 constexpr int RED_THREADS = 256;
 constexpr int RED_MAX_BLOCKS = 1024;
 
+static int red_grid(int Vh) {
+    int g = (Vh + RED_THREADS - 1) / RED_THREADS;
+    return g < RED_MAX_BLOCKS ? g : RED_MAX_BLOCKS;
+}
+
 struct SolverWork {
     char *b, *x, *r, *t64;          // FP64 native even spinors
+    char *msx[32], *msp[32];        // multishift solutions / directions (precision pr of the last multishift)
+    int ms_prec, ms_n;
+    double *ms, *h_ms;              // multishift scalars (device, pinned host)
     char *rs[BQ_NPREC], *xs[BQ_NPREC];   // sloppy residual / solution increment (precision pr)
     char *p[BQ_NPREC], *Ap[BQ_NPREC];    // search direction and its image (precision ps)
     double *scal;                    // device scalars
@@ -43,6 +52,12 @@ void bq_solver_free(bq_ctx *c) {
         cudaFree(w->p[p]);
         cudaFree(w->Ap[p]);
     }
+    for (int k = 0; k < 32; k++) {
+        cudaFree(w->msx[k]);
+        cudaFree(w->msp[k]);
+    }
+    cudaFree(w->ms);
+    cudaFreeHost(w->h_ms);
     cudaFree(w->scal);
     cudaFreeHost(w->h_scal);
     if (w->e0) cudaEventDestroy(w->e0);
@@ -130,20 +145,37 @@ struct RedArgs {
 // --------------------------------------------------------------------------
 // CG kernels; PS = precision of p, Ap; PR = precision of rs, xs
 
-// r = b, rs = b, p = b, xs = 0, x = 0; rr = bb = |b|^2
+// r = b - t - sigma x (t = (Mhat^dag Mhat) x0 when x holds an initial guess, else t = null:
+// r = b and x = 0); rs = r, p = r, xs = 0; rr = |r|^2, bb = |b|^2
 template <int PS, int PR>
-__global__ void __launch_bounds__(RED_THREADS) k_cg_init(const void *b, void *x, void *r, void *rs, void *xs, void *p,
-                                                         RedArgs ra) {
-    double v[1] = {0.0};
+__global__ void __launch_bounds__(RED_THREADS) k_cg_init(const void *b, const void *t, void *x, void *r, void *rs,
+                                                         void *xs, void *p, RedArgs ra) {
+    using TR = typename Traits<PR>::real;
+    using TS = typename Traits<PS>::real;
+    const double sigma = ra.scal[S_SIGMA];
+    double v[2] = {0.0, 0.0};
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < ra.Vh; h += gridDim.x * blockDim.x) {
-        cplx<double> s[12], z[12];
-        SpinorIO<BQ_PREC_DOUBLE>::load(s, b, h, ra.Vh);
+        cplx<double> bv[12], s[12];
+        SpinorIO<BQ_PREC_DOUBLE>::load(bv, b, h, ra.Vh);
+        if (t) {
+            cplx<double> tv[12], xv[12];
+            SpinorIO<BQ_PREC_DOUBLE>::load(tv, t, h, ra.Vh);
+            SpinorIO<BQ_PREC_DOUBLE>::load(xv, x, h, ra.Vh);
 #pragma unroll
-        for (int c = 0; c < 12; c++) z[c] = {0.0, 0.0};
+            for (int c = 0; c < 12; c++) {
+                s[c].re = bv[c].re - tv[c].re - sigma * xv[c].re;
+                s[c].im = bv[c].im - tv[c].im - sigma * xv[c].im;
+            }
+        } else {
+            cplx<double> z[12];
+#pragma unroll
+            for (int c = 0; c < 12; c++) {
+                s[c] = bv[c];
+                z[c] = {0.0, 0.0};
+            }
+            SpinorIO<BQ_PREC_DOUBLE>::store(x, h, ra.Vh, z);
+        }
         SpinorIO<BQ_PREC_DOUBLE>::store(r, h, ra.Vh, s);
-        SpinorIO<BQ_PREC_DOUBLE>::store(x, h, ra.Vh, z);
-        using TR = typename Traits<PR>::real;
-        using TS = typename Traits<PS>::real;
         cplx<TR> sr[12], zr[12];
         cplx<TS> sp[12];
 #pragma unroll
@@ -156,11 +188,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_cg_init(const void *b, void *x,
         SpinorIO<PR>::store(xs, h, ra.Vh, zr);
         SpinorIO<PS>::store(p, h, ra.Vh, sp);
         v[0] += norm2_site(s);
+        v[1] += norm2_site(bv);
     }
-    double tot[1];
+    double tot[2];
     if (grid_sum(v, ra.partials, ra.ticket, tot) && threadIdx.x == 0) {
         ra.scal[S_RR] = tot[0];
-        ra.scal[S_BB] = tot[0];
+        ra.scal[S_BB] = tot[1];
         ra.scal[S_RRTRUE] = tot[0];
     }
 }
@@ -301,13 +334,223 @@ __global__ void __launch_bounds__(RED_THREADS) k_residual(const void *b, const v
     }
 }
 
+
+// --------------------------------------------------------------------------
+// multishift CG (one Krylov space for all shifts; shifted systems follow the
+// collinear-residual recurrences: r_sigma = zeta_sigma r).  Arrays of
+// MS_MAX entries in `ms`, then three scalars.
+
+constexpr int MS_MAX = 32;
+enum { M_ZETA = 0, M_ZOLD, M_ALPHA, M_BETA, M_ACTIVE, M_UPD, M_SHIFT, M_NARR };
+enum { M_APREV = M_NARR * MS_MAX, M_BPREV, M_NACTIVE, M_NTOTAL };
+
+struct MSPtrs {
+    void *x[MS_MAX];  // solution of each shift, precision PR
+    void *p[MS_MAX];  // search direction of each non-base shift, precision PR
+};
+
+// x_k = 0; p_k = b for k != base
+template <int PR>
+__global__ void __launch_bounds__(RED_THREADS) k_ms_init(const void *b, MSPtrs ptr, int n, int base, int Vh) {
+    using TR = typename Traits<PR>::real;
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<double> bv[12];
+        SpinorIO<BQ_PREC_DOUBLE>::load(bv, b, h, Vh);
+        cplx<TR> bt[12], z[12];
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            bt[c] = {(TR)bv[c].re, (TR)bv[c].im};
+            z[c] = {TR(0), TR(0)};
+        }
+        for (int k = 0; k < n; k++) {
+            SpinorIO<PR>::store(ptr.x[k], h, Vh, z);
+            if (k != base) SpinorIO<PR>::store(ptr.p[k], h, Vh, bt);
+        }
+    }
+}
+
+// rs -= alpha Ap; rr_new = |rs|^2; then (last block) beta and every shift's
+// zeta_{j+1} = zeta_j zeta_{j-1} a_{j-1} / (a_j b_{j-1} (zeta_{j-1} - zeta_j) + zeta_{j-1} a_{j-1} (1 + s a_j)),
+// alpha_s = a_j zeta_{j+1} / zeta_j, beta_s = b_j (zeta_{j+1} / zeta_j)^2, s = sigma - sigma_base
+template <int PS, int PR>
+__global__ void __launch_bounds__(RED_THREADS) k_ms_residual(const void *Ap, void *rs, RedArgs ra, double *ms, int n,
+                                                             int base, double tol2bb) {
+    using TS = typename Traits<PS>::real;
+    using TR = typename Traits<PR>::real;
+    const TR alpha = (TR)ra.scal[S_ALPHA];
+    double v[1] = {0.0};
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < ra.Vh; h += gridDim.x * blockDim.x) {
+        cplx<TS> q[12];
+        cplx<TR> rv[12];
+        SpinorIO<PS>::load(q, Ap, h, ra.Vh);
+        SpinorIO<PR>::load(rv, rs, h, ra.Vh);
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            rv[c].re = fma(-alpha, (TR)q[c].re, rv[c].re);
+            rv[c].im = fma(-alpha, (TR)q[c].im, rv[c].im);
+        }
+        SpinorIO<PR>::store(rs, h, ra.Vh, rv);
+        v[0] += norm2_site(rv);
+    }
+    double tot[1];
+    if (grid_sum(v, ra.partials, ra.ticket, tot) && threadIdx.x == 0) {
+        const double rr = ra.scal[S_RR], rrn = tot[0];
+        const double a = ra.scal[S_ALPHA], bta = rrn / rr;
+        ra.scal[S_RRPREV] = rr;
+        ra.scal[S_RR] = rrn;
+        ra.scal[S_BETA] = bta;
+        const double ap = ms[M_APREV], bp = ms[M_BPREV];
+        int nact = 0;
+        for (int k = 0; k < n; k++) {
+            double *z = ms + M_ZETA * MS_MAX, *zo = ms + M_ZOLD * MS_MAX, *al = ms + M_ALPHA * MS_MAX,
+                   *be = ms + M_BETA * MS_MAX, *act = ms + M_ACTIVE * MS_MAX, *upd = ms + M_UPD * MS_MAX;
+            upd[k] = act[k];
+            if (act[k] == 0.0) continue;
+            if (k == base) {
+                al[k] = a;
+                be[k] = bta;
+                act[k] = (rrn > tol2bb) ? 1.0 : 0.0;
+            } else {
+                const double sdiff = ms[M_SHIFT * MS_MAX + k] - ms[M_SHIFT * MS_MAX + base];
+                const double zk = z[k], zok = zo[k];
+                const double den = a * bp * (zok - zk) + zok * ap * (1.0 + sdiff * a);
+                const double zn = zk * zok * ap / den;
+                al[k] = a * zn / zk;
+                be[k] = bta * (zn / zk) * (zn / zk);
+                zo[k] = zk;
+                z[k] = zn;
+                act[k] = (zn * zn * rrn > tol2bb) ? 1.0 : 0.0;
+            }
+            nact += (act[k] != 0.0);
+        }
+        ms[M_APREV] = a;
+        ms[M_BPREV] = bta;
+        ms[M_NACTIVE] = nact;
+    }
+}
+
+// for every shift updated this iteration: x_k += alpha_k p_k; p_k = zeta_k r + beta_k p_k
+// (base: x += alpha p); then the base direction p = r + beta p
+template <int PS, int PR>
+__global__ void __launch_bounds__(RED_THREADS) k_ms_update(void *p, const void *rs, MSPtrs ptr, const double *ms,
+                                                           const double *scal, int n, int base, int Vh) {
+    using TS = typename Traits<PS>::real;
+    using TR = typename Traits<PR>::real;
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<TS> pv[12];
+        cplx<TR> rv[12];
+        SpinorIO<PS>::load(pv, p, h, Vh);
+        SpinorIO<PR>::load(rv, rs, h, Vh);
+        for (int k = 0; k < n; k++) {
+            if (ms[M_UPD * MS_MAX + k] == 0.0) continue;
+            const TR ak = (TR)ms[M_ALPHA * MS_MAX + k];
+            cplx<TR> xv[12];
+            SpinorIO<PR>::load(xv, ptr.x[k], h, Vh);
+            if (k == base) {
+#pragma unroll
+                for (int c = 0; c < 12; c++) {
+                    xv[c].re = fma(ak, (TR)pv[c].re, xv[c].re);
+                    xv[c].im = fma(ak, (TR)pv[c].im, xv[c].im);
+                }
+            } else {
+                const TR zk = (TR)ms[M_ZETA * MS_MAX + k], bk = (TR)ms[M_BETA * MS_MAX + k];
+                cplx<TR> pk[12];
+                SpinorIO<PR>::load(pk, ptr.p[k], h, Vh);
+#pragma unroll
+                for (int c = 0; c < 12; c++) {
+                    xv[c].re = fma(ak, pk[c].re, xv[c].re);
+                    xv[c].im = fma(ak, pk[c].im, xv[c].im);
+                    pk[c].re = fma(bk, pk[c].re, zk * rv[c].re);
+                    pk[c].im = fma(bk, pk[c].im, zk * rv[c].im);
+                }
+                SpinorIO<PR>::store(ptr.p[k], h, Vh, pk);
+            }
+            SpinorIO<PR>::store(ptr.x[k], h, Vh, xv);
+        }
+        const TS bt = (TS)scal[S_BETA];
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            pv[c].re = fma(bt, pv[c].re, (TS)rv[c].re);
+            pv[c].im = fma(bt, pv[c].im, (TS)rv[c].im);
+        }
+        SpinorIO<PS>::store(p, h, Vh, pv);
+    }
+}
+
+// x (FP64) = y (precision PR)
+template <int PR>
+__global__ void __launch_bounds__(RED_THREADS) k_to_double(void *x, const void *y, int Vh) {
+    using TR = typename Traits<PR>::real;
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<TR> yv[12];
+        cplx<double> xv[12];
+        SpinorIO<PR>::load(yv, y, h, Vh);
+#pragma unroll
+        for (int c = 0; c < 12; c++) xv[c] = {(double)yv[c].re, (double)yv[c].im};
+        SpinorIO<BQ_PREC_DOUBLE>::store(x, h, Vh, xv);
+    }
+}
+
+
+// --------------------------------------------------------------------------
+// public BLAS-1 reduction: <a, b> = sum conj(a) b, per-site products in the
+// storage's arithmetic, accumulated in FP64 with the deterministic grid sum
+
+template <int P>
+__global__ void __launch_bounds__(RED_THREADS) k_dot(const void *a, const void *b, double *partials,
+                                                     unsigned int *ticket, double *out, int Vh) {
+    using T = typename Traits<P>::real;
+    double v[2] = {0.0, 0.0};
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<T> av[12], bv[12];
+        SpinorIO<P>::load(av, a, h, Vh);
+        SpinorIO<P>::load(bv, b, h, Vh);
+        T re = T(0), im = T(0);
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            re += av[c].re * bv[c].re + av[c].im * bv[c].im;
+            im += av[c].re * bv[c].im - av[c].im * bv[c].re;
+        }
+        v[0] += (double)re;
+        v[1] += (double)im;
+    }
+    double tot[2];
+    if (grid_sum(v, partials, ticket, tot) && threadIdx.x == 0) {
+        out[0] = tot[0];
+        out[1] = tot[1];
+    }
+}
+
+int bq_dot_launch(bq_ctx *c, const void *a, const void *b, int prec, double *partials, unsigned int *ticket,
+                  double *out_dev) {
+    const int G = red_grid(c->Vh);
+    if (prec == BQ_PREC_DOUBLE)
+        k_dot<BQ_PREC_DOUBLE><<<G, RED_THREADS, 0, c->stream>>>(a, b, partials, ticket, out_dev, c->Vh);
+    else if (prec == BQ_PREC_SINGLE)
+        k_dot<BQ_PREC_SINGLE><<<G, RED_THREADS, 0, c->stream>>>(a, b, partials, ticket, out_dev, c->Vh);
+    else
+        k_dot<BQ_PREC_HALF><<<G, RED_THREADS, 0, c->stream>>>(a, b, partials, ticket, out_dev, c->Vh);
+    BQ_LAUNCH_CHECK();
+    BQ_COUNT(c);
+    return BQ_OK;
+}
+
+extern "C" int bq_spinor_dot(bq_ctx *c, const void *a, const void *b, int prec, double *result) {
+    if (!c || !a || !b || !result || !(prec == BQ_PREC_DOUBLE || prec == BQ_PREC_SINGLE || prec == BQ_PREC_HALF)) {
+        bq_set_error("bq_spinor_dot: bad arguments");
+        return BQ_ERR_ARG;
+    }
+    // partials in the context's reduction scratch; the two result doubles after the partials
+    double *out_dev = c->red_partials + 2 * RED_MAX_BLOCKS;
+    BQ_TRY(bq_dot_launch(c, a, b, prec, c->red_partials, c->red_ticket, out_dev));
+    BQ_CUDA_TRY(cudaMemcpyAsync(result, out_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    BQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return BQ_OK;
+}
+
 // --------------------------------------------------------------------------
 // host driver
 
-static int red_grid(int Vh) {
-    int g = (Vh + RED_THREADS - 1) / RED_THREADS;
-    return g < RED_MAX_BLOCKS ? g : RED_MAX_BLOCKS;
-}
 
 static int ensure_work(bq_ctx *c, int ps, int pr) {
     if (!c->solver) {
@@ -340,8 +583,10 @@ static int read_scalars(bq_ctx *c) {
     return BQ_OK;
 }
 
+// CG / reliable-update mixed CG on (Mhat^dag Mhat + shift) x = b; b is w->b (FP64 native).
+// With have_x0 the solve starts from the FP64 native w->x, else from x = 0.
 template <int PS, int PR>
-static int cg_run(bq_ctx *c, const bq_solver_params *sp, bq_solver_stats *st) {
+static int cg_run(bq_ctx *c, const bq_solver_params *sp, bq_solver_stats *st, bool have_x0) {
     SolverWork *w = c->solver;
     const int Vh = c->Vh;
     const int G = red_grid(Vh);
@@ -353,13 +598,17 @@ static int cg_run(bq_ctx *c, const bq_solver_params *sp, bq_solver_stats *st) {
     double init[S_NSCAL] = {0};
     init[S_SIGMA] = sp->shift;
     BQ_CUDA_TRY(cudaMemcpyAsync(w->scal, init, sizeof init, cudaMemcpyHostToDevice, s));
-    k_cg_init<PS, PR><<<G, RED_THREADS, 0, s>>>(w->b, w->x, w->r, w->rs[PR], w->xs[PR], w->p[PS], ra);
+    if (have_x0)
+        BQ_TRY(bq_mdagm_launch(c, BQ_PREC_DOUBLE, w->t64, w->x, c->tmp_odd[BQ_PREC_DOUBLE], c->tmp_even[BQ_PREC_DOUBLE]));
+    k_cg_init<PS, PR><<<G, RED_THREADS, 0, s>>>(w->b, have_x0 ? w->t64 : nullptr, w->x, w->r, w->rs[PR], w->xs[PR],
+                                                w->p[PS], ra);
+    BQ_COUNT(c);
     BQ_LAUNCH_CHECK();
     BQ_TRY(read_scalars(c));
     const double bb = w->h_scal[S_BB];
     st->iterations = 0;
     st->reliable_updates = 0;
-    st->dslash_calls = 0;
+    st->dslash_calls = have_x0 ? 4 : 0;
     st->converged = 0;
     st->true_residual = 0.0;
     if (bb == 0.0) {
@@ -367,12 +616,19 @@ static int cg_run(bq_ctx *c, const bq_solver_params *sp, bq_solver_stats *st) {
         return BQ_OK;
     }
     const double target = sp->tol * sp->tol * bb;
-    double maxrr = bb, rrtrue = bb;
+    double rrtrue = w->h_scal[S_RR], maxrr = rrtrue;
+    if (rrtrue <= target) {
+        st->converged = 1;
+        st->true_residual = sqrt(rrtrue / bb);
+        return BQ_OK;
+    }
     int it = 0;
     while (true) {
         BQ_TRY(bq_mdagm_launch(c, PS, w->Ap[PS], w->p[PS], c->tmp_odd[PS], c->tmp_even[PS]));
         k_cg_pap<PS><<<G, RED_THREADS, 0, s>>>(w->p[PS], w->Ap[PS], ra);
+        BQ_COUNT(c);
         k_cg_update_xr<PS, PR><<<G, RED_THREADS, 0, s>>>(w->p[PS], w->Ap[PS], w->xs[PR], w->rs[PR], ra);
+        BQ_COUNT(c);
         BQ_LAUNCH_CHECK();
         it++;
         st->dslash_calls += 4;
@@ -387,9 +643,11 @@ static int cg_run(bq_ctx *c, const bq_solver_params *sp, bq_solver_stats *st) {
             if (rr > maxrr) maxrr = rr;
             if (rr < delta * delta * maxrr || rr <= target || it >= sp->max_iter) {
                 k_promote<PR><<<G, RED_THREADS, 0, s>>>(w->x, w->xs[PR], Vh);
+                BQ_COUNT(c);
                 BQ_TRY(bq_mdagm_launch(c, BQ_PREC_DOUBLE, w->t64, w->x, c->tmp_odd[BQ_PREC_DOUBLE],
                                        c->tmp_even[BQ_PREC_DOUBLE]));
                 k_residual<PR><<<G, RED_THREADS, 0, s>>>(w->b, w->t64, w->x, w->r, w->rs[PR], ra);
+                BQ_COUNT(c);
                 BQ_LAUNCH_CHECK();
                 BQ_TRY(read_scalars(c));
                 st->reliable_updates++;
@@ -404,11 +662,18 @@ static int cg_run(bq_ctx *c, const bq_solver_params *sp, bq_solver_stats *st) {
             }
         }
         k_cg_update_p<PS, PR><<<G, RED_THREADS, 0, s>>>(w->p[PS], w->rs[PR], w->scal, Vh);
+        BQ_COUNT(c);
         BQ_LAUNCH_CHECK();
     }
     st->iterations = it;
     st->true_residual = sqrt(rrtrue / bb);
     return BQ_OK;
+}
+
+static int cg_dispatch(bq_ctx *c, const bq_solver_params *sp, bq_solver_stats *st, bool have_x0) {
+    if (sp->precision == BQ_PREC_DOUBLE) return cg_run<BQ_PREC_DOUBLE, BQ_PREC_DOUBLE>(c, sp, st, have_x0);
+    if (sp->precision == BQ_PREC_SINGLE) return cg_run<BQ_PREC_SINGLE, BQ_PREC_SINGLE>(c, sp, st, have_x0);
+    return cg_run<BQ_PREC_HALF, BQ_PREC_SINGLE>(c, sp, st, have_x0);
 }
 
 extern "C" int bq_solve_cg(bq_ctx *c, double *x, const double *b, int where, const bq_solver_params *sp,
@@ -439,9 +704,7 @@ extern "C" int bq_solve_cg(bq_ctx *c, double *x, const double *b, int where, con
     BQ_CUDA_TRY(cudaEventRecord(w->e0, c->stream));
     BQ_TRY(bq_spinor_pack(c, w->b, b, BQ_PREC_DOUBLE, where));
     int status;
-    if (ps == BQ_PREC_DOUBLE) status = cg_run<BQ_PREC_DOUBLE, BQ_PREC_DOUBLE>(c, sp, st);
-    else if (ps == BQ_PREC_SINGLE) status = cg_run<BQ_PREC_SINGLE, BQ_PREC_SINGLE>(c, sp, st);
-    else status = cg_run<BQ_PREC_HALF, BQ_PREC_SINGLE>(c, sp, st);
+    status = cg_dispatch(c, sp, st, false);
     if (status != BQ_OK && status != BQ_ERR_NOT_CONVERGED) return status;
     BQ_TRY(bq_spinor_unpack(c, x, w->x, BQ_PREC_DOUBLE, where));
     BQ_CUDA_TRY(cudaEventRecord(w->e1, c->stream));
@@ -454,4 +717,179 @@ extern "C" int bq_solve_cg(bq_ctx *c, double *x, const double *b, int where, con
         return BQ_ERR_NOT_CONVERGED;
     }
     return status;
+}
+
+// --------------------------------------------------------------------------
+// multishift driver
+
+template <int PS, int PR>
+static int ms_run(bq_ctx *c, int n, const double *shifts, int base, double tol_ms, int max_iter, int check,
+                  int *iters, double *dslash) {
+    SolverWork *w = c->solver;
+    const int Vh = c->Vh;
+    const int G = red_grid(Vh);
+    RedArgs ra{c->red_partials, c->red_ticket, w->scal, Vh};
+    cudaStream_t s = c->stream;
+    MSPtrs ptr;
+    for (int k = 0; k < MS_MAX; k++) {
+        ptr.x[k] = k < n ? w->msx[k] : nullptr;
+        ptr.p[k] = (k < n && k != base) ? w->msp[k] : nullptr;
+    }
+    double init[S_NSCAL] = {0};
+    init[S_SIGMA] = shifts[base];
+    BQ_CUDA_TRY(cudaMemcpyAsync(w->scal, init, sizeof init, cudaMemcpyHostToDevice, s));
+    double hms[M_NTOTAL];
+    memset(hms, 0, sizeof hms);
+    for (int k = 0; k < n; k++) {
+        hms[M_ZETA * MS_MAX + k] = 1.0;
+        hms[M_ZOLD * MS_MAX + k] = 1.0;
+        hms[M_ACTIVE * MS_MAX + k] = 1.0;
+        hms[M_SHIFT * MS_MAX + k] = shifts[k];
+    }
+    hms[M_APREV] = 1.0;
+    hms[M_BPREV] = 0.0;
+    hms[M_NACTIVE] = n;
+    BQ_CUDA_TRY(cudaMemcpyAsync(w->ms, hms, sizeof hms, cudaMemcpyHostToDevice, s));
+    k_cg_init<PS, PR><<<G, RED_THREADS, 0, s>>>(w->b, nullptr, w->x, w->r, w->rs[PR], w->xs[PR], w->p[PS], ra);
+    BQ_COUNT(c);
+    k_ms_init<PR><<<G, RED_THREADS, 0, s>>>(w->b, ptr, n, base, Vh);
+    BQ_COUNT(c);
+    BQ_LAUNCH_CHECK();
+    BQ_TRY(read_scalars(c));
+    const double bb = w->h_scal[S_BB];
+    *iters = 0;
+    if (bb == 0.0) return BQ_OK;
+    const double tol2bb = tol_ms * tol_ms * bb;
+    int it = 0;
+    while (it < max_iter) {
+        BQ_TRY(bq_mdagm_launch(c, PS, w->Ap[PS], w->p[PS], c->tmp_odd[PS], c->tmp_even[PS]));
+        k_cg_pap<PS><<<G, RED_THREADS, 0, s>>>(w->p[PS], w->Ap[PS], ra);
+        BQ_COUNT(c);
+        k_ms_residual<PS, PR><<<G, RED_THREADS, 0, s>>>(w->Ap[PS], w->rs[PR], ra, w->ms, n, base, tol2bb);
+        BQ_COUNT(c);
+        k_ms_update<PS, PR><<<G, RED_THREADS, 0, s>>>(w->p[PS], w->rs[PR], ptr, w->ms, w->scal, n, base, Vh);
+        BQ_COUNT(c);
+        BQ_LAUNCH_CHECK();
+        it++;
+        *dslash += 4;
+        if (it % check == 0) {
+            BQ_CUDA_TRY(cudaMemcpyAsync(w->h_ms, w->ms, sizeof(double) * M_NTOTAL, cudaMemcpyDeviceToHost, s));
+            BQ_CUDA_TRY(cudaStreamSynchronize(s));
+            double na = w->h_ms[M_NACTIVE];
+            if (!(na == na)) {
+                bq_set_error("multishift breakdown: NaN");
+                return BQ_ERR_NOT_CONVERGED;
+            }
+            if (na == 0.0) break;
+        }
+    }
+    *iters = it;
+    return BQ_OK;
+}
+
+extern "C" int bq_solve_multishift_cg(bq_ctx *c, double *const *x, const double *b, int where, int nshift,
+                                      const double *shifts, const bq_solver_params *sp, bq_solver_stats *st,
+                                      double *residuals) {
+    if (!c || !x || !b || !shifts || !sp || !(where == BQ_HOST || where == BQ_DEVICE) || nshift < 1 ||
+        nshift > MS_MAX) {
+        bq_set_error("bq_solve_multishift_cg: bad arguments (1 <= nshift <= %d)", MS_MAX);
+        return BQ_ERR_ARG;
+    }
+    for (int k = 0; k < nshift; k++)
+        if (!x[k] || !(shifts[k] >= 0.0)) {
+            bq_set_error("bq_solve_multishift_cg: null solution pointer or negative shift %d", k);
+            return BQ_ERR_ARG;
+        }
+    int ps = sp->precision;
+    if (!(ps == BQ_PREC_DOUBLE || ps == BQ_PREC_SINGLE || ps == BQ_PREC_HALF) || !(sp->tol > 0) ||
+        sp->max_iter < 1 || sp->delta < 0 || sp->delta >= 1) {
+        bq_set_error("bq_solve_multishift_cg: bad solver parameters");
+        return BQ_ERR_ARG;
+    }
+    if (!c->have_gauge) {
+        bq_set_error("gauge field not set");
+        return BQ_ERR_STATE;
+    }
+    bq_solver_stats local;
+    if (!st) st = &local;
+    memset(st, 0, sizeof *st);
+    int pr = (ps == BQ_PREC_HALF) ? BQ_PREC_SINGLE : ps;
+    BQ_TRY(ensure_work(c, ps, pr));
+    SolverWork *w = c->solver;
+    if (w->ms_prec != pr) {
+        for (int k = 0; k < MS_MAX; k++) {
+            cudaFree(w->msx[k]);
+            cudaFree(w->msp[k]);
+            w->msx[k] = w->msp[k] = nullptr;
+        }
+        w->ms_prec = pr;
+    }
+    size_t vb = spinor_bytes_per_site(pr) * (size_t)c->Vh;
+    for (int k = 0; k < nshift; k++) {
+        BQ_TRY(bq_alloc((void **)&w->msx[k], vb));
+        BQ_TRY(bq_alloc((void **)&w->msp[k], vb));
+    }
+    BQ_TRY(bq_alloc((void **)&w->ms, sizeof(double) * M_NTOTAL));
+    if (!w->h_ms) BQ_CUDA_TRY(cudaMallocHost((void **)&w->h_ms, sizeof(double) * M_NTOTAL));
+    BQ_TRY(bq_prepare_links(c, BQ_PREC_DOUBLE));
+    BQ_TRY(bq_prepare_clover(c, BQ_PREC_DOUBLE));
+    BQ_TRY(bq_prepare_links(c, ps));
+    BQ_TRY(bq_prepare_clover(c, ps));
+
+    int base = 0;
+    for (int k = 1; k < nshift; k++)
+        if (shifts[k] < shifts[base]) base = k;
+    const int check = sp->check_every > 0 ? sp->check_every : 1;
+    // the sloppy Krylov space is run to what its precision resolves; refinement does the rest
+    double tol_ms = ps == BQ_PREC_DOUBLE ? sp->tol : ps == BQ_PREC_SINGLE ? 1e-6 : 1e-3;
+    if (tol_ms < sp->tol) tol_ms = sp->tol;
+
+    BQ_CUDA_TRY(cudaEventRecord(w->e0, c->stream));
+    BQ_TRY(bq_spinor_pack(c, w->b, b, BQ_PREC_DOUBLE, where));
+    int ms_iters = 0;
+    double dsl = 0;
+    int status;
+    if (ps == BQ_PREC_DOUBLE)
+        status = ms_run<BQ_PREC_DOUBLE, BQ_PREC_DOUBLE>(c, nshift, shifts, base, tol_ms, sp->max_iter, check, &ms_iters, &dsl);
+    else if (ps == BQ_PREC_SINGLE)
+        status = ms_run<BQ_PREC_SINGLE, BQ_PREC_SINGLE>(c, nshift, shifts, base, tol_ms, sp->max_iter, check, &ms_iters, &dsl);
+    else
+        status = ms_run<BQ_PREC_HALF, BQ_PREC_SINGLE>(c, nshift, shifts, base, tol_ms, sp->max_iter, check, &ms_iters, &dsl);
+    if (status != BQ_OK) return status;
+    st->iterations = ms_iters;
+    st->dslash_calls = dsl;
+    st->converged = 1;
+    // per-shift refinement from the multishift solution to the true FP64 residual
+    const int G = red_grid(c->Vh);
+    for (int k = 0; k < nshift; k++) {
+        if (pr == BQ_PREC_DOUBLE)
+            k_to_double<BQ_PREC_DOUBLE><<<G, RED_THREADS, 0, c->stream>>>(w->x, w->msx[k], c->Vh);
+        else
+            k_to_double<BQ_PREC_SINGLE><<<G, RED_THREADS, 0, c->stream>>>(w->x, w->msx[k], c->Vh);
+        BQ_COUNT(c);
+        BQ_LAUNCH_CHECK();
+        bq_solver_params rp = *sp;
+        rp.shift = shifts[k];
+        bq_solver_stats rs;
+        memset(&rs, 0, sizeof rs);
+        int s2 = cg_dispatch(c, &rp, &rs, true);
+        if (s2 != BQ_OK && s2 != BQ_ERR_NOT_CONVERGED) return s2;
+        BQ_TRY(bq_spinor_unpack(c, x[k], w->x, BQ_PREC_DOUBLE, where));
+        st->iterations += rs.iterations;
+        st->reliable_updates += rs.reliable_updates;
+        st->dslash_calls += rs.dslash_calls;
+        if (!rs.converged) st->converged = 0;
+        if (rs.true_residual > st->true_residual) st->true_residual = rs.true_residual;
+        if (residuals) residuals[k] = rs.true_residual;
+    }
+    BQ_CUDA_TRY(cudaEventRecord(w->e1, c->stream));
+    BQ_CUDA_TRY(cudaEventSynchronize(w->e1));
+    float msec = 0.f;
+    cudaEventElapsedTime(&msec, w->e0, w->e1);
+    st->seconds = msec * 1e-3;
+    if (!st->converged) {
+        bq_set_error("multishift refinement reached max_iter; worst true residual %.3e", st->true_residual);
+        return BQ_ERR_NOT_CONVERGED;
+    }
+    return BQ_OK;
 }
