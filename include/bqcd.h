@@ -158,6 +158,24 @@ int bq_spinor_unpack(bq_ctx *ctx, double *canonical, const void *native, int pre
  * synchronises the library stream. Uses the context's reduction scratch. */
 int bq_spinor_dot(bq_ctx *ctx, const void *a, const void *b, int precision, double *result);
 
+/* The same <a, b> as bq_spinor_dot, for callers that cannot allocate device
+ * memory: programs that give all of the GPU's memory to their own arena at
+ * start-up, or that must not risk the device-wide synchronisation a
+ * cudaMalloc/cudaFree can imply inside a time-critical loop. The paper has no
+ * counterpart; this is a library service. It needs no context and allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library call): the block
+ * partials, ticket and result live in a 256 KB file-scope device array that
+ * every GPU loading the library holds until exit. a and b are native device
+ * buffers of n_sites = V/2 sites at `precision`; n_sites is limited to
+ * 4 194 304 (16 384 blocks of 256 sites), larger values return BQ_ERR_ARG.
+ * result is host memory; the call synchronises `cuda_stream`. All calls share
+ * the array (its ticket is cleared per call): calls that overlap on the GPU
+ * race and must be serialised by the caller. The first call on a device looks
+ * up the array's address with that device current; make it before any stream
+ * capture. */
+int bq_spinor_dot_noalloc(const void *a, const void *b, long long n_sites, int precision, void *cuda_stream,
+                          double *result);
+
 /* ---- operator (native buffers, device) ---------------------------------- */
 
 /* out = D_hop in restricted to output parity out_parity (Eq. 1 / Eq. 5);

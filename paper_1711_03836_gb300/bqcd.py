@@ -87,6 +87,8 @@ _SIGS = {
     "bq_spinor_unpack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "bq_spinor_dot": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_double)]),
+    "bq_spinor_dot_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
+                                             ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "bq_apply_dhop": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int]),
     "bq_apply_clover": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -215,6 +217,18 @@ def bq_spinor_dot(ctx, a, b, precision):
     """<a, b> over the half lattice (complex), FP64 accumulation."""
     r = (ctypes.c_double * 2)()
     _check(_lib_handle().bq_spinor_dot(ctx, _dev_ptr(a), _dev_ptr(b), PREC_NAMES[precision], r), "bq_spinor_dot")
+    return complex(r[0], r[1])
+
+
+def bq_spinor_dot_noalloc(a, b, n_sites, precision, stream=None):
+    """<a, b> of two native buffers of n_sites sites without a context and without allocating."""
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream().cuda_stream
+    r = (ctypes.c_double * 2)()
+    _check(_lib_handle().bq_spinor_dot_noalloc(_dev_ptr(a), _dev_ptr(b), int(n_sites), PREC_NAMES[precision],
+                                               ctypes.c_void_p(stream), r), "bq_spinor_dot_noalloc")
     return complex(r[0], r[1])
 
 
