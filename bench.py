@@ -317,7 +317,7 @@ def main():
                   "true_residual": stats[-1]["true_residual"], "converged": stats[-1]["converged"]},
     }
 
-    if not args.no_extras and rank == 0:
+    if not args.no_extras and world == 1:
         line.update(extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, ms_max / args.steps, torch, bqcd))
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -325,6 +325,70 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+FP64_PEAK_GFLOPS = 1250.0
+
+
+def _timed(torch, fn):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return r, (time.perf_counter() - t0) * 1e3
+
+
+def batched_extras(torch, bqcd):
+    """12 point sources and 10 RHMC shifts on 24^3x48, and a ragged set of four
+    lattices: one batched solve against the same systems solved one at a time
+    (mixed precision, FP32 inner, to a true FP64 residual 1e-10)."""
+    from paper_1711_03836_gb300 import synth
+
+    out = {}
+    kw = dict(tol=1e-10, precision="single", delta=1e-3, check_every=8, max_iter=20000)
+    wl = WORKLOADS["24^3x48"]
+    lat = bqcd.Lattice(wl["dims"], wl["kappa"], wl["csw"], wl["mu"], -1.0)
+    bqcd.bq_set_gauge(lat.ctx, synth.gauge_field(wl["dims"], wl["eps"], wl["seed"]))
+    bqcd.bq_set_recon(lat.ctx, "single", 12)
+    srcs = [torch.from_numpy(synth.point_source(lat.Vh, 0, s, c)).cuda() for s in range(4) for c in range(3)]
+    xs = [torch.empty_like(b) for b in srcs]
+    bqcd.bq_solve_cg_batch([lat.ctx] * 12, xs, srcs, **kw)  # warm
+    st_b, ms_b = _timed(torch, lambda: bqcd.bq_solve_cg_batch([lat.ctx] * 12, xs, srcs, **kw))
+    st_s, ms_s = _timed(torch, lambda: [bqcd.bq_solve_cg(lat.ctx, x, b, **kw) for x, b in zip(xs, srcs)])
+    out["point_sources_12_24^3x48"] = {
+        "batched_ms": ms_b, "sequential_ms": ms_s, "speedup": ms_s / ms_b,
+        "max_true_residual": max(s_["true_residual"] for s_ in st_b),
+        "iterations_max": max(s_["iterations"] for s_ in st_b)}
+    # RHMC multishift: 10 shifts geometric over [1e-4, 1] vs 10 separate CG solves
+    b = torch.from_numpy(synth.gaussian_spinor(lat.Vh, 77)).cuda()
+    shifts = [10.0 ** (-4 + 4 * k / 9) for k in range(10)]
+    xk = [torch.empty_like(b) for _ in shifts]
+    bqcd.bq_solve_multishift_cg(lat.ctx, xk, b, shifts, tol=1e-10, precision="single", delta=1e-3)
+    st_m, ms_m = _timed(torch, lambda: bqcd.bq_solve_multishift_cg(lat.ctx, xk, b, shifts, tol=1e-10,
+                                                                     precision="single", delta=1e-3))
+    st_10, ms_10 = _timed(torch, lambda: [bqcd.bq_solve_cg(lat.ctx, x, b, shift=sh, **kw)
+                                          for x, sh in zip(xk, shifts)])
+    out["multishift_10_24^3x48"] = {"multishift_ms": ms_m, "separate_cg_ms": ms_10, "speedup": ms_10 / ms_m,
+                                    "worst_true_residual": st_m["true_residual"]}
+    lat.close()
+    # ragged: 8^4, 12^4, 16^3x32, 20^3x40 in one batched solve
+    lats, bs, xr = [], [], []
+    for i, dims in enumerate([(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32), (20, 20, 20, 40)]):
+        l = bqcd.Lattice(dims, 0.1350, 1.7, 0.0, -1.0)
+        bqcd.bq_set_gauge(l.ctx, synth.gauge_field(dims, 0.2, 1 + i))
+        bqcd.bq_set_recon(l.ctx, "single", 12)
+        lats.append(l)
+        bs.append(torch.from_numpy(synth.gaussian_spinor(l.Vh, 900 + i)).cuda())
+        xr.append(torch.empty_like(bs[-1]))
+    ctxs = [l.ctx for l in lats]
+    bqcd.bq_solve_cg_batch(ctxs, xr, bs, **kw)
+    st_r, ms_r = _timed(torch, lambda: bqcd.bq_solve_cg_batch(ctxs, xr, bs, **kw))
+    st_q, ms_q = _timed(torch, lambda: [bqcd.bq_solve_cg(c, x, bb, **kw) for c, x, bb in zip(ctxs, xr, bs)])
+    out["ragged_4_lattices"] = {"batched_ms": ms_r, "sequential_ms": ms_q, "speedup": ms_q / ms_r,
+                                "max_true_residual": max(s_["true_residual"] for s_ in st_r)}
+    for l in lats:
+        l.close()
+    return out
 
 
 def extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, mixed_ms, torch, bqcd):
@@ -376,6 +440,14 @@ def extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, mixed_ms, torch, bqcd):
     bqcd.bq_set_recon(ctx, "single", 12)
     bqcd.bq_set_recon(ctx, "half", 12)
     out["dslash_sweep"] = sweep
+
+    for k, v in sweep.items():
+        if k.startswith("double"):
+            # native FP64 is bound by the FP64 units: 1.25 TFLOP/s nominal on GB300
+            v["frac_of_fp64_alu_1250"] = v["GFLOP/s"] / FP64_PEAK_GFLOPS
+
+    # ---- batching (row a9) and multishift (row a8), each against the same work done one system at a time
+    out["batched"] = batched_extras(torch, bqcd)
 
     # ---- CPU oracle on the host cores (bounded sample: 2 Mhat^dag Mhat applies)
     import oracle

@@ -52,6 +52,7 @@ enum {
 enum { BQ_PREC_DOUBLE = 0, BQ_PREC_SINGLE = 1, BQ_PREC_HALF = 2 };
 enum { BQ_RECON_18 = 18, BQ_RECON_12 = 12 };
 enum { BQ_HOST = 0, BQ_DEVICE = 1 };
+enum { BQ_FP64_NATIVE = 0, BQ_FP64_DF64 = 1 };
 
 typedef struct bq_ctx bq_ctx;
 
@@ -118,6 +119,14 @@ int bq_set_params(bq_ctx *ctx, const bq_params *p);
  * (first two rows; the third is rebuilt as conj(row1 x row2), valid for SU(3)
  * links only, so it is refused while a U(1) field is set). */
 int bq_set_recon(bq_ctx *ctx, int precision, int recon);
+
+/* Arithmetic of the FP64-storage operator kernels (D_hop, clover, fused
+ * epilogues): BQ_FP64_NATIVE uses the FP64 units; BQ_FP64_DF64 splits every
+ * loaded double exactly into a pair of floats and computes in double-float
+ * (error-free two-sum / two-product, about 48 significant bits), rounding back
+ * to FP64 on store -- on GB300 FP32 runs at 62x the FP64 rate. Storage, layout
+ * and every other kernel are unchanged; results agree with FP64 to ~1e-14. */
+int bq_set_fp64_arith(bq_ctx *ctx, int mode);
 
 /* Gauge links in canonical layout U[V][4][3][3] complex FP64, from host or
  * device memory (where = BQ_HOST / BQ_DEVICE). Copied; derived fields rebuilt lazily. */
@@ -201,6 +210,21 @@ int bq_apply_mdagm(bq_ctx *ctx, void *out, const void *in, int precision);
 int bq_solve_cg(bq_ctx *ctx, double *x, const double *b, int where,
                 const bq_solver_params *params, bq_solver_stats *stats);
 
+/* Batched CG: nsys systems (Mhat^dagger Mhat + shift) x[i] = b[i] solved in
+ * lockstep, each with its own scalars, convergence and reliable updates
+ * (Section 3 lists block solvers among BQCD's cg family). System i lives on
+ * lattice ctx[i]; systems that share a context pointer share the link and
+ * clover loads of every hopping-term launch (up to 8 right-hand sides per
+ * site in one warp), systems on different contexts (a ragged set of
+ * lattices) share the launches. Every step of an iteration is one kernel
+ * launch for the whole batch, queued on ctx[0]'s stream. All contexts must be
+ * on one device and use the same link storage (bq_set_recon) and FP64
+ * arithmetic mode. x[i], b[i] canonical even spinors of ctx[i] (all host or all
+ * device); stats is an array of nsys entries (may be NULL). Returns
+ * BQ_ERR_NOT_CONVERGED if any system hit max_iter. */
+int bq_solve_cg_batch(bq_ctx *const *ctx, int nsys, double *const *x, const double *const *b, int where,
+                      const bq_solver_params *params, bq_solver_stats *stats);
+
 /* Multishift CG (Section 4 lists multishift cg; the shifted systems of an
  * RHMC rational approximation): solve (Mhat^dag Mhat + shifts[k]) x[k] = b for
  * k < nshift (1..32, shifts >= 0) in ONE Krylov space of the smallest shift,
@@ -208,7 +232,7 @@ int bq_solve_cg(bq_ctx *ctx, double *x, const double *b, int where,
  * FP32: 1e-6, FP16: 1e-3 relative iterated residual), with per-shift
  * zeta/alpha/beta recurrences and per-shift freezing; then every shift is
  * refined by (mixed-precision) CG from that solution to a TRUE FP64 residual
- * <= tol |b|.  x[k] are canonical even spinors (host or device, as b); stats
+ * <= tol |b|, all shifts together as one batched solve.  x[k] are canonical even spinors (host or device, as b); stats
  * sum iterations and Dslash calls over both phases and report the worst true
  * residual; residuals[k] (may be NULL) receives each shift's true residual. */
 int bq_solve_multishift_cg(bq_ctx *ctx, double *const *x, const double *b, int where, int nshift,

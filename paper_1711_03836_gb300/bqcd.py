@@ -22,6 +22,7 @@ BQ_OK, BQ_ERR_ARG, BQ_ERR_CUDA, BQ_ERR_NOT_CONVERGED, BQ_ERR_TIMEOUT, BQ_ERR_CLO
 BQ_PREC_DOUBLE, BQ_PREC_SINGLE, BQ_PREC_HALF = 0, 1, 2
 BQ_RECON_18, BQ_RECON_12 = 18, 12
 BQ_HOST, BQ_DEVICE = 0, 1
+BQ_FP64_NATIVE, BQ_FP64_DF64 = 0, 1
 PREC_NAMES = {"double": 0, "single": 1, "half": 2, 0: 0, 1: 1, 2: 2}
 
 
@@ -79,6 +80,7 @@ _SIGS = {
     "bq_reset_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "bq_get_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(bq_counters)]),
     "bq_set_recon": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "bq_set_fp64_arith": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "bq_set_gauge": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "bq_set_u1": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "bq_build_clover": (ctypes.c_int, [ctypes.c_void_p]),
@@ -97,6 +99,10 @@ _SIGS = {
     "bq_apply_mdagm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "bq_solve_cg": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                    ctypes.POINTER(bq_solver_params), ctypes.POINTER(bq_solver_stats)]),
+    "bq_solve_cg_batch": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.c_int, ctypes.POINTER(bq_solver_params),
+                                         ctypes.POINTER(bq_solver_stats)]),
     "bq_solve_multishift_cg": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
                                               ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(bq_solver_params), ctypes.POINTER(bq_solver_stats),
@@ -182,6 +188,12 @@ def bq_set_recon(ctx, precision, recon):
     _check(_lib_handle().bq_set_recon(ctx, PREC_NAMES[precision], int(recon)), "bq_set_recon")
 
 
+def bq_set_fp64_arith(ctx, mode):
+    """"native" (FP64 units) or "df64" (double-float on the FP32 units) for FP64-storage operator kernels."""
+    m = {"native": BQ_FP64_NATIVE, "df64": BQ_FP64_DF64, 0: 0, 1: 1}[mode]
+    _check(_lib_handle().bq_set_fp64_arith(ctx, m), "bq_set_fp64_arith")
+
+
 def bq_set_gauge(ctx, U):
     p, w = _ptr_where(U)
     _check(_lib_handle().bq_set_gauge(ctx, p, w), "bq_set_gauge")
@@ -264,6 +276,33 @@ def bq_solve_cg(ctx, x, b, tol=1e-10, max_iter=10000, precision="double", delta=
     if s != BQ_OK and (raise_on_nonconvergence or s != BQ_ERR_NOT_CONVERGED):
         raise BqError(s, "bq_solve_cg")
     return st.as_dict()
+
+
+def bq_solve_cg_batch(ctxs, xs, bs, tol=1e-10, max_iter=20000, precision="double", delta=1e-3, check_every=8,
+                      shift=0.0, raise_on_nonconvergence=True):
+    """Solve (Mhat^dag Mhat + shift) xs[i] = bs[i] on lattice ctxs[i] for every i in one batched solve."""
+    n = len(ctxs)
+    if len(xs) != n or len(bs) != n:
+        raise ValueError("one x and one b per system")
+    where = None
+    px, pb = [], []
+    for x, b in zip(xs, bs):
+        p1, w1 = _ptr_where(x)
+        p2, w2 = _ptr_where(b)
+        if w1 != w2 or (where is not None and w1 != where):
+            raise ValueError("all x and b must be host buffers or all device buffers")
+        where = w1
+        px.append(p1)
+        pb.append(p2)
+    carr = (ctypes.c_void_p * n)(*[c.value for c in ctxs])
+    xarr = (ctypes.c_void_p * n)(*px)
+    barr = (ctypes.c_void_p * n)(*pb)
+    sp = bq_solver_params(tol, int(max_iter), PREC_NAMES[precision], delta, int(check_every), shift)
+    st = (bq_solver_stats * n)()
+    s = _lib_handle().bq_solve_cg_batch(carr, n, xarr, barr, where, ctypes.byref(sp), st)
+    if s != BQ_OK and (raise_on_nonconvergence or s != BQ_ERR_NOT_CONVERGED):
+        raise BqError(s, "bq_solve_cg_batch")
+    return [st[i].as_dict() for i in range(n)]
 
 
 def bq_solve_multishift_cg(ctx, xs, b, shifts, tol=1e-10, max_iter=20000, precision="double", delta=1e-3,

@@ -1,0 +1,826 @@
+// bq_batch.cu -- CG and reliable-update mixed-precision CG over a batch of
+// systems (Section 3 lists cg and block multishift cg among BQCD's solvers).
+//
+// A system is one right-hand side on one lattice (a context) with its own
+// shift. All systems iterate in lockstep: every step of an iteration is ONE
+// launch for the whole batch -- the hopping-term steps through a unit table
+// (systems on the same lattice share link loads inside a warp, different
+// lattices get their own block ranges), the BLAS-1 steps with one grid row
+// per system. Each system has its own scalars (alpha, beta, residual norms,
+// computed by the last block of its reduction) and its own flags: `active`
+// (still iterating) and `update` (due for an FP64 residual recomputation).
+// The host reads all residuals every check_every iterations, decides reliable
+// updates and convergence per system, and runs the FP64 update only for the
+// systems that need it.
+//
+// Iteration body: p = rs + beta p; Ap = (Mhat^dag Mhat + sigma) p (4 hopping
+// launches with fused clover epilogues); alpha = rr / <p, Ap>;
+// xs += alpha p, rs -= alpha Ap, rr_new = |rs|^2, beta = rr_new / rr.
+// Reliable update: x += xs, xs = 0, r = b - (Mhat^dag Mhat + sigma) x in FP64,
+// rs = r; the search direction is kept (beta = rr_true / rr_prev) unless the
+// iterated residual had drifted below a quarter of the true one, in which
+// case it restarts (beta = 0).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "bq_reduce.cuh"
+
+struct SysVec {
+    void *b, *x, *r, *t;  // FP64 native
+    void *rs, *xs;        // precision pr
+    void *p, *Ap;         // precision ps
+    int Vh;
+};
+
+struct BArgs {
+    const SysVec *sys;
+    double *scal;          // [nsys][S_NSCAL]
+    double *partials;      // [nsys][2 * RED_MAX_BLOCKS]
+    unsigned int *ticket;  // [nsys]
+    const double *mask;    // [nsys]
+};
+
+#define BATCH_PROLOGUE                                                   \
+    const int sy = blockIdx.y;                                           \
+    if (ba.mask[sy] == 0.0) return;                                      \
+    const SysVec sv = ba.sys[sy];                                        \
+    double *scal = ba.scal + (size_t)sy * S_NSCAL;                       \
+    double *part = ba.partials + (size_t)sy * 2 * RED_MAX_BLOCKS;        \
+    unsigned int *tick = ba.ticket + sy;                                 \
+    const int Vh = sv.Vh;                                                \
+    (void)scal;                                                          \
+    (void)part;                                                          \
+    (void)tick;
+
+// r = b - t - sigma x (use_t) or r = b, x = 0; rs = r, p = r, xs = 0; rr, bb; beta = 0
+template <int PS, int PR>
+__global__ void __launch_bounds__(RED_THREADS) kb_init(BArgs ba, int use_t) {
+    BATCH_PROLOGUE
+    using TR = typename Traits<PR>::real;
+    using TS = typename Traits<PS>::real;
+    const double sigma = scal[S_SIGMA];
+    double v[2] = {0.0, 0.0};
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<double> bv[12], s[12];
+        SpinorIO<BQ_PREC_DOUBLE>::load(bv, sv.b, h, Vh);
+        if (use_t) {
+            cplx<double> tv[12], xv[12];
+            SpinorIO<BQ_PREC_DOUBLE>::load(tv, sv.t, h, Vh);
+            SpinorIO<BQ_PREC_DOUBLE>::load(xv, sv.x, h, Vh);
+#pragma unroll
+            for (int c = 0; c < 12; c++) {
+                s[c].re = bv[c].re - tv[c].re - sigma * xv[c].re;
+                s[c].im = bv[c].im - tv[c].im - sigma * xv[c].im;
+            }
+        } else {
+            cplx<double> z[12];
+#pragma unroll
+            for (int c = 0; c < 12; c++) {
+                s[c] = bv[c];
+                z[c] = {0.0, 0.0};
+            }
+            SpinorIO<BQ_PREC_DOUBLE>::store(sv.x, h, Vh, z);
+        }
+        SpinorIO<BQ_PREC_DOUBLE>::store(sv.r, h, Vh, s);
+        cplx<TR> sr[12], zr[12];
+        cplx<TS> sp[12];
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            sr[c] = {(TR)s[c].re, (TR)s[c].im};
+            zr[c] = {TR(0), TR(0)};
+            sp[c] = {(TS)s[c].re, (TS)s[c].im};
+        }
+        SpinorIO<PR>::store(sv.rs, h, Vh, sr);
+        SpinorIO<PR>::store(sv.xs, h, Vh, zr);
+        SpinorIO<PS>::store(sv.p, h, Vh, sp);
+        v[0] += norm2_site(s);
+        v[1] += norm2_site(bv);
+    }
+    double tot[2];
+    if (grid_sum(v, part, tick, tot) && threadIdx.x == 0) {
+        scal[S_RR] = tot[0];
+        scal[S_BB] = tot[1];
+        scal[S_RRTRUE] = tot[0];
+        scal[S_RRPREV] = tot[0];
+        scal[S_BETA] = 0.0;
+    }
+}
+
+// p = rs + beta p
+template <int PS, int PR>
+__global__ void __launch_bounds__(RED_THREADS) kb_update_p(BArgs ba) {
+    BATCH_PROLOGUE
+    using TS = typename Traits<PS>::real;
+    using TR = typename Traits<PR>::real;
+    const TS beta = (TS)scal[S_BETA];
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<TS> a[12];
+        cplx<TR> rv[12];
+        SpinorIO<PS>::load(a, sv.p, h, Vh);
+        SpinorIO<PR>::load(rv, sv.rs, h, Vh);
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            a[c].re = fma(beta, a[c].re, (TS)rv[c].re);
+            a[c].im = fma(beta, a[c].im, (TS)rv[c].im);
+        }
+        SpinorIO<PS>::store(sv.p, h, Vh, a);
+    }
+}
+
+// Ap += sigma p; pAp = Re <p, Ap>; alpha = rr / pAp
+template <int PS>
+__global__ void __launch_bounds__(RED_THREADS) kb_pap(BArgs ba) {
+    BATCH_PROLOGUE
+    using T = typename Traits<PS>::real;
+    const double sigma = scal[S_SIGMA];
+    double v[1] = {0.0};
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<T> a[12], q[12];
+        SpinorIO<PS>::load(a, sv.p, h, Vh);
+        SpinorIO<PS>::load(q, sv.Ap, h, Vh);
+        if (sigma != 0.0) {
+#pragma unroll
+            for (int c = 0; c < 12; c++) {
+                q[c].re = fma((T)sigma, a[c].re, q[c].re);
+                q[c].im = fma((T)sigma, a[c].im, q[c].im);
+            }
+            SpinorIO<PS>::store(sv.Ap, h, Vh, q);
+        }
+        T d = T(0);
+#pragma unroll
+        for (int c = 0; c < 12; c++) d += a[c].re * q[c].re + a[c].im * q[c].im;
+        v[0] += (double)d;
+    }
+    double tot[1];
+    if (grid_sum(v, part, tick, tot) && threadIdx.x == 0) {
+        scal[S_PAP] = tot[0];
+        scal[S_ALPHA] = scal[S_RR] / tot[0];
+    }
+}
+
+// xs += alpha p; rs -= alpha Ap; rr_new = |rs|^2; beta = rr_new / rr
+template <int PS, int PR>
+__global__ void __launch_bounds__(RED_THREADS) kb_update_xr(BArgs ba) {
+    BATCH_PROLOGUE
+    using TS = typename Traits<PS>::real;
+    using TR = typename Traits<PR>::real;
+    const TR alpha = (TR)scal[S_ALPHA];
+    double v[1] = {0.0};
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<TS> a[12], q[12];
+        cplx<TR> xv[12], rv[12];
+        SpinorIO<PS>::load(a, sv.p, h, Vh);
+        SpinorIO<PS>::load(q, sv.Ap, h, Vh);
+        SpinorIO<PR>::load(xv, sv.xs, h, Vh);
+        SpinorIO<PR>::load(rv, sv.rs, h, Vh);
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            xv[c].re = fma(alpha, (TR)a[c].re, xv[c].re);
+            xv[c].im = fma(alpha, (TR)a[c].im, xv[c].im);
+            rv[c].re = fma(-alpha, (TR)q[c].re, rv[c].re);
+            rv[c].im = fma(-alpha, (TR)q[c].im, rv[c].im);
+        }
+        SpinorIO<PR>::store(sv.xs, h, Vh, xv);
+        SpinorIO<PR>::store(sv.rs, h, Vh, rv);
+        v[0] += norm2_site(rv);
+    }
+    double tot[1];
+    if (grid_sum(v, part, tick, tot) && threadIdx.x == 0) {
+        const double rr = scal[S_RR];
+        scal[S_RRPREV] = rr;
+        scal[S_RR] = tot[0];
+        scal[S_BETA] = tot[0] / rr;
+    }
+}
+
+// x += xs; xs = 0 (x FP64)
+template <int PR>
+__global__ void __launch_bounds__(RED_THREADS) kb_promote(BArgs ba) {
+    BATCH_PROLOGUE
+    using TR = typename Traits<PR>::real;
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<double> xv[12];
+        cplx<TR> d[12];
+        SpinorIO<BQ_PREC_DOUBLE>::load(xv, sv.x, h, Vh);
+        SpinorIO<PR>::load(d, sv.xs, h, Vh);
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            xv[c].re += (double)d[c].re;
+            xv[c].im += (double)d[c].im;
+            d[c] = {TR(0), TR(0)};
+        }
+        SpinorIO<BQ_PREC_DOUBLE>::store(sv.x, h, Vh, xv);
+        SpinorIO<PR>::store(sv.xs, h, Vh, d);
+    }
+}
+
+// r = b - t - sigma x (FP64), rs = r, rr_true = |r|^2; beta for the kept direction
+template <int PR>
+__global__ void __launch_bounds__(RED_THREADS) kb_residual(BArgs ba) {
+    BATCH_PROLOGUE
+    using TR = typename Traits<PR>::real;
+    const double sigma = scal[S_SIGMA];
+    double v[1] = {0.0};
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<double> bv[12], tv[12], xv[12];
+        SpinorIO<BQ_PREC_DOUBLE>::load(bv, sv.b, h, Vh);
+        SpinorIO<BQ_PREC_DOUBLE>::load(tv, sv.t, h, Vh);
+        SpinorIO<BQ_PREC_DOUBLE>::load(xv, sv.x, h, Vh);
+        cplx<TR> sr[12];
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            bv[c].re = bv[c].re - tv[c].re - sigma * xv[c].re;
+            bv[c].im = bv[c].im - tv[c].im - sigma * xv[c].im;
+            sr[c] = {(TR)bv[c].re, (TR)bv[c].im};
+        }
+        SpinorIO<BQ_PREC_DOUBLE>::store(sv.r, h, Vh, bv);
+        SpinorIO<PR>::store(sv.rs, h, Vh, sr);
+        v[0] += norm2_site(bv);
+    }
+    double tot[1];
+    if (grid_sum(v, part, tick, tot) && threadIdx.x == 0) {
+        const double rr_iter = scal[S_RR];
+        scal[S_RRTRUE] = tot[0];
+        scal[S_RR] = tot[0];
+        scal[S_BETA] = (tot[0] > 4.0 * rr_iter) ? 0.0 : tot[0] / scal[S_RRPREV];
+    }
+}
+
+// --------------------------------------------------------------------------
+// workspace: per-system vectors cached in the first context, reused across calls
+
+struct BatchSlot {
+    int Vh, ps, pr;
+    char *b, *x, *r, *t, *rs, *xs, *p, *Ap, *to_s, *te_s, *to_d;
+};
+
+struct BatchWork {
+    int cap;            // slots allocated
+    BatchSlot *slot;    // [cap]
+    int dev_cap;        // device tables sized for this many systems / units
+    SysVec *d_sys;
+    double *d_scal, *d_part, *d_flags;
+    unsigned int *d_ticket;
+    DslashUnit *d_units;  // [8 steps][dev_cap units]
+    int *d_block0;        // [8 steps][dev_cap + 1]
+    double *h_scal, *h_flags;  // pinned mirrors
+    double *stage;             // canonical staging for host spinors
+    size_t stage_bytes;
+    DslashUnit *h_units;       // host mirror of d_units
+    int h_units_cap;
+    cudaEvent_t e0, e1;
+};
+
+static void free_slot(BatchSlot *s) {
+    cudaFree(s->b);
+    cudaFree(s->x);
+    cudaFree(s->r);
+    cudaFree(s->t);
+    cudaFree(s->rs);
+    cudaFree(s->xs);
+    cudaFree(s->p);
+    cudaFree(s->Ap);
+    cudaFree(s->to_s);
+    cudaFree(s->te_s);
+    cudaFree(s->to_d);
+    memset(s, 0, sizeof *s);
+}
+
+void bq_batch_free(bq_ctx *c) {
+    BatchWork *w = c->batch;
+    if (!w) return;
+    for (int i = 0; i < w->cap; i++) free_slot(&w->slot[i]);
+    free(w->slot);
+    cudaFree(w->d_sys);
+    cudaFree(w->d_scal);
+    cudaFree(w->d_part);
+    cudaFree(w->d_flags);
+    cudaFree(w->d_ticket);
+    cudaFree(w->d_units);
+    cudaFree(w->d_block0);
+    cudaFreeHost(w->h_scal);
+    cudaFreeHost(w->h_flags);
+    cudaFree(w->stage);
+    free(w->h_units);
+    if (w->e0) cudaEventDestroy(w->e0);
+    if (w->e1) cudaEventDestroy(w->e1);
+    free(w);
+    c->batch = nullptr;
+}
+
+// make slots [0, nsys) hold vectors for ctxs[s] at (ps, pr)
+int bq_batch_reserve(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int pr) {
+    if (!c0->batch) {
+        c0->batch = (BatchWork *)calloc(1, sizeof(BatchWork));
+        if (!c0->batch) return BQ_ERR_NOMEM;
+        BQ_CUDA_TRY(cudaEventCreate(&c0->batch->e0));
+        BQ_CUDA_TRY(cudaEventCreate(&c0->batch->e1));
+    }
+    BatchWork *w = c0->batch;
+    if (w->cap < nsys) {
+        BatchSlot *ns = (BatchSlot *)calloc(nsys, sizeof(BatchSlot));
+        if (!ns) return BQ_ERR_NOMEM;
+        if (w->slot) memcpy(ns, w->slot, sizeof(BatchSlot) * w->cap);
+        free(w->slot);
+        w->slot = ns;
+        w->cap = nsys;
+    }
+    for (int s = 0; s < nsys; s++) {
+        BatchSlot *sl = &w->slot[s];
+        const int Vh = ctxs[s]->Vh;
+        if (sl->b && (sl->Vh != Vh || sl->ps != ps || sl->pr != pr)) free_slot(sl);
+        if (sl->b) continue;
+        const size_t v64 = spinor_bytes_per_site(BQ_PREC_DOUBLE) * (size_t)Vh;
+        const size_t vr = spinor_bytes_per_site(pr) * (size_t)Vh, vs = spinor_bytes_per_site(ps) * (size_t)Vh;
+        BQ_TRY(bq_alloc((void **)&sl->b, v64));
+        BQ_TRY(bq_alloc((void **)&sl->x, v64));
+        BQ_TRY(bq_alloc((void **)&sl->r, v64));
+        BQ_TRY(bq_alloc((void **)&sl->t, v64));
+        BQ_TRY(bq_alloc((void **)&sl->to_d, v64));
+        BQ_TRY(bq_alloc((void **)&sl->rs, vr));
+        BQ_TRY(bq_alloc((void **)&sl->xs, vr));
+        BQ_TRY(bq_alloc((void **)&sl->p, vs));
+        BQ_TRY(bq_alloc((void **)&sl->Ap, vs));
+        BQ_TRY(bq_alloc((void **)&sl->to_s, vs));
+        BQ_TRY(bq_alloc((void **)&sl->te_s, vs));
+        sl->Vh = Vh;
+        sl->ps = ps;
+        sl->pr = pr;
+    }
+    if (w->dev_cap < nsys) {
+        cudaFree(w->d_sys);
+        cudaFree(w->d_scal);
+        cudaFree(w->d_part);
+        cudaFree(w->d_flags);
+        cudaFree(w->d_ticket);
+        cudaFree(w->d_units);
+        cudaFree(w->d_block0);
+        cudaFreeHost(w->h_scal);
+        cudaFreeHost(w->h_flags);
+        w->d_sys = nullptr;
+        w->d_scal = w->d_part = w->d_flags = nullptr;
+        w->d_ticket = nullptr;
+        w->d_units = nullptr;
+        w->d_block0 = nullptr;
+        w->h_scal = w->h_flags = nullptr;
+        BQ_TRY(bq_alloc((void **)&w->d_sys, sizeof(SysVec) * nsys));
+        BQ_TRY(bq_alloc((void **)&w->d_scal, sizeof(double) * S_NSCAL * nsys));
+        BQ_TRY(bq_alloc((void **)&w->d_part, sizeof(double) * 2 * RED_MAX_BLOCKS * nsys));
+        BQ_TRY(bq_alloc((void **)&w->d_flags, sizeof(double) * 2 * nsys));
+        BQ_TRY(bq_alloc((void **)&w->d_ticket, sizeof(unsigned int) * nsys));
+        BQ_TRY(bq_alloc((void **)&w->d_units, sizeof(DslashUnit) * 8 * nsys));
+        BQ_TRY(bq_alloc((void **)&w->d_block0, sizeof(int) * 8 * (nsys + 1)));
+        BQ_CUDA_TRY(cudaMallocHost((void **)&w->h_scal, sizeof(double) * S_NSCAL * nsys));
+        BQ_CUDA_TRY(cudaMallocHost((void **)&w->h_flags, sizeof(double) * 2 * nsys));
+        BQ_CUDA_TRY(cudaMemsetAsync(w->d_ticket, 0, sizeof(unsigned int) * nsys, c0->stream));
+        w->dev_cap = nsys;
+    }
+    return BQ_OK;
+}
+
+BatchSlot *bq_batch_slot(bq_ctx *c0, int s) { return &c0->batch->slot[s]; }
+void *bq_batch_slot_b(bq_ctx *c0, int s) { return c0->batch->slot[s].b; }
+void *bq_batch_slot_x(bq_ctx *c0, int s) { return c0->batch->slot[s].x; }
+
+// --------------------------------------------------------------------------
+// unit tables of the two Mhat^dag Mhat applications (sloppy p -> Ap, FP64 x -> t)
+
+struct UnitPlan {
+    int nunits[8];
+    int nblocks[8];
+    double bytes_all[8];  // algorithmic bytes of each step with every system active
+    double flops_all[8];
+};
+
+static int log2_ceil(int n) {
+    int l = 0;
+    while ((1 << l) < n) l++;
+    return l;
+}
+
+// steps 0-3 sloppy (prec ps), 4-7 FP64: D_oe+A^-1, A x - k D_eo, and the two adjoint ones
+static int build_units(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int rhs_per_unit, UnitPlan *plan,
+                       DslashUnit *h_units, int *h_block0) {
+    BatchWork *w = c0->batch;
+    for (int step = 0; step < 8; step++) {
+        const int prec = step < 4 ? ps : BQ_PREC_DOUBLE;
+        const int k = step & 3;
+        const int parity = (k == 0 || k == 2) ? 1 : 0;
+        const int dagger = k >= 2;
+        const int epi = parity == 1 ? EPI_CLOVINV : EPI_XPAY;
+        DslashUnit *U = h_units + step * nsys;
+        int *B0 = h_block0 + step * (nsys + 1);
+        int nu = 0, blocks = 0;
+        double bytes = 0, flops = 0;
+        int s = 0;
+        while (s < nsys) {
+            // the run of systems on the same lattice, cut into units of rhs_per_unit
+            int e = s + 1;
+            while (e < nsys && ctxs[e] == ctxs[s] && e - s < rhs_per_unit) e++;
+            bq_ctx *c = ctxs[s];
+            const double kk = c->params.kappa * c->params.kappa;
+            DslashUnit *u = &U[nu];
+            memset(u, 0, sizeof *u);
+            BQ_TRY(bq_dslash_unit_fill(c, prec, parity, dagger, epi, kk, &u->a));
+            u->nr = e - s;
+            u->log2R = log2_ceil(u->nr);
+            for (int q = 0; q < u->nr; q++) {
+                BatchSlot *sl = &w->slot[s + q];
+                void *sin, *sout, *sx;
+                if (step < 4) {
+                    void *pv[4][3] = {{sl->p, sl->to_s, nullptr},
+                                      {sl->to_s, sl->te_s, sl->p},
+                                      {sl->te_s, sl->to_s, nullptr},
+                                      {sl->to_s, sl->Ap, sl->te_s}};
+                    sin = pv[k][0];
+                    sout = pv[k][1];
+                    sx = pv[k][2];
+                } else {
+                    void *pv[4][3] = {{sl->x, sl->to_d, nullptr},
+                                      {sl->to_d, sl->r, sl->x},
+                                      {sl->r, sl->to_d, nullptr},
+                                      {sl->to_d, sl->t, sl->r}};
+                    sin = pv[k][0];
+                    sout = pv[k][1];
+                    sx = pv[k][2];
+                }
+                u->in[q] = sin;
+                u->out[q] = sout;
+                u->xin[q] = sx;
+                u->sys[q] = s + q;
+            }
+            B0[nu] = blocks;
+            blocks += (int)(((long long)c->Vh * (1 << u->log2R) + 127) / 128);
+            // links and clover once per site of the unit, spinors per rhs
+            const int recon = c->links_recon[prec];
+            const double shared = 8.0 * link_bytes_per_link(prec, recon) + clover_bytes_per_site(prec);
+            const double per_rhs = dslash_site_bytes(prec, recon, epi) - shared;
+            bytes += (shared + per_rhs * u->nr) * (double)c->Vh;
+            flops += dslash_site_flops(epi) * u->nr * (double)c->Vh;
+            nu++;
+            s = e;
+        }
+        B0[nu] = blocks;
+        plan->nunits[step] = nu;
+        plan->nblocks[step] = blocks;
+        plan->bytes_all[step] = bytes;
+        plan->flops_all[step] = flops;
+    }
+    return BQ_OK;
+}
+
+static int mdagm_batch(bq_ctx *c0, int prec, int recon, int first_step, const UnitPlan *plan, int nsys,
+                       const double *mask_dev, double active_fraction) {
+    BatchWork *w = c0->batch;
+    for (int k = 0; k < 4; k++) {
+        const int step = first_step + k;
+        const int parity = (k == 0 || k == 2) ? 1 : 0;
+        const int dagger = k >= 2;
+        const int epi = parity == 1 ? EPI_CLOVINV : EPI_XPAY;
+        if (nsys == 1) {
+            // a single system: the plain kernel, no unit indirection (it is
+            // active whenever this runs: the loop stops at convergence)
+            const DslashUnit &u = w->h_units[step * nsys];
+            BQ_TRY(bq_dslash_launch(c0, prec, u.out[0], u.in[0], parity, dagger, epi, u.xin[0], u.a.k));
+            continue;
+        }
+        BQ_TRY(bq_dslash_batch_launch(c0, prec, recon, w->d_units + step * nsys, w->d_block0 + step * (nsys + 1),
+                                      plan->nunits[step], plan->nblocks[step], mask_dev, dagger, epi,
+                                      plan->bytes_all[step] * active_fraction,
+                                      plan->flops_all[step] * active_fraction));
+    }
+    return BQ_OK;
+}
+
+// --------------------------------------------------------------------------
+// the batched solver core
+
+template <int PS, int PR>
+static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double *shifts,
+                        const bq_solver_params *sp, bool have_x0, int rhs_per_unit, bq_solver_stats *st) {
+    BatchWork *w = c0->batch;
+    cudaStream_t s = c0->stream;
+    const int recon_s = ctxs[0]->links_recon[PS], recon_d = ctxs[0]->links_recon[BQ_PREC_DOUBLE];
+    int maxVh = 0;
+    for (int i = 0; i < nsys; i++) maxVh = ctxs[i]->Vh > maxVh ? ctxs[i]->Vh : maxVh;
+    const dim3 G(red_grid(maxVh), nsys);
+
+    // device tables
+    SysVec *hs = (SysVec *)calloc(nsys, sizeof(SysVec));
+    if (w->h_units_cap < 8 * nsys) {
+        free(w->h_units);
+        w->h_units = (DslashUnit *)calloc(8 * nsys, sizeof(DslashUnit));
+        w->h_units_cap = w->h_units ? 8 * nsys : 0;
+    }
+    DslashUnit *hu = w->h_units;
+    int *hb = (int *)calloc(8 * (nsys + 1), sizeof(int));
+    double *hscal = (double *)calloc((size_t)S_NSCAL * nsys, sizeof(double));
+    if (!hs || !hu || !hb || !hscal) {
+        free(hs);
+        free(hb);
+        free(hscal);
+        return BQ_ERR_NOMEM;
+    }
+    for (int i = 0; i < nsys; i++) {
+        BatchSlot *sl = &w->slot[i];
+        hs[i] = SysVec{sl->b, sl->x, sl->r, sl->t, sl->rs, sl->xs, sl->p, sl->Ap, sl->Vh};
+        hscal[(size_t)i * S_NSCAL + S_SIGMA] = shifts ? shifts[i] : sp->shift;
+    }
+    UnitPlan plan;
+    int status = build_units(c0, nsys, ctxs, PS, rhs_per_unit, &plan, hu, hb);
+    if (status == BQ_OK) {
+        if (cudaMemcpyAsync(w->d_sys, hs, sizeof(SysVec) * nsys, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(w->d_units, hu, sizeof(DslashUnit) * 8 * nsys, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(w->d_block0, hb, sizeof(int) * 8 * (nsys + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(w->d_scal, hscal, sizeof(double) * S_NSCAL * nsys, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            bq_set_error("batched CG: table upload failed");
+            status = BQ_ERR_CUDA;
+        }
+    }
+    free(hs);
+    free(hb);
+    free(hscal);
+    if (status != BQ_OK) return status;
+
+    double *active = w->h_flags, *update = w->h_flags + nsys;
+    double *d_active = w->d_flags, *d_update = w->d_flags + nsys;
+    auto upload_flags = [&]() -> int {
+        BQ_CUDA_TRY(cudaMemcpyAsync(w->d_flags, w->h_flags, sizeof(double) * 2 * nsys, cudaMemcpyHostToDevice, s));
+        return BQ_OK;
+    };
+    auto read_scal = [&]() -> int {
+        BQ_CUDA_TRY(cudaMemcpyAsync(w->h_scal, w->d_scal, sizeof(double) * S_NSCAL * nsys, cudaMemcpyDeviceToHost, s));
+        BQ_CUDA_TRY(cudaStreamSynchronize(s));
+        return BQ_OK;
+    };
+    const BArgs ba_act{w->d_sys, w->d_scal, w->d_part, w->d_ticket, d_active};
+    const BArgs ba_upd{w->d_sys, w->d_scal, w->d_part, w->d_ticket, d_update};
+
+    for (int i = 0; i < nsys; i++) {
+        active[i] = 1.0;
+        update[i] = have_x0 ? 1.0 : 0.0;
+        memset(&st[i], 0, sizeof st[i]);
+    }
+    BQ_TRY(upload_flags());
+    if (have_x0) {
+        BQ_TRY(mdagm_batch(c0, BQ_PREC_DOUBLE, recon_d, 4, &plan, nsys, d_update, 1.0));
+        for (int i = 0; i < nsys; i++) {
+            update[i] = 0.0;
+            st[i].dslash_calls = 4;
+        }
+        BQ_TRY(upload_flags());
+    }
+    kb_init<PS, PR><<<G, RED_THREADS, 0, s>>>(ba_act, have_x0 ? 1 : 0);
+    BQ_COUNT(c0);
+    BQ_LAUNCH_CHECK();
+    BQ_TRY(read_scal());
+    std::vector<double> bb(nsys), maxrr(nsys), rrtrue(nsys);
+    int nactive = 0;
+    for (int i = 0; i < nsys; i++) {
+        const double *sc = w->h_scal + (size_t)i * S_NSCAL;
+        bb[i] = sc[S_BB];
+        rrtrue[i] = maxrr[i] = sc[S_RR];
+        if (bb[i] == 0.0 || rrtrue[i] <= sp->tol * sp->tol * bb[i]) {
+            active[i] = 0.0;
+            st[i].converged = 1;
+            st[i].true_residual = bb[i] == 0.0 ? 0.0 : sqrt(rrtrue[i] / bb[i]);
+        } else {
+            nactive++;
+        }
+    }
+    BQ_TRY(upload_flags());
+    const double delta = (PS == BQ_PREC_DOUBLE) ? 0.0 : sp->delta;
+    const int check = sp->check_every > 0 ? sp->check_every : 1;
+    int it = 0;
+    status = BQ_OK;
+    while (nactive > 0) {
+        const double frac = (double)nactive / nsys;
+        kb_update_p<PS, PR><<<G, RED_THREADS, 0, s>>>(ba_act);
+        BQ_COUNT(c0);
+        BQ_TRY(mdagm_batch(c0, PS, recon_s, 0, &plan, nsys, d_active, frac));
+        kb_pap<PS><<<G, RED_THREADS, 0, s>>>(ba_act);
+        BQ_COUNT(c0);
+        kb_update_xr<PS, PR><<<G, RED_THREADS, 0, s>>>(ba_act);
+        BQ_COUNT(c0);
+        BQ_LAUNCH_CHECK();
+        it++;
+        for (int i = 0; i < nsys; i++)
+            if (active[i] != 0.0) {
+                st[i].iterations++;
+                st[i].dslash_calls += 4;
+            }
+        if (it % check != 0 && it < sp->max_iter) continue;
+        BQ_TRY(read_scal());
+        int nupd = 0;
+        for (int i = 0; i < nsys; i++) {
+            if (active[i] == 0.0) continue;
+            const double rr = w->h_scal[(size_t)i * S_NSCAL + S_RR];
+            if (!(rr == rr)) {
+                bq_set_error("batched CG: system %d residual is NaN", i);
+                return BQ_ERR_NOT_CONVERGED;
+            }
+            if (rr > maxrr[i]) maxrr[i] = rr;
+            if (rr < delta * delta * maxrr[i] || rr <= sp->tol * sp->tol * bb[i] || it >= sp->max_iter) {
+                update[i] = 1.0;
+                nupd++;
+            }
+        }
+        if (nupd) {
+            BQ_TRY(upload_flags());
+            kb_promote<PR><<<G, RED_THREADS, 0, s>>>(ba_upd);
+            BQ_COUNT(c0);
+            BQ_TRY(mdagm_batch(c0, BQ_PREC_DOUBLE, recon_d, 4, &plan, nsys, d_update, (double)nupd / nsys));
+            kb_residual<PR><<<G, RED_THREADS, 0, s>>>(ba_upd);
+            BQ_COUNT(c0);
+            BQ_LAUNCH_CHECK();
+            BQ_TRY(read_scal());
+            for (int i = 0; i < nsys; i++) {
+                if (update[i] == 0.0) continue;
+                update[i] = 0.0;
+                st[i].reliable_updates++;
+                st[i].dslash_calls += 4;
+                rrtrue[i] = w->h_scal[(size_t)i * S_NSCAL + S_RRTRUE];
+                maxrr[i] = rrtrue[i];
+                st[i].true_residual = sqrt(rrtrue[i] / bb[i]);
+                if (rrtrue[i] <= sp->tol * sp->tol * bb[i]) {
+                    st[i].converged = 1;
+                    active[i] = 0.0;
+                    nactive--;
+                } else if (it >= sp->max_iter) {
+                    active[i] = 0.0;
+                    nactive--;
+                }
+            }
+            BQ_TRY(upload_flags());
+        }
+    }
+    return status;
+}
+
+static int cg_batch_dispatch(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double *shifts,
+                             const bq_solver_params *sp, bool have_x0, int rhs_per_unit, bq_solver_stats *st) {
+    if (sp->precision == BQ_PREC_DOUBLE)
+        return cg_batch_run<BQ_PREC_DOUBLE, BQ_PREC_DOUBLE>(c0, nsys, ctxs, shifts, sp, have_x0, rhs_per_unit, st);
+    if (sp->precision == BQ_PREC_SINGLE)
+        return cg_batch_run<BQ_PREC_SINGLE, BQ_PREC_SINGLE>(c0, nsys, ctxs, shifts, sp, have_x0, rhs_per_unit, st);
+    return cg_batch_run<BQ_PREC_HALF, BQ_PREC_SINGLE>(c0, nsys, ctxs, shifts, sp, have_x0, rhs_per_unit, st);
+}
+
+// check a batch: same sloppy recon and FP64 arithmetic everywhere; fields prepared
+static int batch_prepare(int nsys, bq_ctx *const *ctxs, int ps) {
+    for (int i = 0; i < nsys; i++) {
+        bq_ctx *c = ctxs[i];
+        if (!c) {
+            bq_set_error("batched CG: null context %d", i);
+            return BQ_ERR_ARG;
+        }
+        if (!c->have_gauge) {
+            bq_set_error("batched CG: gauge field of system %d not set", i);
+            return BQ_ERR_STATE;
+        }
+        if (c->recon[ps] != ctxs[0]->recon[ps] || c->recon[BQ_PREC_DOUBLE] != ctxs[0]->recon[BQ_PREC_DOUBLE] ||
+            c->fp64_arith != ctxs[0]->fp64_arith) {
+            bq_set_error("batched CG: system %d uses a different link storage or FP64 arithmetic", i);
+            return BQ_ERR_ARG;
+        }
+        if (i > 0 && c->device != ctxs[0]->device) {
+            bq_set_error("batched CG: all contexts must be on one device");
+            return BQ_ERR_ARG;
+        }
+        BQ_TRY(bq_prepare_links(c, BQ_PREC_DOUBLE));
+        BQ_TRY(bq_prepare_clover(c, BQ_PREC_DOUBLE));
+        BQ_TRY(bq_prepare_links(c, ps));
+        BQ_TRY(bq_prepare_clover(c, ps));
+        // field preparation ran on this context's stream; the batch runs on ctx[0]'s
+        if (c->stream != ctxs[0]->stream) BQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    return BQ_OK;
+}
+
+static int check_solver_params(const bq_solver_params *sp) {
+    if (!sp) return BQ_ERR_ARG;
+    int ps = sp->precision;
+    if (!(ps == BQ_PREC_DOUBLE || ps == BQ_PREC_SINGLE || ps == BQ_PREC_HALF) || !(sp->tol > 0) ||
+        sp->max_iter < 1 || !(sp->shift >= 0) || sp->delta < 0 || sp->delta >= 1) {
+        bq_set_error("bad solver parameters");
+        return BQ_ERR_ARG;
+    }
+    return BQ_OK;
+}
+
+// Internal entry for the multishift refinement: systems already hold b (FP64
+// native) and x (initial guess) in slots [0, nsys) of c0's batch workspace.
+int bq_cg_batch_core(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double *shifts, const bq_solver_params *sp,
+                     bool have_x0, bq_solver_stats *st) {
+    const int rpu = nsys < DSLASH_UNIT_RHS ? nsys : DSLASH_UNIT_RHS;
+    return cg_batch_dispatch(c0, nsys, ctxs, shifts, sp, have_x0, rpu, st);
+}
+
+extern "C" int bq_solve_cg_batch(bq_ctx *const *ctxs, int nsys, double *const *x, const double *const *b, int where,
+                                 const bq_solver_params *sp, bq_solver_stats *stats) {
+    if (!ctxs || nsys < 1 || !x || !b || !(where == BQ_HOST || where == BQ_DEVICE)) {
+        bq_set_error("bq_solve_cg_batch: bad arguments");
+        return BQ_ERR_ARG;
+    }
+    BQ_TRY(check_solver_params(sp));
+    for (int i = 0; i < nsys; i++)
+        if (!x[i] || !b[i]) {
+            bq_set_error("bq_solve_cg_batch: null spinor for system %d", i);
+            return BQ_ERR_ARG;
+        }
+    const int ps = sp->precision, pr = (ps == BQ_PREC_HALF) ? BQ_PREC_SINGLE : ps;
+    BQ_TRY(batch_prepare(nsys, ctxs, ps));
+    bq_ctx *c0 = ctxs[0];
+    BQ_TRY(bq_batch_reserve(c0, nsys, ctxs, ps, pr));
+    bq_solver_stats *st = stats;
+    bq_solver_stats *local = nullptr;
+    if (!st) {
+        local = (bq_solver_stats *)calloc(nsys, sizeof(bq_solver_stats));
+        if (!local) return BQ_ERR_NOMEM;
+        st = local;
+    }
+    BatchWork *w = c0->batch;
+    int status = BQ_OK;
+    if (cudaEventRecord(w->e0, c0->stream) != cudaSuccess) status = BQ_ERR_CUDA;
+    // b into the slots (through c0's stream, staging host data per system)
+    if (where == BQ_HOST) {
+        size_t need = 0;
+        for (int i = 0; i < nsys; i++) need = (size_t)ctxs[i]->Vh * 192 > need ? (size_t)ctxs[i]->Vh * 192 : need;
+        if (w->stage_bytes < need) {
+            cudaFree(w->stage);
+            w->stage = nullptr;
+            w->stage_bytes = 0;
+            status = bq_alloc((void **)&w->stage, need);
+            if (status == BQ_OK) w->stage_bytes = need;
+        }
+    }
+    for (int i = 0; i < nsys && status == BQ_OK; i++) {
+        bq_ctx *c = ctxs[i];
+        const double *src = b[i];
+        if (where == BQ_HOST) {
+            if (cudaMemcpyAsync(w->stage, b[i], (size_t)c->Vh * 192, cudaMemcpyHostToDevice, c0->stream) !=
+                cudaSuccess)
+                status = BQ_ERR_CUDA;
+            src = w->stage;
+        }
+        if (status == BQ_OK) {
+            cudaStream_t keep = c->stream;
+            c->stream = c0->stream;
+            status = bq_pack(c, w->slot[i].b, src, BQ_PREC_DOUBLE);
+            c->stream = keep;
+        }
+    }
+    if (status == BQ_OK) {
+        const int rpu = nsys < DSLASH_UNIT_RHS ? nsys : DSLASH_UNIT_RHS;
+        status = cg_batch_dispatch(c0, nsys, ctxs, nullptr, sp, false, rpu, st);
+    }
+    for (int i = 0; i < nsys && (status == BQ_OK || status == BQ_ERR_NOT_CONVERGED); i++) {
+        bq_ctx *c = ctxs[i];
+        cudaStream_t keep = c->stream;
+        c->stream = c0->stream;
+        int s2;
+        if (where == BQ_DEVICE) {
+            s2 = bq_unpack(c, x[i], w->slot[i].x, BQ_PREC_DOUBLE);
+        } else {
+            s2 = bq_unpack(c, w->stage, w->slot[i].x, BQ_PREC_DOUBLE);
+            if (s2 == BQ_OK && cudaMemcpyAsync(x[i], w->stage, (size_t)c->Vh * 192, cudaMemcpyDeviceToHost,
+                                               c0->stream) != cudaSuccess)
+                s2 = BQ_ERR_CUDA;
+            if (s2 == BQ_OK && cudaStreamSynchronize(c0->stream) != cudaSuccess) s2 = BQ_ERR_CUDA;
+        }
+        c->stream = keep;
+        if (s2 != BQ_OK) status = s2;
+    }
+    if (status == BQ_OK || status == BQ_ERR_NOT_CONVERGED) {
+        float ms = 0.f;
+        if (cudaEventRecord(w->e1, c0->stream) == cudaSuccess && cudaEventSynchronize(w->e1) == cudaSuccess)
+            cudaEventElapsedTime(&ms, w->e0, w->e1);
+        for (int i = 0; i < nsys; i++) st[i].seconds = ms * 1e-3;
+        if (status == BQ_OK)
+            for (int i = 0; i < nsys; i++)
+                if (!st[i].converged) {
+                    bq_set_error("CG reached max_iter=%d; system %d true residual %.3e", sp->max_iter, i,
+                                 st[i].true_residual);
+                    status = BQ_ERR_NOT_CONVERGED;
+                    break;
+                }
+    }
+    free(local);
+    return status;
+}
+
+extern "C" int bq_solve_cg(bq_ctx *c, double *x, const double *b, int where, const bq_solver_params *sp,
+                           bq_solver_stats *st) {
+    if (!c || !x || !b) {
+        bq_set_error("bq_solve_cg: bad arguments");
+        return BQ_ERR_ARG;
+    }
+    bq_ctx *ctxs[1] = {c};
+    double *xs[1] = {x};
+    const double *bs[1] = {b};
+    return bq_solve_cg_batch(ctxs, 1, xs, bs, where, sp, st);
+}

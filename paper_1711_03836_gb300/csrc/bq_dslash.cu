@@ -15,19 +15,6 @@
 
 #include "bq_internal.cuh"
 
-struct DslashArgs {
-    void *out;
-    const void *in;
-    const char *links;
-    size_t lblk;  // bytes of one (parity, mu) link block
-    const void *clov;
-    const void *xin;
-    int L0, L1, L2, L3, Lxh, Vh, parity;
-    double cf, cb;  // time-hop factors forward / backward (e^{+mu}, e^{-mu}; swapped for the adjoint)
-    double bc;      // time boundary sign
-    double k;       // xpay coefficient
-};
-
 // (1 + S gamma_mu) psi = (h0, h1, ...) in the chiral basis: the projection ...
 template <int MU, int S, typename T>
 __device__ __forceinline__ void project(const cplx<T> p[12], cplx<T> h0[3], cplx<T> h1[3]) {
@@ -107,10 +94,8 @@ __device__ __forceinline__ void hop(cplx<typename Traits<PREC>::real> acc[12], c
 }
 
 template <int PREC, int RECON, bool DAG, int EPI>
-__global__ void __launch_bounds__(128) k_dslash(const DslashArgs a) {
+__device__ __forceinline__ void dslash_site(const DslashArgs &a, const int h) {
     using T = typename Traits<PREC>::real;
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= a.Vh) return;
     const int Lxh = a.Lxh, Vh = a.Vh;
     const int xh = h % Lxh;
     int r = h / Lxh;
@@ -187,6 +172,36 @@ __global__ void __launch_bounds__(128) k_dslash(const DslashArgs a) {
     }
 }
 
+template <int PREC, int RECON, bool DAG, int EPI>
+__global__ void __launch_bounds__(128) k_dslash(const DslashArgs a) {
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= a.Vh) return;
+    dslash_site<PREC, RECON, DAG, EPI>(a, h);
+}
+
+// Batched launch: the grid is cut into units (one lattice, up to DSLASH_UNIT_RHS
+// right-hand sides); inside a unit thread t serves site t / R of rhs t % R, so
+// the R threads of one site sit in the same warp and one link load serves all
+// R right-hand sides. mask[sys] == 0 skips a system (converged, or not due
+// for an update).
+template <int PREC, int RECON, bool DAG, int EPI>
+__global__ void __launch_bounds__(128) k_dslash_batch(const DslashUnit *units, const int *block0, int nunits,
+                                                      const double *mask) {
+    int u = 0;
+    while (u + 1 < nunits && __ldg(block0 + u + 1) <= (int)blockIdx.x) u++;
+    const DslashUnit *U = units + u;
+    const int lr = U->log2R;
+    const int t = ((int)blockIdx.x - __ldg(block0 + u)) * blockDim.x + threadIdx.x;
+    const int r = t & ((1 << lr) - 1), h = t >> lr;
+    if (r >= U->nr || h >= U->a.Vh) return;
+    if (mask && mask[U->sys[r]] == 0.0) return;
+    DslashArgs a = U->a;
+    a.in = U->in[r];
+    a.out = U->out[r];
+    a.xin = U->xin[r];
+    dslash_site<PREC, RECON, DAG, EPI>(a, h);
+}
+
 template <int PREC>
 __global__ void k_clover(void *out, const void *in, const void *clov, int Vh) {
     using T = typename Traits<PREC>::real;
@@ -200,6 +215,16 @@ __global__ void k_clover(void *out, const void *in, const void *clov, int Vh) {
 
 // --------------------------------------------------------------------------
 // dispatch
+
+// algorithmic traffic of one output site for one right-hand side: 8 links,
+// the input and output spinors, plus the clover block pair and (xpay) the x spinor
+double dslash_site_bytes(int prec, int recon, int epi) {
+    double b = 8.0 * link_bytes_per_link(prec, recon) + 2.0 * spinor_bytes_per_site(prec);
+    if (epi != EPI_PLAIN) b += clover_bytes_per_site(prec);
+    if (epi == EPI_XPAY) b += spinor_bytes_per_site(prec);
+    return b;
+}
+double dslash_site_flops(int epi) { return 1320.0 + (epi != EPI_PLAIN ? 504.0 : 0.0) + (epi == EPI_XPAY ? 48.0 : 0.0); }
 
 template <int PREC, int RECON>
 static void launch_dslash_pr(const DslashArgs &a, bool dag, int epi, unsigned grid, cudaStream_t s) {
@@ -248,7 +273,10 @@ int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_par
         c->ev_bucket[slot] = prec * 3 + epi;
         BQ_CUDA_TRY(cudaEventRecord(c->ev[2 * slot], c->stream));
     }
-    if (prec == BQ_PREC_DOUBLE) {
+    if (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) {
+        if (recon == 12) launch_dslash_pr<BQ_PREC_DF64, 12>(a, dagger, epi, grid, c->stream);
+        else launch_dslash_pr<BQ_PREC_DF64, 18>(a, dagger, epi, grid, c->stream);
+    } else if (prec == BQ_PREC_DOUBLE) {
         if (recon == 12) launch_dslash_pr<BQ_PREC_DOUBLE, 12>(a, dagger, epi, grid, c->stream);
         else launch_dslash_pr<BQ_PREC_DOUBLE, 18>(a, dagger, epi, grid, c->stream);
     } else if (prec == BQ_PREC_SINGLE) {
@@ -260,17 +288,7 @@ int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_par
     }
     BQ_LAUNCH_CHECK();
     if (slot >= 0) BQ_CUDA_TRY(cudaEventRecord(c->ev[2 * slot + 1], c->stream));
-    // algorithmic traffic and work of this launch
-    double site_bytes = 8.0 * link_bytes_per_link(prec, recon) + 2.0 * spinor_bytes_per_site(prec);
-    double site_flops = 1320.0;
-    if (epi != EPI_PLAIN) {
-        site_bytes += clover_bytes_per_site(prec);
-        site_flops += 504.0;
-    }
-    if (epi == EPI_XPAY) {
-        site_bytes += spinor_bytes_per_site(prec);
-        site_flops += 48.0;
-    }
+    const double site_bytes = dslash_site_bytes(prec, recon, epi), site_flops = dslash_site_flops(epi);
     BQ_COUNT(c);
     c->counters.dslash_launches[prec][epi]++;
     c->counters.dslash_bytes[prec][epi] += site_bytes * c->Vh;
@@ -312,11 +330,91 @@ extern "C" int bq_get_counters(bq_ctx *c, bq_counters *out) {
     return BQ_OK;
 }
 
+template <int PREC, int RECON>
+static void launch_batch_pr(const DslashUnit *units, const int *block0, int nunits, const double *mask, int nblocks,
+                            bool dag, int epi, cudaStream_t s) {
+    if (dag) {
+        if (epi == EPI_PLAIN) k_dslash_batch<PREC, RECON, true, EPI_PLAIN><<<nblocks, 128, 0, s>>>(units, block0, nunits, mask);
+        else if (epi == EPI_CLOVINV) k_dslash_batch<PREC, RECON, true, EPI_CLOVINV><<<nblocks, 128, 0, s>>>(units, block0, nunits, mask);
+        else k_dslash_batch<PREC, RECON, true, EPI_XPAY><<<nblocks, 128, 0, s>>>(units, block0, nunits, mask);
+    } else {
+        if (epi == EPI_PLAIN) k_dslash_batch<PREC, RECON, false, EPI_PLAIN><<<nblocks, 128, 0, s>>>(units, block0, nunits, mask);
+        else if (epi == EPI_CLOVINV) k_dslash_batch<PREC, RECON, false, EPI_CLOVINV><<<nblocks, 128, 0, s>>>(units, block0, nunits, mask);
+        else k_dslash_batch<PREC, RECON, false, EPI_XPAY><<<nblocks, 128, 0, s>>>(units, block0, nunits, mask);
+    }
+}
+
+// Fill the lattice-level part of a unit for one launch type (fields of c at
+// precision prec, output parity, adjoint, epilogue); the rhs pointers are the caller's.
+int bq_dslash_unit_fill(bq_ctx *c, int prec, int out_parity, int dagger, int epi, double k, DslashArgs *a) {
+    BQ_TRY(bq_prepare_links(c, prec));
+    if (epi != EPI_PLAIN) BQ_TRY(bq_prepare_clover(c, prec));
+    a->out = nullptr;
+    a->in = nullptr;
+    a->xin = nullptr;
+    a->links = links_ptr(c, prec);
+    a->lblk = links_block_bytes(c, prec);
+    a->clov = (epi == EPI_CLOVINV) ? clover_ptr(c, prec, out_parity, 1)
+            : (epi == EPI_XPAY)    ? clover_ptr(c, prec, out_parity, 0)
+                                   : nullptr;
+    a->L0 = c->L[0];
+    a->L1 = c->L[1];
+    a->L2 = c->L[2];
+    a->L3 = c->L[3];
+    a->Lxh = c->L[0] / 2;
+    a->Vh = c->Vh;
+    a->parity = out_parity;
+    double ef = exp(c->params.mu), eb = exp(-c->params.mu);
+    a->cf = dagger ? eb : ef;
+    a->cb = dagger ? ef : eb;
+    a->bc = c->params.t_bc;
+    a->k = k;
+    return BQ_OK;
+}
+
+// One batched hopping-term launch over a unit table already on the device.
+// All units must use precision prec with recon `recon` and the FP64
+// arithmetic mode of c (the context that owns the stream and the counters).
+int bq_dslash_batch_launch(bq_ctx *c, int prec, int recon, const DslashUnit *units_dev, const int *block0_dev,
+                           int nunits, int nblocks, const double *mask, int dagger, int epi, double site_bytes_total,
+                           double site_flops_total) {
+    int slot = -1;
+    if (c->timing) {
+        if (c->ev_used == BQ_EV_PAIRS) BQ_TRY(bq_fold_events(c));
+        slot = c->ev_used++;
+        c->ev_bucket[slot] = prec * 3 + epi;
+        BQ_CUDA_TRY(cudaEventRecord(c->ev[2 * slot], c->stream));
+    }
+    cudaStream_t s = c->stream;
+    if (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) {
+        if (recon == 12) launch_batch_pr<BQ_PREC_DF64, 12>(units_dev, block0_dev, nunits, mask, nblocks, dagger, epi, s);
+        else launch_batch_pr<BQ_PREC_DF64, 18>(units_dev, block0_dev, nunits, mask, nblocks, dagger, epi, s);
+    } else if (prec == BQ_PREC_DOUBLE) {
+        if (recon == 12) launch_batch_pr<BQ_PREC_DOUBLE, 12>(units_dev, block0_dev, nunits, mask, nblocks, dagger, epi, s);
+        else launch_batch_pr<BQ_PREC_DOUBLE, 18>(units_dev, block0_dev, nunits, mask, nblocks, dagger, epi, s);
+    } else if (prec == BQ_PREC_SINGLE) {
+        if (recon == 12) launch_batch_pr<BQ_PREC_SINGLE, 12>(units_dev, block0_dev, nunits, mask, nblocks, dagger, epi, s);
+        else launch_batch_pr<BQ_PREC_SINGLE, 18>(units_dev, block0_dev, nunits, mask, nblocks, dagger, epi, s);
+    } else {
+        if (recon == 12) launch_batch_pr<BQ_PREC_HALF, 12>(units_dev, block0_dev, nunits, mask, nblocks, dagger, epi, s);
+        else launch_batch_pr<BQ_PREC_HALF, 18>(units_dev, block0_dev, nunits, mask, nblocks, dagger, epi, s);
+    }
+    BQ_LAUNCH_CHECK();
+    if (slot >= 0) BQ_CUDA_TRY(cudaEventRecord(c->ev[2 * slot + 1], c->stream));
+    BQ_COUNT(c);
+    c->counters.dslash_launches[prec][epi]++;
+    c->counters.dslash_bytes[prec][epi] += site_bytes_total;
+    c->counters.dslash_flops[prec][epi] += site_flops_total;
+    return BQ_OK;
+}
+
 int bq_clover_launch(bq_ctx *c, int prec, void *out, const void *in, int parity, int inverse) {
     BQ_TRY(bq_prepare_clover(c, prec));
     const void *cl = clover_ptr(c, prec, parity, inverse);
     unsigned grid = (unsigned)((c->Vh + 127) / 128);
-    if (prec == BQ_PREC_DOUBLE) k_clover<BQ_PREC_DOUBLE><<<grid, 128, 0, c->stream>>>(out, in, cl, c->Vh);
+    if (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64)
+        k_clover<BQ_PREC_DF64><<<grid, 128, 0, c->stream>>>(out, in, cl, c->Vh);
+    else if (prec == BQ_PREC_DOUBLE) k_clover<BQ_PREC_DOUBLE><<<grid, 128, 0, c->stream>>>(out, in, cl, c->Vh);
     else if (prec == BQ_PREC_SINGLE) k_clover<BQ_PREC_SINGLE><<<grid, 128, 0, c->stream>>>(out, in, cl, c->Vh);
     else k_clover<BQ_PREC_HALF><<<grid, 128, 0, c->stream>>>(out, in, cl, c->Vh);
     BQ_LAUNCH_CHECK();
@@ -345,6 +443,15 @@ int bq_workspace(bq_ctx *c, int prec) {
 
 // --------------------------------------------------------------------------
 // C ABI
+
+extern "C" int bq_set_fp64_arith(bq_ctx *c, int mode) {
+    if (!c || !(mode == BQ_FP64_NATIVE || mode == BQ_FP64_DF64)) {
+        bq_set_error("bq_set_fp64_arith: bad arguments");
+        return BQ_ERR_ARG;
+    }
+    c->fp64_arith = mode;
+    return BQ_OK;
+}
 
 static int check_apply(bq_ctx *c, const void *out, const void *in, int prec) {
     if (!c || !out || !in || !(prec == BQ_PREC_DOUBLE || prec == BQ_PREC_SINGLE || prec == BQ_PREC_HALF)) {

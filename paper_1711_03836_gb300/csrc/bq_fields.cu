@@ -116,6 +116,7 @@ extern "C" int bq_destroy(bq_ctx *c) {
     if (!c) return BQ_OK;
     cudaStreamSynchronize(c->stream);
     bq_solver_free(c);
+    bq_batch_free(c);
     cudaFree(c->U_canon);
     cudaFree(c->A_u1);
     for (int p = 0; p < BQ_NPREC; p++) {

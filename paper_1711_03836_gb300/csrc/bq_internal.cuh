@@ -399,6 +399,147 @@ struct CloverIO<BQ_PREC_HALF> {
     }
 };
 
+
+// --------------------------------------------------------------------------
+// double-float ("df64") arithmetic: a value is hi + lo with two floats,
+// |lo| <= ulp(hi)/2 after normalisation, about 48 significant bits.  Sums use
+// Knuth's two-sum, products Dekker's two-product through FMA; the intrinsics
+// below are never contracted into FMAs by the compiler, which the error-free
+// transforms rely on.  GB300 runs FP32 at 62x its FP64 rate, so FP64-storage
+// kernels compute in df64 and round back to FP64 on store.
+
+struct df {
+    float hi, lo;
+    df() = default;
+    __device__ __forceinline__ constexpr df(float h, float l) : hi(h), lo(l) {}
+    __device__ __forceinline__ df(float f) : hi(f), lo(0.0f) {}
+    __device__ __forceinline__ df(int i) : hi((float)i), lo(0.0f) {}
+    // scalars only (FP64 pipe); bulk data goes through df_from_double
+    __device__ __forceinline__ explicit df(double d) {
+        hi = __double2float_rn(d);
+        lo = __double2float_rn(d - (double)hi);
+    }
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return df(s, e);
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // needs |a| >= |b| or a == 0
+    const float s = __fadd_rn(a, b);
+    return df(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ df operator+(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+// a * b + c
+__device__ __forceinline__ df fma(df a, df b, df c) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    df s = two_sum(p, c.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
+}
+
+// exact split of an IEEE double into hi (its leading 24 significant bits,
+// truncated) and lo (the next 29 bits rounded to 24), with integer operations
+// only; |d| outside [2^-126, 2^128) maps to 0 / infinity
+__device__ __forceinline__ df df_from_double(double d) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const unsigned h32 = (unsigned)(u >> 32), l32 = (unsigned)u;
+    const unsigned sign = h32 & 0x80000000u;
+    const int e = (int)((h32 >> 20) & 0x7ffu);
+    const int ef = e - 896;  // biased float exponent of hi (1023 - 127)
+    const unsigned m23 = ((h32 & 0xfffffu) << 3) | (l32 >> 29);
+    const int el = e - 948;  // biased float exponent of 2^(e - 1075), the weight of the lowest bit
+    const float scale = (el >= 1) ? __uint_as_float((unsigned)el << 23) : 0.0f;
+    float lo = __fmul_rn(__uint2float_rn(l32 & 0x1fffffffu), scale);
+    lo = __uint_as_float(__float_as_uint(lo) | sign);
+    float hi = __uint_as_float(sign | ((unsigned)ef << 23) | m23);
+    if (ef < 1) {
+        hi = 0.0f;
+        lo = 0.0f;
+    } else if (ef > 254) {
+        hi = __uint_as_float(sign | 0x7f800000u);
+        lo = 0.0f;
+    }
+    return df(hi, lo);
+}
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+enum { BQ_PREC_DF64 = 3 };  // internal: FP64 storage and layout, df64 arithmetic
+
+template <>
+struct Traits<BQ_PREC_DF64> {
+    using real = df;
+};
+
+template <>
+struct SpinorIO<BQ_PREC_DF64> {
+    using T = df;
+    __device__ static __forceinline__ void load(cplx<T> s[12], const void *base, int h, int Vh) {
+        const double2 *p = static_cast<const double2 *>(base);
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            double2 v = ldg(p + (size_t)c * Vh + h);
+            s[c] = {df_from_double(v.x), df_from_double(v.y)};
+        }
+    }
+    __device__ static __forceinline__ void store(void *base, int h, int Vh, const cplx<T> s[12]) {
+        double2 *p = static_cast<double2 *>(base);
+#pragma unroll
+        for (int c = 0; c < 12; c++) p[(size_t)c * Vh + h] = make_double2(df_to_double(s[c].re), df_to_double(s[c].im));
+    }
+};
+
+template <int RECON>
+struct LinkIO<BQ_PREC_DF64, RECON> {
+    using T = df;
+    static constexpr int NC = (RECON == 12) ? 6 : 9;
+    __device__ static __forceinline__ void load(cplx<T> U[9], const char *blk, int h, int Vh) {
+        const double2 *p = reinterpret_cast<const double2 *>(blk);
+#pragma unroll
+        for (int c = 0; c < NC; c++) {
+            double2 v = ldg(p + (size_t)c * Vh + h);
+            U[c] = {df_from_double(v.x), df_from_double(v.y)};
+        }
+        if (RECON == 12) reconstruct_row2(U);
+    }
+};
+
+template <>
+struct CloverIO<BQ_PREC_DF64> {
+    using T = df;
+    __device__ static __forceinline__ void load_block(T d[6], cplx<T> o[15], const void *base, int b, int h,
+                                                      int Vh) {
+        const double2 *p = static_cast<const double2 *>(base) + (size_t)(18 * b) * Vh + h;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            double2 v = ldg(p + (size_t)k * Vh);
+            d[2 * k] = df_from_double(v.x);
+            d[2 * k + 1] = df_from_double(v.y);
+        }
+#pragma unroll
+        for (int k = 0; k < 15; k++) {
+            double2 v = ldg(p + (size_t)(3 + k) * Vh);
+            o[k] = {df_from_double(v.x), df_from_double(v.y)};
+        }
+    }
+};
+
 // y = B x for one packed Hermitian 6x6 block
 template <typename T>
 __device__ __forceinline__ void herm6_apply(const T d[6], const cplx<T> o[15], const cplx<T> x[6], cplx<T> y[6]) {
@@ -434,6 +575,7 @@ __device__ __forceinline__ void clover_apply_site(cplx<T> out[12], const cplx<T>
 enum { BQ_NPREC = 3 };
 
 struct SolverWork;  // defined in the solver translation unit
+struct BatchWork;   // defined in the batched solver translation unit
 
 struct bq_ctx {
     int L[4];
@@ -443,6 +585,7 @@ struct bq_ctx {
     cudaStream_t stream;
     bq_params params;
     int recon[BQ_NPREC];
+    int fp64_arith;  // BQ_FP64_NATIVE or BQ_FP64_DF64 for FP64-storage operator kernels
 
     // master fields (FP64, device)
     double2 *U_canon;  // [V][4][9]
@@ -466,6 +609,7 @@ struct bq_ctx {
     unsigned int *red_ticket;      // last-block ticket
     int *dev_flag;                 // device error flag (singular clover etc.)
     SolverWork *solver;
+    BatchWork *batch;
 
     // counters and optional per-launch event timing of the hopping term
     bq_counters counters;
@@ -495,6 +639,32 @@ inline size_t links_block_bytes(const bq_ctx *c, int prec) {
     return link_bytes_per_link(prec, c->links_recon[prec]) * (size_t)c->Vh;
 }
 
+struct DslashArgs {
+    void *out;
+    const void *in;
+    const char *links;
+    size_t lblk;  // bytes of one (parity, mu) link block
+    const void *clov;
+    const void *xin;
+    int L0, L1, L2, L3, Lxh, Vh, parity;
+    double cf, cb;  // time-hop factors forward / backward (e^{+mu}, e^{-mu}, swapped for the adjoint)
+    double bc;      // time boundary sign
+    double k;       // xpay coefficient
+};
+
+// one unit of a batched hopping-term launch: a lattice (fields, geometry and
+// parameters in `a`) and up to DSLASH_UNIT_RHS right-hand sides
+enum { DSLASH_UNIT_RHS = 8 };
+struct DslashUnit {
+    DslashArgs a;
+    const void *in[DSLASH_UNIT_RHS];
+    void *out[DSLASH_UNIT_RHS];
+    const void *xin[DSLASH_UNIT_RHS];
+    int sys[DSLASH_UNIT_RHS];  // mask index of each rhs
+    int nr;                    // right-hand sides in use
+    int log2R;                 // threads per site = 1 << log2R >= nr
+};
+
 // operator launches (bq_dslash.cu)
 enum { EPI_PLAIN = 0, EPI_CLOVINV = 1, EPI_XPAY = 2 };
 int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_parity, int dagger, int epi,
@@ -503,3 +673,17 @@ int bq_clover_launch(bq_ctx *c, int prec, void *out, const void *in, int parity,
 int bq_mhat_launch(bq_ctx *c, int prec, void *out, const void *in, int dagger, void *tmp_odd);
 int bq_mdagm_launch(bq_ctx *c, int prec, void *out, const void *in, void *tmp_odd, void *tmp_even);
 int bq_workspace(bq_ctx *c, int prec);
+int bq_dslash_unit_fill(bq_ctx *c, int prec, int out_parity, int dagger, int epi, double k, DslashArgs *a);
+int bq_dslash_batch_launch(bq_ctx *c, int prec, int recon, const DslashUnit *units_dev, const int *block0_dev,
+                           int nunits, int nblocks, const double *mask, int dagger, int epi, double site_bytes_total,
+                           double site_flops_total);
+double dslash_site_bytes(int prec, int recon, int epi);
+double dslash_site_flops(int epi);
+
+// batched solver (bq_batch.cu)
+int bq_batch_reserve(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int pr);
+void *bq_batch_slot_b(bq_ctx *c0, int s);
+void *bq_batch_slot_x(bq_ctx *c0, int s);
+int bq_cg_batch_core(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double *shifts, const bq_solver_params *sp,
+                     bool have_x0, bq_solver_stats *st);
+void bq_batch_free(bq_ctx *c);

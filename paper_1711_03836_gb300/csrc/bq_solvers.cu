@@ -15,17 +15,9 @@
 #include <stdlib.h>
 #include <string.h>
 
-#include "bq_internal.cuh"
+#include <vector>
 
-enum { S_RR = 0, S_BB, S_PAP, S_ALPHA, S_BETA, S_RRPREV, S_RRTRUE, S_SIGMA, S_NSCAL };
-
-constexpr int RED_THREADS = 256;
-constexpr int RED_MAX_BLOCKS = 1024;
-
-static int red_grid(int Vh) {
-    int g = (Vh + RED_THREADS - 1) / RED_THREADS;
-    return g < RED_MAX_BLOCKS ? g : RED_MAX_BLOCKS;
-}
+#include "bq_reduce.cuh"
 
 struct SolverWork {
     char *b, *x, *r, *t64;          // FP64 native even spinors
@@ -65,82 +57,6 @@ void bq_solver_free(bq_ctx *c) {
     free(w);
     c->solver = nullptr;
 }
-
-// --------------------------------------------------------------------------
-// reductions: warp shuffles, one partial per block, last block sums the
-// partials in block order (deterministic for a given grid)
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV]) {
-    __shared__ double sm[NV][32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NV; k++) {
-        v[k] = warp_sum(v[k]);
-        if (lane == 0) sm[k][wid] = v[k];
-    }
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; k++) v[k] = warp_sum(lane < nw ? sm[k][lane] : 0.0);
-    }
-}
-
-// Returns true in every thread of the last block to finish, with tot = grid sums.
-template <int NV>
-__device__ bool grid_sum(double (&v)[NV], double *partials, unsigned int *ticket, double (&tot)[NV]) {
-    __shared__ bool last;
-    __shared__ double res[NV];
-    block_sum(v);
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; k++) partials[k * gridDim.x + blockIdx.x] = v[k];
-        __threadfence();
-        unsigned int t = atomicAdd(ticket, 1u);
-        last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return false;
-    __threadfence();
-    double s[NV];
-#pragma unroll
-    for (int k = 0; k < NV; k++) s[k] = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
-#pragma unroll
-        for (int k = 0; k < NV; k++) s[k] += __ldcg(partials + k * gridDim.x + i);
-    block_sum(s);
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; k++) res[k] = s[k];
-        *ticket = 0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NV; k++) tot[k] = res[k];
-    return true;
-}
-
-template <typename T>
-__device__ __forceinline__ double norm2_site(const cplx<T> s[12]) {
-    T a = T(0);
-#pragma unroll
-    for (int c = 0; c < 12; c++) a += s[c].re * s[c].re + s[c].im * s[c].im;
-    return (double)a;
-}
-
-struct RedArgs {
-    double *partials;
-    unsigned int *ticket;
-    double *scal;
-    int Vh;
-};
 
 // --------------------------------------------------------------------------
 // CG kernels; PS = precision of p, Ap; PR = precision of rs, xs
@@ -228,111 +144,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_cg_pap(const void *p, void *Ap,
     }
 }
 
-// xs += alpha p; rs -= alpha Ap; rr_new = |rs|^2; beta = rr_new / rr
-template <int PS, int PR>
-__global__ void __launch_bounds__(RED_THREADS) k_cg_update_xr(const void *p, const void *Ap, void *xs, void *rs,
-                                                              RedArgs ra) {
-    using TS = typename Traits<PS>::real;
-    using TR = typename Traits<PR>::real;
-    const TR alpha = (TR)ra.scal[S_ALPHA];
-    double v[1] = {0.0};
-    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < ra.Vh; h += gridDim.x * blockDim.x) {
-        cplx<TS> a[12], q[12];
-        cplx<TR> xv[12], rv[12];
-        SpinorIO<PS>::load(a, p, h, ra.Vh);
-        SpinorIO<PS>::load(q, Ap, h, ra.Vh);
-        SpinorIO<PR>::load(xv, xs, h, ra.Vh);
-        SpinorIO<PR>::load(rv, rs, h, ra.Vh);
-#pragma unroll
-        for (int c = 0; c < 12; c++) {
-            xv[c].re = fma(alpha, (TR)a[c].re, xv[c].re);
-            xv[c].im = fma(alpha, (TR)a[c].im, xv[c].im);
-            rv[c].re = fma(-alpha, (TR)q[c].re, rv[c].re);
-            rv[c].im = fma(-alpha, (TR)q[c].im, rv[c].im);
-        }
-        SpinorIO<PR>::store(xs, h, ra.Vh, xv);
-        SpinorIO<PR>::store(rs, h, ra.Vh, rv);
-        v[0] += norm2_site(rv);
-    }
-    double tot[1];
-    if (grid_sum(v, ra.partials, ra.ticket, tot) && threadIdx.x == 0) {
-        double rr = ra.scal[S_RR];
-        ra.scal[S_RRPREV] = rr;
-        ra.scal[S_RR] = tot[0];
-        ra.scal[S_BETA] = tot[0] / rr;
-    }
-}
 
-// p = rs + beta p
-template <int PS, int PR>
-__global__ void __launch_bounds__(RED_THREADS) k_cg_update_p(void *p, const void *rs, const double *scal, int Vh) {
-    using TS = typename Traits<PS>::real;
-    using TR = typename Traits<PR>::real;
-    const TS beta = (TS)scal[S_BETA];
-    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
-        cplx<TS> a[12];
-        cplx<TR> rv[12];
-        SpinorIO<PS>::load(a, p, h, Vh);
-        SpinorIO<PR>::load(rv, rs, h, Vh);
-#pragma unroll
-        for (int c = 0; c < 12; c++) {
-            a[c].re = fma(beta, a[c].re, (TS)rv[c].re);
-            a[c].im = fma(beta, a[c].im, (TS)rv[c].im);
-        }
-        SpinorIO<PS>::store(p, h, Vh, a);
-    }
-}
 
-// x += xs; xs = 0   (x FP64)
-template <int PR>
-__global__ void __launch_bounds__(RED_THREADS) k_promote(void *x, void *xs, int Vh) {
-    using TR = typename Traits<PR>::real;
-    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
-        cplx<double> xv[12];
-        cplx<TR> d[12];
-        SpinorIO<BQ_PREC_DOUBLE>::load(xv, x, h, Vh);
-        SpinorIO<PR>::load(d, xs, h, Vh);
-#pragma unroll
-        for (int c = 0; c < 12; c++) {
-            xv[c].re += (double)d[c].re;
-            xv[c].im += (double)d[c].im;
-            d[c] = {TR(0), TR(0)};
-        }
-        SpinorIO<BQ_PREC_DOUBLE>::store(x, h, Vh, xv);
-        SpinorIO<PR>::store(xs, h, Vh, d);
-    }
-}
 
-// r = b - t - sigma x (FP64), rs = r, rr_true = |r|^2; rr = rr_true, beta = rr_true / rr_prev
-template <int PR>
-__global__ void __launch_bounds__(RED_THREADS) k_residual(const void *b, const void *t, const void *x, void *r,
-                                                          void *rs, RedArgs ra) {
-    using TR = typename Traits<PR>::real;
-    const double sigma = ra.scal[S_SIGMA];
-    double v[1] = {0.0};
-    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < ra.Vh; h += gridDim.x * blockDim.x) {
-        cplx<double> bv[12], tv[12], xv[12];
-        SpinorIO<BQ_PREC_DOUBLE>::load(bv, b, h, ra.Vh);
-        SpinorIO<BQ_PREC_DOUBLE>::load(tv, t, h, ra.Vh);
-        SpinorIO<BQ_PREC_DOUBLE>::load(xv, x, h, ra.Vh);
-        cplx<TR> sr[12];
-#pragma unroll
-        for (int c = 0; c < 12; c++) {
-            bv[c].re = bv[c].re - tv[c].re - sigma * xv[c].re;
-            bv[c].im = bv[c].im - tv[c].im - sigma * xv[c].im;
-            sr[c] = {(TR)bv[c].re, (TR)bv[c].im};
-        }
-        SpinorIO<BQ_PREC_DOUBLE>::store(r, h, ra.Vh, bv);
-        SpinorIO<PR>::store(rs, h, ra.Vh, sr);
-        v[0] += norm2_site(bv);
-    }
-    double tot[1];
-    if (grid_sum(v, ra.partials, ra.ticket, tot) && threadIdx.x == 0) {
-        ra.scal[S_RRTRUE] = tot[0];
-        ra.scal[S_RR] = tot[0];
-        ra.scal[S_BETA] = tot[0] / ra.scal[S_RRPREV];
-    }
-}
 
 
 // --------------------------------------------------------------------------
@@ -583,142 +397,6 @@ static int read_scalars(bq_ctx *c) {
     return BQ_OK;
 }
 
-// CG / reliable-update mixed CG on (Mhat^dag Mhat + shift) x = b; b is w->b (FP64 native).
-// With have_x0 the solve starts from the FP64 native w->x, else from x = 0.
-template <int PS, int PR>
-static int cg_run(bq_ctx *c, const bq_solver_params *sp, bq_solver_stats *st, bool have_x0) {
-    SolverWork *w = c->solver;
-    const int Vh = c->Vh;
-    const int G = red_grid(Vh);
-    RedArgs ra{c->red_partials, c->red_ticket, w->scal, Vh};
-    cudaStream_t s = c->stream;
-    const double delta = (PS == BQ_PREC_DOUBLE) ? 0.0 : sp->delta;
-    const int check = sp->check_every > 0 ? sp->check_every : 1;
-
-    double init[S_NSCAL] = {0};
-    init[S_SIGMA] = sp->shift;
-    BQ_CUDA_TRY(cudaMemcpyAsync(w->scal, init, sizeof init, cudaMemcpyHostToDevice, s));
-    if (have_x0)
-        BQ_TRY(bq_mdagm_launch(c, BQ_PREC_DOUBLE, w->t64, w->x, c->tmp_odd[BQ_PREC_DOUBLE], c->tmp_even[BQ_PREC_DOUBLE]));
-    k_cg_init<PS, PR><<<G, RED_THREADS, 0, s>>>(w->b, have_x0 ? w->t64 : nullptr, w->x, w->r, w->rs[PR], w->xs[PR],
-                                                w->p[PS], ra);
-    BQ_COUNT(c);
-    BQ_LAUNCH_CHECK();
-    BQ_TRY(read_scalars(c));
-    const double bb = w->h_scal[S_BB];
-    st->iterations = 0;
-    st->reliable_updates = 0;
-    st->dslash_calls = have_x0 ? 4 : 0;
-    st->converged = 0;
-    st->true_residual = 0.0;
-    if (bb == 0.0) {
-        st->converged = 1;
-        return BQ_OK;
-    }
-    const double target = sp->tol * sp->tol * bb;
-    double rrtrue = w->h_scal[S_RR], maxrr = rrtrue;
-    if (rrtrue <= target) {
-        st->converged = 1;
-        st->true_residual = sqrt(rrtrue / bb);
-        return BQ_OK;
-    }
-    int it = 0;
-    while (true) {
-        BQ_TRY(bq_mdagm_launch(c, PS, w->Ap[PS], w->p[PS], c->tmp_odd[PS], c->tmp_even[PS]));
-        k_cg_pap<PS><<<G, RED_THREADS, 0, s>>>(w->p[PS], w->Ap[PS], ra);
-        BQ_COUNT(c);
-        k_cg_update_xr<PS, PR><<<G, RED_THREADS, 0, s>>>(w->p[PS], w->Ap[PS], w->xs[PR], w->rs[PR], ra);
-        BQ_COUNT(c);
-        BQ_LAUNCH_CHECK();
-        it++;
-        st->dslash_calls += 4;
-        if (it % check == 0 || it >= sp->max_iter) {
-            BQ_TRY(read_scalars(c));
-            double rr = w->h_scal[S_RR];
-            if (!(rr == rr)) {
-                bq_set_error("solver breakdown: residual is NaN");
-                st->iterations = it;
-                return BQ_ERR_NOT_CONVERGED;
-            }
-            if (rr > maxrr) maxrr = rr;
-            if (rr < delta * delta * maxrr || rr <= target || it >= sp->max_iter) {
-                k_promote<PR><<<G, RED_THREADS, 0, s>>>(w->x, w->xs[PR], Vh);
-                BQ_COUNT(c);
-                BQ_TRY(bq_mdagm_launch(c, BQ_PREC_DOUBLE, w->t64, w->x, c->tmp_odd[BQ_PREC_DOUBLE],
-                                       c->tmp_even[BQ_PREC_DOUBLE]));
-                k_residual<PR><<<G, RED_THREADS, 0, s>>>(w->b, w->t64, w->x, w->r, w->rs[PR], ra);
-                BQ_COUNT(c);
-                BQ_LAUNCH_CHECK();
-                BQ_TRY(read_scalars(c));
-                st->reliable_updates++;
-                st->dslash_calls += 4;
-                rrtrue = w->h_scal[S_RRTRUE];
-                maxrr = rrtrue;
-                if (rrtrue <= target) {
-                    st->converged = 1;
-                    break;
-                }
-                if (it >= sp->max_iter) break;
-            }
-        }
-        k_cg_update_p<PS, PR><<<G, RED_THREADS, 0, s>>>(w->p[PS], w->rs[PR], w->scal, Vh);
-        BQ_COUNT(c);
-        BQ_LAUNCH_CHECK();
-    }
-    st->iterations = it;
-    st->true_residual = sqrt(rrtrue / bb);
-    return BQ_OK;
-}
-
-static int cg_dispatch(bq_ctx *c, const bq_solver_params *sp, bq_solver_stats *st, bool have_x0) {
-    if (sp->precision == BQ_PREC_DOUBLE) return cg_run<BQ_PREC_DOUBLE, BQ_PREC_DOUBLE>(c, sp, st, have_x0);
-    if (sp->precision == BQ_PREC_SINGLE) return cg_run<BQ_PREC_SINGLE, BQ_PREC_SINGLE>(c, sp, st, have_x0);
-    return cg_run<BQ_PREC_HALF, BQ_PREC_SINGLE>(c, sp, st, have_x0);
-}
-
-extern "C" int bq_solve_cg(bq_ctx *c, double *x, const double *b, int where, const bq_solver_params *sp,
-                           bq_solver_stats *st) {
-    if (!c || !x || !b || !sp || !(where == BQ_HOST || where == BQ_DEVICE)) {
-        bq_set_error("bq_solve_cg: bad arguments");
-        return BQ_ERR_ARG;
-    }
-    int ps = sp->precision;
-    if (!(ps == BQ_PREC_DOUBLE || ps == BQ_PREC_SINGLE || ps == BQ_PREC_HALF) || !(sp->tol > 0) ||
-        sp->max_iter < 1 || sp->shift < 0 || sp->delta < 0 || sp->delta >= 1) {
-        bq_set_error("bq_solve_cg: bad solver parameters");
-        return BQ_ERR_ARG;
-    }
-    if (!c->have_gauge) {
-        bq_set_error("gauge field not set");
-        return BQ_ERR_STATE;
-    }
-    bq_solver_stats local;
-    if (!st) st = &local;
-    int pr = (ps == BQ_PREC_HALF) ? BQ_PREC_SINGLE : ps;
-    BQ_TRY(ensure_work(c, ps, pr));
-    BQ_TRY(bq_prepare_links(c, BQ_PREC_DOUBLE));
-    BQ_TRY(bq_prepare_clover(c, BQ_PREC_DOUBLE));
-    BQ_TRY(bq_prepare_links(c, ps));
-    BQ_TRY(bq_prepare_clover(c, ps));
-    SolverWork *w = c->solver;
-    BQ_CUDA_TRY(cudaEventRecord(w->e0, c->stream));
-    BQ_TRY(bq_spinor_pack(c, w->b, b, BQ_PREC_DOUBLE, where));
-    int status;
-    status = cg_dispatch(c, sp, st, false);
-    if (status != BQ_OK && status != BQ_ERR_NOT_CONVERGED) return status;
-    BQ_TRY(bq_spinor_unpack(c, x, w->x, BQ_PREC_DOUBLE, where));
-    BQ_CUDA_TRY(cudaEventRecord(w->e1, c->stream));
-    BQ_CUDA_TRY(cudaEventSynchronize(w->e1));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, w->e0, w->e1);
-    st->seconds = ms * 1e-3;
-    if (status == BQ_OK && !st->converged) {
-        bq_set_error("CG reached max_iter=%d with true residual %.3e", sp->max_iter, st->true_residual);
-        return BQ_ERR_NOT_CONVERGED;
-    }
-    return status;
-}
-
 // --------------------------------------------------------------------------
 // multishift driver
 
@@ -859,28 +537,33 @@ extern "C" int bq_solve_multishift_cg(bq_ctx *c, double *const *x, const double 
     st->iterations = ms_iters;
     st->dslash_calls = dsl;
     st->converged = 1;
-    // per-shift refinement from the multishift solution to the true FP64 residual
+    // per-shift refinement from the multishift solution to the true FP64 residual:
+    // all shifts at once as one batch (shared link loads, one launch per step)
     const int G = red_grid(c->Vh);
+    std::vector<bq_ctx *> ctxs(nshift, c);
+    BQ_TRY(bq_batch_reserve(c, nshift, ctxs.data(), ps, pr));
     for (int k = 0; k < nshift; k++) {
+        void *xk = bq_batch_slot_x(c, k);
         if (pr == BQ_PREC_DOUBLE)
-            k_to_double<BQ_PREC_DOUBLE><<<G, RED_THREADS, 0, c->stream>>>(w->x, w->msx[k], c->Vh);
+            k_to_double<BQ_PREC_DOUBLE><<<G, RED_THREADS, 0, c->stream>>>(xk, w->msx[k], c->Vh);
         else
-            k_to_double<BQ_PREC_SINGLE><<<G, RED_THREADS, 0, c->stream>>>(w->x, w->msx[k], c->Vh);
+            k_to_double<BQ_PREC_SINGLE><<<G, RED_THREADS, 0, c->stream>>>(xk, w->msx[k], c->Vh);
         BQ_COUNT(c);
         BQ_LAUNCH_CHECK();
-        bq_solver_params rp = *sp;
-        rp.shift = shifts[k];
-        bq_solver_stats rs;
-        memset(&rs, 0, sizeof rs);
-        int s2 = cg_dispatch(c, &rp, &rs, true);
-        if (s2 != BQ_OK && s2 != BQ_ERR_NOT_CONVERGED) return s2;
-        BQ_TRY(bq_spinor_unpack(c, x[k], w->x, BQ_PREC_DOUBLE, where));
-        st->iterations += rs.iterations;
-        st->reliable_updates += rs.reliable_updates;
-        st->dslash_calls += rs.dslash_calls;
-        if (!rs.converged) st->converged = 0;
-        if (rs.true_residual > st->true_residual) st->true_residual = rs.true_residual;
-        if (residuals) residuals[k] = rs.true_residual;
+        BQ_CUDA_TRY(cudaMemcpyAsync(bq_batch_slot_b(c, k), w->b, (size_t)c->Vh * 192, cudaMemcpyDeviceToDevice,
+                                    c->stream));
+    }
+    std::vector<bq_solver_stats> rs(nshift);
+    int s2 = bq_cg_batch_core(c, nshift, ctxs.data(), shifts, sp, true, rs.data());
+    if (s2 != BQ_OK && s2 != BQ_ERR_NOT_CONVERGED) return s2;
+    for (int k = 0; k < nshift; k++) {
+        BQ_TRY(bq_spinor_unpack(c, x[k], bq_batch_slot_x(c, k), BQ_PREC_DOUBLE, where));
+        st->iterations += rs[k].iterations;
+        st->reliable_updates += rs[k].reliable_updates;
+        st->dslash_calls += rs[k].dslash_calls;
+        if (!rs[k].converged) st->converged = 0;
+        if (rs[k].true_residual > st->true_residual) st->true_residual = rs[k].true_residual;
+        if (residuals) residuals[k] = rs[k].true_residual;
     }
     BQ_CUDA_TRY(cudaEventRecord(w->e1, c->stream));
     BQ_CUDA_TRY(cudaEventSynchronize(w->e1));

@@ -274,3 +274,100 @@ def test_spinor_dot(bq, prec):
     assert abs(got - ref) / abs(ref) < (1e-13 if prec == "double" else 1e-6)
     assert bq.bq_spinor_dot(lat.ctx, na, nb, prec) == got  # fixed reduction order
     lat.close()
+
+
+DF64_CASES = [(18, 0.0, 0.0), (12, 0.1, 0.0), (18, 0.1, 2.0 / 3.0)]
+
+
+@pytest.mark.parametrize("recon,mu,charge", DF64_CASES)
+def test_df64_arith_parity(bq, recon, mu, charge):
+    """FP64 storage with double-float arithmetic meets the FP64 tolerance (1e-13)."""
+    dims = (6, 4, 6, 10)
+    lat, U, A, p = make(bq, dims, mu=mu, charge=charge, recon=recon, precision="double")
+    bq.bq_set_fp64_arith(lat.ctx, "df64")
+    op = oracle.Operator(p, U, A)
+    psi = synth.gaussian_spinor(lat.Vh, 15)
+    src = lat.pack(psi, "double")
+    out = lat.spinor("double")
+    for par in (0, 1):
+        for dag in (False, True):
+            bq.bq_apply_dhop(lat.ctx, out, src, par, dag, "double")
+            assert rel(lat.unpack(out), oracle.dhop(p, U, A, psi, par, dag)) < 1e-13, (par, dag)
+    for dag in (False, True):
+        bq.bq_apply_mhat(lat.ctx, out, src, dag, "double")
+        assert rel(lat.unpack(out), op.mhat(psi, dag)) < 1e-13, dag
+    for par in (0, 1):
+        for inv in (False, True):
+            bq.bq_apply_clover(lat.ctx, out, src, par, inv, "double")
+            Am = oracle.clover_field(p, U, par)
+            ref = oracle.clover_apply(oracle.clover_invert(Am) if inv else Am, psi)
+            assert rel(lat.unpack(out), ref) < 1e-13
+    # values spanning many binades, exact zeros and a point source survive the float-pair split
+    wide = psi * np.exp(np.random.default_rng(3).uniform(-30, 30, psi.shape))
+    wide[::7] = 0
+    bq.bq_apply_mhat(lat.ctx, out, lat.pack(wide, "double"), 0, "double")
+    assert rel(lat.unpack(out), op.mhat(wide)) < 1e-13
+    x = np.empty_like(psi)
+    st = bq.bq_solve_cg(lat.ctx, x, psi, tol=1e-10, precision="single")
+    assert st["converged"] and np.linalg.norm(op.mdagm(x) - psi) / np.linalg.norm(psi) <= 1e-10
+    lat.close()
+
+
+def test_df64_full_size_sampled(bq):
+    dims = (32, 32, 32, 64)
+    U = synth.gauge_field(dims, 0.15, 1)
+    lat = bq.Lattice(dims, 0.1355, 1.9, 0.0, -1.0)
+    bq.bq_set_gauge(lat.ctx, U)
+    bq.bq_set_fp64_arith(lat.ctx, "df64")
+    p = oracle.params(dims, kappa=0.1355, csw=1.9, mu=0.0, t_bc=-1.0)
+    psi = synth.gaussian_spinor(lat.Vh, 19)
+    sites = np.unique(np.concatenate([[0, lat.Vh - 1], np.random.default_rng(1).integers(0, lat.Vh, 30)]))
+    out = lat.spinor("double")
+    bq.bq_apply_mhat(lat.ctx, out, lat.pack(psi), 0, "double")
+    assert rel(lat.unpack(out)[sites], oracle.mhat_sites(p, U, None, psi, sites)) < 1e-13
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", ["double", "single", "half"])
+def test_batched_point_sources(bq, prec):
+    """12 spin-colour point sources on one lattice in one batched solve: each
+    solution reaches a true FP64 residual <= 1e-10 and equals the oracle CG."""
+    dims = (6, 4, 6, 10)
+    lat, U, A, p = make(bq, dims, kappa=0.1350, csw=1.7, eps=0.2, recon=12 if prec != "double" else 18,
+                        precision=prec)
+    op = oracle.Operator(p, U)
+    bs = [synth.point_source(lat.Vh, 0, s, c) for s in range(4) for c in range(3)]
+    xs = [np.empty_like(b) for b in bs]
+    stats = bq.bq_solve_cg_batch([lat.ctx] * 12, xs, bs, tol=1e-10, precision=prec,
+                                 delta=1e-3 if prec == "single" else 1e-1)
+    for b, x, st in zip(bs, xs, stats):
+        res = np.linalg.norm(op.mdagm(x) - b) / np.linalg.norm(b)
+        assert st["converged"] and res <= 1e-10, res
+        assert abs(st["true_residual"] - res) < 1e-11
+        xo, _ = op.cg(b, tol=1e-12)
+        assert rel(x, xo) < 1e-8
+    lat.close()
+
+
+def test_batched_ragged_lattices(bq):
+    """A ragged batch (different lattices, parameters, chemical potential and
+    shift) in one batched solve, on device buffers."""
+    import torch
+
+    cases = [((8, 8, 8, 8), 0.125, 1.0, 0.0, 0.3), ((6, 4, 6, 10), 0.1350, 1.7, 0.1, 0.2), ((4, 4, 4, 4), 0.13, 1.9, 0.0, 0.2)]
+    lats, ops, bs_d, xs_d, bs = [], [], [], [], []
+    for i, (dims, kappa, csw, mu, eps) in enumerate(cases):
+        lat, U, A, p = make(bq, dims, kappa=kappa, csw=csw, mu=mu, eps=eps, seed=10 + i, recon=12, precision="single")
+        lats.append(lat)
+        ops.append(oracle.Operator(p, U))
+        b = synth.gaussian_spinor(lat.Vh, 500 + i)
+        bs.append(b)
+        bs_d.append(torch.from_numpy(b).cuda())
+        xs_d.append(torch.empty_like(bs_d[-1]))
+    stats = bq.bq_solve_cg_batch([l.ctx for l in lats], xs_d, bs_d, tol=1e-10, precision="single", shift=0.01)
+    for op, b, x, st in zip(ops, bs, xs_d, stats):
+        x = x.cpu().numpy()
+        res = np.linalg.norm(op.mdagm(x, 0.01) - b) / np.linalg.norm(b)
+        assert st["converged"] and res <= 1e-10, res
+    for l in lats:
+        l.close()
