@@ -43,6 +43,7 @@ METRIC = "Dslash GB/s vs HBM peak; mixed/batched vs FP64 CG time to |r|/|b|<1e-1
 WORKLOADS = {
     "32^3x64": dict(dims=(32, 32, 32, 64), eps=0.15, kappa=0.1355, csw=1.9, mu=0.0, seed=1),
     "24^3x48": dict(dims=(24, 24, 24, 48), eps=0.2, kappa=0.1350, csw=1.7, mu=0.0, seed=1),
+    "20^3x40": dict(dims=(20, 20, 20, 40), eps=0.2, kappa=0.1350, csw=1.7, mu=0.0, seed=1),
     "16^3x32": dict(dims=(16, 16, 16, 32), eps=0.2, kappa=0.1350, csw=1.7, mu=0.0, seed=1),
     "8^4": dict(dims=(8, 8, 8, 8), eps=0.3, kappa=0.125, csw=1.0, mu=0.0, seed=1),
 }
@@ -71,8 +72,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="32^3x64", choices=sorted(WORKLOADS))
     ap.add_argument("--inner", default="single", choices=["single", "half"])
-    ap.add_argument("--delta", type=float, default=None)
+    ap.add_argument("--delta", type=float, default=None, help="reliable-update threshold (default 1e-3 FP32, 0.1 FP16)")
+    ap.add_argument("--check-every", type=int, default=8, help="iterations between host residual checks")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 CG, sweep, e2e and CPU baseline")
+    ap.add_argument("--mode", default="cg", choices=["cg", "batch12", "multishift10", "ragged4"],
+                    help="the timed step: one mixed CG solve (default), 12 point sources in one batched "
+                         "solve, a 10-shift multishift solve, or a ragged batch of four lattices")
     return ap.parse_args()
 
 
@@ -253,10 +258,11 @@ def main():
     b_dev = torch.from_numpy(b).cuda()
     x_dev = torch.empty_like(b_dev)
     delta = args.delta if args.delta is not None else (1e-3 if args.inner == "single" else 1e-1)
-    solve_kw = dict(tol=1e-10, precision=args.inner, delta=delta, check_every=8, max_iter=20000)
+    solve_kw = dict(tol=1e-10, precision=args.inner, delta=delta, check_every=args.check_every, max_iter=20000)
 
+    step, extra_ctxs = make_step(args, torch, bqcd, synth, lat, b_dev, x_dev, solve_kw)
     for _ in range(max(args.warmup, 0)):
-        bqcd.bq_solve_cg(ctx, x_dev, b_dev, **solve_kw)
+        step()
     torch.cuda.synchronize()
 
     # ---- timed region: K solves, inputs resident in HBM
@@ -268,7 +274,7 @@ def main():
     stats = []
     e0.record()
     for _ in range(args.steps):
-        stats.append(bqcd.bq_solve_cg(ctx, x_dev, b_dev, **solve_kw))
+        stats.append(step())
     e1.record()
     torch.cuda.synchronize()
     barrier()
@@ -313,11 +319,14 @@ def main():
         "roofline": roofline,
         "gpu_launches": cnt["launches"],
         "clocks": clocks,
-        "solve": {"iterations": stats[-1]["iterations"], "reliable_updates": stats[-1]["reliable_updates"],
-                  "true_residual": stats[-1]["true_residual"], "converged": stats[-1]["converged"]},
+        "solve": summarize(stats[-1]),
     }
+    if args.mode != "cg":
+        line["config"]["workload"] = f"{args.mode} on " + line["config"]["workload"]
 
-    if not args.no_extras and world == 1:
+    for l in extra_ctxs:
+        l.close()
+    if not args.no_extras and world == 1 and args.mode == "cg":
         line.update(extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, ms_max / args.steps, torch, bqcd))
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -389,6 +398,42 @@ def batched_extras(torch, bqcd):
     for l in lats:
         l.close()
     return out
+
+
+def summarize(st):
+    sts = st if isinstance(st, list) else [st]
+    return {"systems": len(sts), "iterations": max(x["iterations"] for x in sts),
+            "reliable_updates": max(x["reliable_updates"] for x in sts),
+            "true_residual": max(x["true_residual"] for x in sts),
+            "converged": int(all(x["converged"] for x in sts))}
+
+
+def make_step(args, torch, bqcd, synth, lat, b_dev, x_dev, solve_kw):
+    """The timed step of each mode; returns (callable, extra lattices to close)."""
+    ctx = lat.ctx
+    if args.mode == "cg":
+        return (lambda: bqcd.bq_solve_cg(ctx, x_dev, b_dev, **solve_kw)), []
+    if args.mode == "batch12":
+        srcs = [torch.from_numpy(synth.point_source(lat.Vh, 0, s, c)).cuda() for s in range(4) for c in range(3)]
+        xs = [torch.empty_like(b) for b in srcs]
+        return (lambda: bqcd.bq_solve_cg_batch([ctx] * 12, xs, srcs, **solve_kw)), []
+    if args.mode == "multishift10":
+        shifts = [10.0 ** (-4 + 4 * k / 9) for k in range(10)]
+        xk = [torch.empty_like(b_dev) for _ in shifts]
+        kw = {k: v for k, v in solve_kw.items() if k != "max_iter"}
+        return (lambda: bqcd.bq_solve_multishift_cg(ctx, xk, b_dev, shifts, **kw)), []
+    # ragged: the workload lattice plus 8^4, 12^4 and 16^3x32, in one batched solve
+    lats, bs, xr = [lat], [b_dev], [x_dev]
+    for i, dims in enumerate([(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32)]):
+        l = bqcd.Lattice(dims, 0.1350, 1.7, 0.0, -1.0)
+        bqcd.bq_set_gauge(l.ctx, synth.gauge_field(dims, 0.2, 1 + i))
+        bqcd.bq_set_recon(l.ctx, "single", 12)
+        bqcd.bq_set_recon(l.ctx, "half", 12)
+        lats.append(l)
+        bs.append(torch.from_numpy(synth.gaussian_spinor(l.Vh, 900 + i)).cuda())
+        xr.append(torch.empty_like(bs[-1]))
+    ctxs = [l.ctx for l in lats]
+    return (lambda: bqcd.bq_solve_cg_batch(ctxs, xr, bs, **solve_kw)), lats[1:]
 
 
 def extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, mixed_ms, torch, bqcd):

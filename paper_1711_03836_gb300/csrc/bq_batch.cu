@@ -24,6 +24,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <new>
 #include <vector>
 
 #include "bq_reduce.cuh"
@@ -264,13 +265,12 @@ struct BatchWork {
     SysVec *d_sys;
     double *d_scal, *d_part, *d_flags;
     unsigned int *d_ticket;
-    DslashUnit *d_units;  // [8 steps][dev_cap units]
-    int *d_block0;        // [8 steps][dev_cap + 1]
     double *h_scal, *h_flags;  // pinned mirrors
     double *stage;             // canonical staging for host spinors
     size_t stage_bytes;
-    DslashUnit *h_units;       // host mirror of d_units
-    int h_units_cap;
+    // launch tables of the 8 hopping-term steps (4 sloppy, 4 FP64), each split
+    // into chunks of at most DSLASH_MAX_UNITS units, passed by value at launch
+    std::vector<DslashBatchTable> tables[8];
     cudaEvent_t e0, e1;
 };
 
@@ -299,22 +299,19 @@ void bq_batch_free(bq_ctx *c) {
     cudaFree(w->d_part);
     cudaFree(w->d_flags);
     cudaFree(w->d_ticket);
-    cudaFree(w->d_units);
-    cudaFree(w->d_block0);
     cudaFreeHost(w->h_scal);
     cudaFreeHost(w->h_flags);
     cudaFree(w->stage);
-    free(w->h_units);
     if (w->e0) cudaEventDestroy(w->e0);
     if (w->e1) cudaEventDestroy(w->e1);
-    free(w);
+    delete w;
     c->batch = nullptr;
 }
 
 // make slots [0, nsys) hold vectors for ctxs[s] at (ps, pr)
 int bq_batch_reserve(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int pr) {
     if (!c0->batch) {
-        c0->batch = (BatchWork *)calloc(1, sizeof(BatchWork));
+        c0->batch = new (std::nothrow) BatchWork();
         if (!c0->batch) return BQ_ERR_NOMEM;
         BQ_CUDA_TRY(cudaEventCreate(&c0->batch->e0));
         BQ_CUDA_TRY(cudaEventCreate(&c0->batch->e1));
@@ -356,23 +353,17 @@ int bq_batch_reserve(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int pr) 
         cudaFree(w->d_part);
         cudaFree(w->d_flags);
         cudaFree(w->d_ticket);
-        cudaFree(w->d_units);
-        cudaFree(w->d_block0);
         cudaFreeHost(w->h_scal);
         cudaFreeHost(w->h_flags);
         w->d_sys = nullptr;
         w->d_scal = w->d_part = w->d_flags = nullptr;
         w->d_ticket = nullptr;
-        w->d_units = nullptr;
-        w->d_block0 = nullptr;
         w->h_scal = w->h_flags = nullptr;
         BQ_TRY(bq_alloc((void **)&w->d_sys, sizeof(SysVec) * nsys));
         BQ_TRY(bq_alloc((void **)&w->d_scal, sizeof(double) * S_NSCAL * nsys));
         BQ_TRY(bq_alloc((void **)&w->d_part, sizeof(double) * 2 * RED_MAX_BLOCKS * nsys));
         BQ_TRY(bq_alloc((void **)&w->d_flags, sizeof(double) * 2 * nsys));
         BQ_TRY(bq_alloc((void **)&w->d_ticket, sizeof(unsigned int) * nsys));
-        BQ_TRY(bq_alloc((void **)&w->d_units, sizeof(DslashUnit) * 8 * nsys));
-        BQ_TRY(bq_alloc((void **)&w->d_block0, sizeof(int) * 8 * (nsys + 1)));
         BQ_CUDA_TRY(cudaMallocHost((void **)&w->h_scal, sizeof(double) * S_NSCAL * nsys));
         BQ_CUDA_TRY(cudaMallocHost((void **)&w->h_flags, sizeof(double) * 2 * nsys));
         BQ_CUDA_TRY(cudaMemsetAsync(w->d_ticket, 0, sizeof(unsigned int) * nsys, c0->stream));
@@ -389,8 +380,6 @@ void *bq_batch_slot_x(bq_ctx *c0, int s) { return c0->batch->slot[s].x; }
 // unit tables of the two Mhat^dag Mhat applications (sloppy p -> Ap, FP64 x -> t)
 
 struct UnitPlan {
-    int nunits[8];
-    int nblocks[8];
     double bytes_all[8];  // algorithmic bytes of each step with every system active
     double flops_all[8];
 };
@@ -402,8 +391,7 @@ static int log2_ceil(int n) {
 }
 
 // steps 0-3 sloppy (prec ps), 4-7 FP64: D_oe+A^-1, A x - k D_eo, and the two adjoint ones
-static int build_units(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int rhs_per_unit, UnitPlan *plan,
-                       DslashUnit *h_units, int *h_block0) {
+static int build_units(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int rhs_per_unit, UnitPlan *plan) {
     BatchWork *w = c0->batch;
     for (int step = 0; step < 8; step++) {
         const int prec = step < 4 ? ps : BQ_PREC_DOUBLE;
@@ -411,61 +399,47 @@ static int build_units(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int rh
         const int parity = (k == 0 || k == 2) ? 1 : 0;
         const int dagger = k >= 2;
         const int epi = parity == 1 ? EPI_CLOVINV : EPI_XPAY;
-        DslashUnit *U = h_units + step * nsys;
-        int *B0 = h_block0 + step * (nsys + 1);
-        int nu = 0, blocks = 0;
+        std::vector<DslashBatchTable> &tabs = w->tables[step];
+        tabs.clear();
         double bytes = 0, flops = 0;
         int s = 0;
         while (s < nsys) {
+            if (tabs.empty() || tabs.back().nunits == DSLASH_MAX_UNITS) {
+                tabs.emplace_back();
+                memset(&tabs.back(), 0, sizeof(DslashBatchTable));
+            }
+            DslashBatchTable &tab = tabs.back();
             // the run of systems on the same lattice, cut into units of rhs_per_unit
             int e = s + 1;
             while (e < nsys && ctxs[e] == ctxs[s] && e - s < rhs_per_unit) e++;
             bq_ctx *c = ctxs[s];
             const double kk = c->params.kappa * c->params.kappa;
-            DslashUnit *u = &U[nu];
-            memset(u, 0, sizeof *u);
+            DslashUnit *u = &tab.units[tab.nunits];
             BQ_TRY(bq_dslash_unit_fill(c, prec, parity, dagger, epi, kk, &u->a));
             u->nr = e - s;
             u->log2R = log2_ceil(u->nr);
             for (int q = 0; q < u->nr; q++) {
                 BatchSlot *sl = &w->slot[s + q];
-                void *sin, *sout, *sx;
-                if (step < 4) {
-                    void *pv[4][3] = {{sl->p, sl->to_s, nullptr},
-                                      {sl->to_s, sl->te_s, sl->p},
-                                      {sl->te_s, sl->to_s, nullptr},
-                                      {sl->to_s, sl->Ap, sl->te_s}};
-                    sin = pv[k][0];
-                    sout = pv[k][1];
-                    sx = pv[k][2];
-                } else {
-                    void *pv[4][3] = {{sl->x, sl->to_d, nullptr},
-                                      {sl->to_d, sl->r, sl->x},
-                                      {sl->r, sl->to_d, nullptr},
-                                      {sl->to_d, sl->t, sl->r}};
-                    sin = pv[k][0];
-                    sout = pv[k][1];
-                    sx = pv[k][2];
-                }
-                u->in[q] = sin;
-                u->out[q] = sout;
-                u->xin[q] = sx;
+                void *pv[8][3] = {{sl->p, sl->to_s, nullptr},  {sl->to_s, sl->te_s, sl->p},
+                                  {sl->te_s, sl->to_s, nullptr}, {sl->to_s, sl->Ap, sl->te_s},
+                                  {sl->x, sl->to_d, nullptr},   {sl->to_d, sl->r, sl->x},
+                                  {sl->r, sl->to_d, nullptr},   {sl->to_d, sl->t, sl->r}};
+                u->in[q] = pv[step][0];
+                u->out[q] = pv[step][1];
+                u->xin[q] = pv[step][2];
                 u->sys[q] = s + q;
             }
-            B0[nu] = blocks;
-            blocks += (int)(((long long)c->Vh * (1 << u->log2R) + 127) / 128);
+            const int blocks = (int)(((long long)c->Vh * (1 << u->log2R) + 127) / 128);
+            tab.block0[tab.nunits + 1] = tab.block0[tab.nunits] + blocks;
+            tab.nunits++;
             // links and clover once per site of the unit, spinors per rhs
             const int recon = c->links_recon[prec];
             const double shared = 8.0 * link_bytes_per_link(prec, recon) + clover_bytes_per_site(prec);
             const double per_rhs = dslash_site_bytes(prec, recon, epi) - shared;
             bytes += (shared + per_rhs * u->nr) * (double)c->Vh;
             flops += dslash_site_flops(epi) * u->nr * (double)c->Vh;
-            nu++;
             s = e;
         }
-        B0[nu] = blocks;
-        plan->nunits[step] = nu;
-        plan->nblocks[step] = blocks;
         plan->bytes_all[step] = bytes;
         plan->flops_all[step] = flops;
     }
@@ -480,17 +454,18 @@ static int mdagm_batch(bq_ctx *c0, int prec, int recon, int first_step, const Un
         const int parity = (k == 0 || k == 2) ? 1 : 0;
         const int dagger = k >= 2;
         const int epi = parity == 1 ? EPI_CLOVINV : EPI_XPAY;
+        const std::vector<DslashBatchTable> &tabs = w->tables[step];
         if (nsys == 1) {
             // a single system: the plain kernel, no unit indirection (it is
             // active whenever this runs: the loop stops at convergence)
-            const DslashUnit &u = w->h_units[step * nsys];
+            const DslashUnit &u = tabs[0].units[0];
             BQ_TRY(bq_dslash_launch(c0, prec, u.out[0], u.in[0], parity, dagger, epi, u.xin[0], u.a.k));
             continue;
         }
-        BQ_TRY(bq_dslash_batch_launch(c0, prec, recon, w->d_units + step * nsys, w->d_block0 + step * (nsys + 1),
-                                      plan->nunits[step], plan->nblocks[step], mask_dev, dagger, epi,
-                                      plan->bytes_all[step] * active_fraction,
-                                      plan->flops_all[step] * active_fraction));
+        for (size_t q = 0; q < tabs.size(); q++)
+            BQ_TRY(bq_dslash_batch_launch(c0, prec, recon, &tabs[q], mask_dev, dagger, epi,
+                                          plan->bytes_all[step] * active_fraction / tabs.size(),
+                                          plan->flops_all[step] * active_fraction / tabs.size()));
     }
     return BQ_OK;
 }
@@ -508,43 +483,20 @@ static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double 
     for (int i = 0; i < nsys; i++) maxVh = ctxs[i]->Vh > maxVh ? ctxs[i]->Vh : maxVh;
     const dim3 G(red_grid(maxVh), nsys);
 
-    // device tables
-    SysVec *hs = (SysVec *)calloc(nsys, sizeof(SysVec));
-    if (w->h_units_cap < 8 * nsys) {
-        free(w->h_units);
-        w->h_units = (DslashUnit *)calloc(8 * nsys, sizeof(DslashUnit));
-        w->h_units_cap = w->h_units ? 8 * nsys : 0;
-    }
-    DslashUnit *hu = w->h_units;
-    int *hb = (int *)calloc(8 * (nsys + 1), sizeof(int));
-    double *hscal = (double *)calloc((size_t)S_NSCAL * nsys, sizeof(double));
-    if (!hs || !hu || !hb || !hscal) {
-        free(hs);
-        free(hb);
-        free(hscal);
-        return BQ_ERR_NOMEM;
-    }
+    // device tables: per-system vectors and scalars (the launch tables stay on the host)
+    std::vector<SysVec> hs(nsys);
+    std::vector<double> hscal((size_t)S_NSCAL * nsys, 0.0);
     for (int i = 0; i < nsys; i++) {
         BatchSlot *sl = &w->slot[i];
         hs[i] = SysVec{sl->b, sl->x, sl->r, sl->t, sl->rs, sl->xs, sl->p, sl->Ap, sl->Vh};
         hscal[(size_t)i * S_NSCAL + S_SIGMA] = shifts ? shifts[i] : sp->shift;
     }
     UnitPlan plan;
-    int status = build_units(c0, nsys, ctxs, PS, rhs_per_unit, &plan, hu, hb);
-    if (status == BQ_OK) {
-        if (cudaMemcpyAsync(w->d_sys, hs, sizeof(SysVec) * nsys, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(w->d_units, hu, sizeof(DslashUnit) * 8 * nsys, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(w->d_block0, hb, sizeof(int) * 8 * (nsys + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(w->d_scal, hscal, sizeof(double) * S_NSCAL * nsys, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) {
-            bq_set_error("batched CG: table upload failed");
-            status = BQ_ERR_CUDA;
-        }
-    }
-    free(hs);
-    free(hb);
-    free(hscal);
-    if (status != BQ_OK) return status;
+    BQ_TRY(build_units(c0, nsys, ctxs, PS, rhs_per_unit, &plan));
+    BQ_CUDA_TRY(cudaMemcpyAsync(w->d_sys, hs.data(), sizeof(SysVec) * nsys, cudaMemcpyHostToDevice, s));
+    BQ_CUDA_TRY(cudaMemcpyAsync(w->d_scal, hscal.data(), sizeof(double) * S_NSCAL * nsys, cudaMemcpyHostToDevice, s));
+    BQ_CUDA_TRY(cudaStreamSynchronize(s));
+    int status = BQ_OK;
 
     double *active = w->h_flags, *update = w->h_flags + nsys;
     double *d_active = w->d_flags, *d_update = w->d_flags + nsys;
@@ -596,7 +548,6 @@ static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double 
     const double delta = (PS == BQ_PREC_DOUBLE) ? 0.0 : sp->delta;
     const int check = sp->check_every > 0 ? sp->check_every : 1;
     int it = 0;
-    status = BQ_OK;
     while (nactive > 0) {
         const double frac = (double)nactive / nsys;
         kb_update_p<PS, PR><<<G, RED_THREADS, 0, s>>>(ba_act);

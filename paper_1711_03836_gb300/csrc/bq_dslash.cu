@@ -94,7 +94,8 @@ __device__ __forceinline__ void hop(cplx<typename Traits<PREC>::real> acc[12], c
 }
 
 template <int PREC, int RECON, bool DAG, int EPI>
-__device__ __forceinline__ void dslash_site(const DslashArgs &a, const int h) {
+__device__ __forceinline__ void dslash_site(const DslashArgs &a, const void *in, void *out, const void *xin,
+                                            const int h) {
     using T = typename Traits<PREC>::real;
     const int Lxh = a.Lxh, Vh = a.Vh;
     const int xh = h % Lxh;
@@ -116,51 +117,51 @@ __device__ __forceinline__ void dslash_site(const DslashArgs &a, const int h) {
 
     {
         const int xn = (x + 1 == a.L0) ? 0 : x + 1;
-        hop<PREC, RECON, 0, SF, false, false>(acc, a.in, h - xh + (xn >> 1), Lo, h, Vh, T(1));
+        hop<PREC, RECON, 0, SF, false, false>(acc, in, h - xh + (xn >> 1), Lo, h, Vh, T(1));
     }
     {
         const int xn = (x == 0) ? a.L0 - 1 : x - 1;
         const int hn = h - xh + (xn >> 1);
-        hop<PREC, RECON, 0, SB, true, false>(acc, a.in, hn, Li, hn, Vh, T(1));
+        hop<PREC, RECON, 0, SB, true, false>(acc, in, hn, Li, hn, Vh, T(1));
     }
     {
         const int hn = (y + 1 == a.L1) ? h - (a.L1 - 1) * sy : h + sy;
-        hop<PREC, RECON, 1, SF, false, false>(acc, a.in, hn, Lo + a.lblk, h, Vh, T(1));
+        hop<PREC, RECON, 1, SF, false, false>(acc, in, hn, Lo + a.lblk, h, Vh, T(1));
     }
     {
         const int hn = (y == 0) ? h + (a.L1 - 1) * sy : h - sy;
-        hop<PREC, RECON, 1, SB, true, false>(acc, a.in, hn, Li + a.lblk, hn, Vh, T(1));
+        hop<PREC, RECON, 1, SB, true, false>(acc, in, hn, Li + a.lblk, hn, Vh, T(1));
     }
     {
         const int hn = (z + 1 == a.L2) ? h - (a.L2 - 1) * sz : h + sz;
-        hop<PREC, RECON, 2, SF, false, false>(acc, a.in, hn, Lo + 2 * a.lblk, h, Vh, T(1));
+        hop<PREC, RECON, 2, SF, false, false>(acc, in, hn, Lo + 2 * a.lblk, h, Vh, T(1));
     }
     {
         const int hn = (z == 0) ? h + (a.L2 - 1) * sz : h - sz;
-        hop<PREC, RECON, 2, SB, true, false>(acc, a.in, hn, Li + 2 * a.lblk, hn, Vh, T(1));
+        hop<PREC, RECON, 2, SB, true, false>(acc, in, hn, Li + 2 * a.lblk, hn, Vh, T(1));
     }
     {
         const bool wrap = (t + 1 == a.L3);
         const int hn = wrap ? h - (a.L3 - 1) * st : h + st;
         const T coef = (T)(wrap ? a.cf * a.bc : a.cf);
-        hop<PREC, RECON, 3, SF, false, true>(acc, a.in, hn, Lo + 3 * a.lblk, h, Vh, coef);
+        hop<PREC, RECON, 3, SF, false, true>(acc, in, hn, Lo + 3 * a.lblk, h, Vh, coef);
     }
     {
         const bool wrap = (t == 0);
         const int hn = wrap ? h + (a.L3 - 1) * st : h - st;
         const T coef = (T)(wrap ? a.cb * a.bc : a.cb);
-        hop<PREC, RECON, 3, SB, true, true>(acc, a.in, hn, Li + 3 * a.lblk, hn, Vh, coef);
+        hop<PREC, RECON, 3, SB, true, true>(acc, in, hn, Li + 3 * a.lblk, hn, Vh, coef);
     }
 
     if (EPI == EPI_PLAIN) {
-        SpinorIO<PREC>::store(a.out, h, Vh, acc);
+        SpinorIO<PREC>::store(out, h, Vh, acc);
     } else if (EPI == EPI_CLOVINV) {
         cplx<T> o[12];
         clover_apply_site<PREC>(o, acc, a.clov, h, Vh);
-        SpinorIO<PREC>::store(a.out, h, Vh, o);
+        SpinorIO<PREC>::store(out, h, Vh, o);
     } else {
         cplx<T> xv[12], o[12];
-        SpinorIO<PREC>::load(xv, a.xin, h, Vh);
+        SpinorIO<PREC>::load(xv, xin, h, Vh);
         clover_apply_site<PREC>(o, xv, a.clov, h, Vh);
         const T k = (T)a.k;
 #pragma unroll
@@ -168,7 +169,7 @@ __device__ __forceinline__ void dslash_site(const DslashArgs &a, const int h) {
             o[c].re = fma(-k, acc[c].re, o[c].re);
             o[c].im = fma(-k, acc[c].im, o[c].im);
         }
-        SpinorIO<PREC>::store(a.out, h, Vh, o);
+        SpinorIO<PREC>::store(out, h, Vh, o);
     }
 }
 
@@ -176,7 +177,7 @@ template <int PREC, int RECON, bool DAG, int EPI>
 __global__ void __launch_bounds__(128) k_dslash(const DslashArgs a) {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= a.Vh) return;
-    dslash_site<PREC, RECON, DAG, EPI>(a, h);
+    dslash_site<PREC, RECON, DAG, EPI>(a, a.in, a.out, a.xin, h);
 }
 
 // Batched launch: the grid is cut into units (one lattice, up to DSLASH_UNIT_RHS
@@ -185,21 +186,16 @@ __global__ void __launch_bounds__(128) k_dslash(const DslashArgs a) {
 // R right-hand sides. mask[sys] == 0 skips a system (converged, or not due
 // for an update).
 template <int PREC, int RECON, bool DAG, int EPI>
-__global__ void __launch_bounds__(128) k_dslash_batch(const DslashUnit *units, const int *block0, int nunits,
-                                                      const double *mask) {
+__global__ void __launch_bounds__(128) k_dslash_batch(const __grid_constant__ DslashBatchTable tab, const double *mask) {
     int u = 0;
-    while (u + 1 < nunits && __ldg(block0 + u + 1) <= (int)blockIdx.x) u++;
-    const DslashUnit *U = units + u;
-    const int lr = U->log2R;
-    const int t = ((int)blockIdx.x - __ldg(block0 + u)) * blockDim.x + threadIdx.x;
+    while (u + 1 < tab.nunits && tab.block0[u + 1] <= (int)blockIdx.x) u++;
+    const DslashUnit &U = tab.units[u];
+    const int lr = U.log2R;
+    const int t = ((int)blockIdx.x - tab.block0[u]) * blockDim.x + threadIdx.x;
     const int r = t & ((1 << lr) - 1), h = t >> lr;
-    if (r >= U->nr || h >= U->a.Vh) return;
-    if (mask && mask[U->sys[r]] == 0.0) return;
-    DslashArgs a = U->a;
-    a.in = U->in[r];
-    a.out = U->out[r];
-    a.xin = U->xin[r];
-    dslash_site<PREC, RECON, DAG, EPI>(a, h);
+    if (r >= U.nr || h >= U.a.Vh) return;
+    if (mask && mask[U.sys[r]] == 0.0) return;
+    dslash_site<PREC, RECON, DAG, EPI>(U.a, U.in[r], U.out[r], U.xin[r], h);
 }
 
 template <int PREC>
@@ -331,16 +327,16 @@ extern "C" int bq_get_counters(bq_ctx *c, bq_counters *out) {
 }
 
 template <int PREC, int RECON>
-static void launch_batch_pr(const DslashUnit *units, const int *block0, int nunits, const double *mask, int nblocks,
-                            bool dag, int epi, cudaStream_t s) {
+static void launch_batch_pr(const DslashBatchTable &tab, const double *mask, int nblocks, bool dag, int epi,
+                            cudaStream_t s) {
     if (dag) {
-        if (epi == EPI_PLAIN) k_dslash_batch<PREC, RECON, true, EPI_PLAIN><<<nblocks, 128, 0, s>>>(units, block0, nunits, mask);
-        else if (epi == EPI_CLOVINV) k_dslash_batch<PREC, RECON, true, EPI_CLOVINV><<<nblocks, 128, 0, s>>>(units, block0, nunits, mask);
-        else k_dslash_batch<PREC, RECON, true, EPI_XPAY><<<nblocks, 128, 0, s>>>(units, block0, nunits, mask);
+        if (epi == EPI_PLAIN) k_dslash_batch<PREC, RECON, true, EPI_PLAIN><<<nblocks, 128, 0, s>>>(tab, mask);
+        else if (epi == EPI_CLOVINV) k_dslash_batch<PREC, RECON, true, EPI_CLOVINV><<<nblocks, 128, 0, s>>>(tab, mask);
+        else k_dslash_batch<PREC, RECON, true, EPI_XPAY><<<nblocks, 128, 0, s>>>(tab, mask);
     } else {
-        if (epi == EPI_PLAIN) k_dslash_batch<PREC, RECON, false, EPI_PLAIN><<<nblocks, 128, 0, s>>>(units, block0, nunits, mask);
-        else if (epi == EPI_CLOVINV) k_dslash_batch<PREC, RECON, false, EPI_CLOVINV><<<nblocks, 128, 0, s>>>(units, block0, nunits, mask);
-        else k_dslash_batch<PREC, RECON, false, EPI_XPAY><<<nblocks, 128, 0, s>>>(units, block0, nunits, mask);
+        if (epi == EPI_PLAIN) k_dslash_batch<PREC, RECON, false, EPI_PLAIN><<<nblocks, 128, 0, s>>>(tab, mask);
+        else if (epi == EPI_CLOVINV) k_dslash_batch<PREC, RECON, false, EPI_CLOVINV><<<nblocks, 128, 0, s>>>(tab, mask);
+        else k_dslash_batch<PREC, RECON, false, EPI_XPAY><<<nblocks, 128, 0, s>>>(tab, mask);
     }
 }
 
@@ -375,9 +371,9 @@ int bq_dslash_unit_fill(bq_ctx *c, int prec, int out_parity, int dagger, int epi
 // One batched hopping-term launch over a unit table already on the device.
 // All units must use precision prec with recon `recon` and the FP64
 // arithmetic mode of c (the context that owns the stream and the counters).
-int bq_dslash_batch_launch(bq_ctx *c, int prec, int recon, const DslashUnit *units_dev, const int *block0_dev,
-                           int nunits, int nblocks, const double *mask, int dagger, int epi, double site_bytes_total,
-                           double site_flops_total) {
+int bq_dslash_batch_launch(bq_ctx *c, int prec, int recon, const DslashBatchTable *tab, const double *mask,
+                           int dagger, int epi, double site_bytes_total, double site_flops_total) {
+    const int nblocks = tab->block0[tab->nunits];
     int slot = -1;
     if (c->timing) {
         if (c->ev_used == BQ_EV_PAIRS) BQ_TRY(bq_fold_events(c));
@@ -387,17 +383,17 @@ int bq_dslash_batch_launch(bq_ctx *c, int prec, int recon, const DslashUnit *uni
     }
     cudaStream_t s = c->stream;
     if (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) {
-        if (recon == 12) launch_batch_pr<BQ_PREC_DF64, 12>(units_dev, block0_dev, nunits, mask, nblocks, dagger, epi, s);
-        else launch_batch_pr<BQ_PREC_DF64, 18>(units_dev, block0_dev, nunits, mask, nblocks, dagger, epi, s);
+        if (recon == 12) launch_batch_pr<BQ_PREC_DF64, 12>(*tab, mask, nblocks, dagger, epi, s);
+        else launch_batch_pr<BQ_PREC_DF64, 18>(*tab, mask, nblocks, dagger, epi, s);
     } else if (prec == BQ_PREC_DOUBLE) {
-        if (recon == 12) launch_batch_pr<BQ_PREC_DOUBLE, 12>(units_dev, block0_dev, nunits, mask, nblocks, dagger, epi, s);
-        else launch_batch_pr<BQ_PREC_DOUBLE, 18>(units_dev, block0_dev, nunits, mask, nblocks, dagger, epi, s);
+        if (recon == 12) launch_batch_pr<BQ_PREC_DOUBLE, 12>(*tab, mask, nblocks, dagger, epi, s);
+        else launch_batch_pr<BQ_PREC_DOUBLE, 18>(*tab, mask, nblocks, dagger, epi, s);
     } else if (prec == BQ_PREC_SINGLE) {
-        if (recon == 12) launch_batch_pr<BQ_PREC_SINGLE, 12>(units_dev, block0_dev, nunits, mask, nblocks, dagger, epi, s);
-        else launch_batch_pr<BQ_PREC_SINGLE, 18>(units_dev, block0_dev, nunits, mask, nblocks, dagger, epi, s);
+        if (recon == 12) launch_batch_pr<BQ_PREC_SINGLE, 12>(*tab, mask, nblocks, dagger, epi, s);
+        else launch_batch_pr<BQ_PREC_SINGLE, 18>(*tab, mask, nblocks, dagger, epi, s);
     } else {
-        if (recon == 12) launch_batch_pr<BQ_PREC_HALF, 12>(units_dev, block0_dev, nunits, mask, nblocks, dagger, epi, s);
-        else launch_batch_pr<BQ_PREC_HALF, 18>(units_dev, block0_dev, nunits, mask, nblocks, dagger, epi, s);
+        if (recon == 12) launch_batch_pr<BQ_PREC_HALF, 12>(*tab, mask, nblocks, dagger, epi, s);
+        else launch_batch_pr<BQ_PREC_HALF, 18>(*tab, mask, nblocks, dagger, epi, s);
     }
     BQ_LAUNCH_CHECK();
     if (slot >= 0) BQ_CUDA_TRY(cudaEventRecord(c->ev[2 * slot + 1], c->stream));

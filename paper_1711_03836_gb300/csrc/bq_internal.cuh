@@ -665,6 +665,15 @@ struct DslashUnit {
     int log2R;                 // threads per site = 1 << log2R >= nr
 };
 
+// a batched launch passes its units by value (kernel parameter space, read
+// through the constant cache); more units than this are split over launches
+enum { DSLASH_MAX_UNITS = 16 };
+struct DslashBatchTable {
+    int nunits;
+    int block0[DSLASH_MAX_UNITS + 1];  // first block of each unit; block0[nunits] = grid size
+    DslashUnit units[DSLASH_MAX_UNITS];
+};
+
 // operator launches (bq_dslash.cu)
 enum { EPI_PLAIN = 0, EPI_CLOVINV = 1, EPI_XPAY = 2 };
 int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_parity, int dagger, int epi,
@@ -674,9 +683,8 @@ int bq_mhat_launch(bq_ctx *c, int prec, void *out, const void *in, int dagger, v
 int bq_mdagm_launch(bq_ctx *c, int prec, void *out, const void *in, void *tmp_odd, void *tmp_even);
 int bq_workspace(bq_ctx *c, int prec);
 int bq_dslash_unit_fill(bq_ctx *c, int prec, int out_parity, int dagger, int epi, double k, DslashArgs *a);
-int bq_dslash_batch_launch(bq_ctx *c, int prec, int recon, const DslashUnit *units_dev, const int *block0_dev,
-                           int nunits, int nblocks, const double *mask, int dagger, int epi, double site_bytes_total,
-                           double site_flops_total);
+int bq_dslash_batch_launch(bq_ctx *c, int prec, int recon, const DslashBatchTable *tab, const double *mask,
+                           int dagger, int epi, double site_bytes_total, double site_flops_total);
 double dslash_site_bytes(int prec, int recon, int epi);
 double dslash_site_flops(int epi);
 
