@@ -128,6 +128,12 @@ int bq_set_recon(bq_ctx *ctx, int precision, int recon);
  * and every other kernel are unchanged; results agree with FP64 to ~1e-14. */
 int bq_set_fp64_arith(bq_ctx *ctx, int mode);
 
+/* Solvers capture check_every iterations of their loop (every launch of every
+ * system) as one CUDA graph per solve and launch it between residual checks
+ * (default on); enable = 0 launches every kernel individually. Results are
+ * identical either way. */
+int bq_set_cuda_graphs(bq_ctx *ctx, int enable);
+
 /* Gauge links in canonical layout U[V][4][3][3] complex FP64, from host or
  * device memory (where = BQ_HOST / BQ_DEVICE). Copied; derived fields rebuilt lazily. */
 int bq_set_gauge(bq_ctx *ctx, const double *U, int where);

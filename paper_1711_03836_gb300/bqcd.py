@@ -81,6 +81,7 @@ _SIGS = {
     "bq_get_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(bq_counters)]),
     "bq_set_recon": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "bq_set_fp64_arith": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "bq_set_cuda_graphs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "bq_set_gauge": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "bq_set_u1": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "bq_build_clover": (ctypes.c_int, [ctypes.c_void_p]),
@@ -192,6 +193,10 @@ def bq_set_fp64_arith(ctx, mode):
     """"native" (FP64 units) or "df64" (double-float on the FP32 units) for FP64-storage operator kernels."""
     m = {"native": BQ_FP64_NATIVE, "df64": BQ_FP64_DF64, 0: 0, 1: 1}[mode]
     _check(_lib_handle().bq_set_fp64_arith(ctx, m), "bq_set_fp64_arith")
+
+
+def bq_set_cuda_graphs(ctx, enable):
+    _check(_lib_handle().bq_set_cuda_graphs(ctx, int(bool(enable))), "bq_set_cuda_graphs")
 
 
 def bq_set_gauge(ctx, U):

@@ -22,6 +22,7 @@
 // case it restarts (beta = 0).
 #include <math.h>
 #include <stdlib.h>
+#include <stdint.h>
 #include <string.h>
 
 #include <new>
@@ -253,6 +254,12 @@ __global__ void __launch_bounds__(RED_THREADS) kb_residual(BArgs ba) {
 // --------------------------------------------------------------------------
 // workspace: per-system vectors cached in the first context, reused across calls
 
+struct GraphRun {
+    cudaGraphExec_t exec = nullptr;
+    bq_counters per_launch;  // counter increments of one launch of the graph (all systems active)
+    int slot0 = 0, nslots = 0;
+};
+
 struct BatchSlot {
     int Vh, ps, pr;
     char *b, *x, *r, *t, *rs, *xs, *p, *Ap, *to_s, *te_s, *to_d;
@@ -271,7 +278,14 @@ struct BatchWork {
     // launch tables of the 8 hopping-term steps (4 sloppy, 4 FP64), each split
     // into chunks of at most DSLASH_MAX_UNITS units, passed by value at launch
     std::vector<DslashBatchTable> tables[8];
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0, e1, t0, t1;
+    // autotuned rhs mapping of the batched hopping term, cached per batch signature
+    unsigned long long tuned_sig;
+    int tuned_mapping;
+    // instantiated graph of the iteration body, reused while its launch tables are unchanged
+    GraphRun graph;
+    unsigned long long graph_sig;
+    int graph_gen;
 };
 
 static void free_slot(BatchSlot *s) {
@@ -304,6 +318,9 @@ void bq_batch_free(bq_ctx *c) {
     cudaFree(w->stage);
     if (w->e0) cudaEventDestroy(w->e0);
     if (w->e1) cudaEventDestroy(w->e1);
+    if (w->t0) cudaEventDestroy(w->t0);
+    if (w->t1) cudaEventDestroy(w->t1);
+    if (w->graph.exec) cudaGraphExecDestroy(w->graph.exec);
     delete w;
     c->batch = nullptr;
 }
@@ -315,6 +332,8 @@ int bq_batch_reserve(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int pr) 
         if (!c0->batch) return BQ_ERR_NOMEM;
         BQ_CUDA_TRY(cudaEventCreate(&c0->batch->e0));
         BQ_CUDA_TRY(cudaEventCreate(&c0->batch->e1));
+        BQ_CUDA_TRY(cudaEventCreate(&c0->batch->t0));
+        BQ_CUDA_TRY(cudaEventCreate(&c0->batch->t1));
     }
     BatchWork *w = c0->batch;
     if (w->cap < nsys) {
@@ -391,7 +410,10 @@ static int log2_ceil(int n) {
 }
 
 // steps 0-3 sloppy (prec ps), 4-7 FP64: D_oe+A^-1, A x - k D_eo, and the two adjoint ones
-static int build_units(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int rhs_per_unit, UnitPlan *plan) {
+// mapping < 0: block-interleaved units of up to DSLASH_UNIT_RHS rhs; mapping > 0:
+// warp-interleaved units of `mapping` rhs
+static int build_units(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int mapping, UnitPlan *plan) {
+    const int rhs_per_unit = mapping < 0 ? DSLASH_UNIT_RHS : mapping;
     BatchWork *w = c0->batch;
     for (int step = 0; step < 8; step++) {
         const int prec = step < 4 ? ps : BQ_PREC_DOUBLE;
@@ -418,6 +440,7 @@ static int build_units(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int rh
             BQ_TRY(bq_dslash_unit_fill(c, prec, parity, dagger, epi, kk, &u->a));
             u->nr = e - s;
             u->log2R = log2_ceil(u->nr);
+            u->interleave = mapping < 0 ? 1 : 0;
             for (int q = 0; q < u->nr; q++) {
                 BatchSlot *sl = &w->slot[s + q];
                 void *pv[8][3] = {{sl->p, sl->to_s, nullptr},  {sl->to_s, sl->te_s, sl->p},
@@ -429,7 +452,8 @@ static int build_units(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int rh
                 u->xin[q] = pv[step][2];
                 u->sys[q] = s + q;
             }
-            const int blocks = (int)(((long long)c->Vh * (1 << u->log2R) + 127) / 128);
+            const int blocks = u->interleave ? ((c->Vh + 127) / 128) * u->nr
+                                             : (int)(((long long)c->Vh * (1 << u->log2R) + 127) / 128);
             tab.block0[tab.nunits + 1] = tab.block0[tab.nunits] + blocks;
             tab.nunits++;
             // links and clover once per site of the unit, spinors per rhs
@@ -470,6 +494,133 @@ static int mdagm_batch(bq_ctx *c0, int prec, int recon, int first_step, const Un
     return BQ_OK;
 }
 
+// Autotuner of the batched hopping term: times one sloppy Mhat^dag Mhat of the
+// batch (after one warm-up) for each rhs mapping -- block-interleaved units and
+// warp-interleaved units of 2, 4 and 8 -- and keeps the fastest for this batch
+// (same contexts, same number of systems, same precision) on later calls.
+static int tune_mapping(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int *mapping) {
+    BatchWork *w = c0->batch;
+    unsigned long long sig = 1469598103934665603ull ^ (unsigned long long)nsys ^ ((unsigned long long)ps << 40);
+    int maxrun = 1, run = 1;
+    for (int i = 0; i < nsys; i++) {
+        sig = (sig ^ (unsigned long long)(uintptr_t)ctxs[i]) * 1099511628211ull;
+        if (i > 0) run = (ctxs[i] == ctxs[i - 1]) ? run + 1 : 1;
+        maxrun = run > maxrun ? run : maxrun;
+    }
+    if (w->tuned_sig == sig) {
+        *mapping = w->tuned_mapping;
+        return BQ_OK;
+    }
+    int cand[4] = {-1, 2, 4, 8};
+    int ncand = 1;
+    for (int k = 1; k < 4; k++)
+        if (cand[k] <= maxrun) cand[ncand++] = cand[k];
+    double *h_on = w->h_flags;
+    for (int i = 0; i < nsys; i++) h_on[i] = 1.0;
+    BQ_CUDA_TRY(cudaMemcpyAsync(w->d_flags, h_on, sizeof(double) * nsys, cudaMemcpyHostToDevice, c0->stream));
+    const int recon = ctxs[0]->links_recon[ps];
+    float best = 1e30f;
+    int best_m = -1;
+    for (int k = 0; k < ncand; k++) {
+        UnitPlan plan;
+        BQ_TRY(build_units(c0, nsys, ctxs, ps, cand[k], &plan));
+        BQ_TRY(mdagm_batch(c0, ps, recon, 0, &plan, nsys, w->d_flags, 1.0));  // warm-up
+        BQ_CUDA_TRY(cudaEventRecord(w->t0, c0->stream));
+        BQ_TRY(mdagm_batch(c0, ps, recon, 0, &plan, nsys, w->d_flags, 1.0));
+        BQ_CUDA_TRY(cudaEventRecord(w->t1, c0->stream));
+        BQ_CUDA_TRY(cudaEventSynchronize(w->t1));
+        float ms = 0.f;
+        BQ_CUDA_TRY(cudaEventElapsedTime(&ms, w->t0, w->t1));
+        if (ms < best) {
+            best = ms;
+            best_m = cand[k];
+        }
+    }
+    w->tuned_sig = sig;
+    w->tuned_mapping = best_m;
+    *mapping = best_m;
+    return BQ_OK;
+}
+
+// --------------------------------------------------------------------------
+// CUDA graph of the iteration body
+
+template <typename Body>
+static int capture_iterations(bq_ctx *c0, int iters, Body &body, GraphRun *gr) {
+    if (!c0->cap_stream) BQ_CUDA_TRY(cudaStreamCreateWithFlags(&c0->cap_stream, cudaStreamNonBlocking));
+    if (c0->timing) BQ_TRY(bq_fold_events(c0));
+    const bq_counters before = c0->counters;
+    gr->slot0 = c0->ev_used;
+    cudaStream_t keep = c0->stream;
+    // the capture stream must not start before the library stream's pending work
+    BQ_CUDA_TRY(cudaStreamSynchronize(keep));
+    c0->stream = c0->cap_stream;
+    c0->capturing = 1;
+    int status = BQ_OK;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(c0->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        bq_set_error("graph capture could not start");
+        status = BQ_ERR_CUDA;
+    } else {
+        for (int k = 0; k < iters && status == BQ_OK; k++) status = body(1.0);
+        cudaError_t e = cudaStreamEndCapture(c0->stream, &graph);
+        if (status == BQ_OK && e != cudaSuccess) {
+            bq_set_error("graph capture failed: %s", cudaGetErrorString(e));
+            status = BQ_ERR_CUDA;
+        }
+    }
+    c0->capturing = 0;
+    c0->stream = keep;
+    if (status == BQ_OK && cudaGraphInstantiate(&gr->exec, graph, 0) != cudaSuccess) {
+        bq_set_error("graph instantiation failed");
+        gr->exec = nullptr;
+        status = BQ_ERR_CUDA;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    bq_counters &d = gr->per_launch;
+    d.launches = c0->counters.launches - before.launches;
+    for (int p = 0; p < 3; p++)
+        for (int e = 0; e < 3; e++) {
+            d.dslash_launches[p][e] = c0->counters.dslash_launches[p][e] - before.dslash_launches[p][e];
+            d.dslash_bytes[p][e] = c0->counters.dslash_bytes[p][e] - before.dslash_bytes[p][e];
+            d.dslash_flops[p][e] = c0->counters.dslash_flops[p][e] - before.dslash_flops[p][e];
+            d.dslash_ms[p][e] = 0;
+        }
+    c0->counters = before;
+    gr->nslots = c0->ev_used - gr->slot0;
+    c0->ev_floor = c0->ev_used;  // eager launches record above the graph's slots
+    return status;
+}
+
+static void credit_replay(bq_ctx *c0, const GraphRun &gr, double frac) {
+    c0->counters.launches += gr.per_launch.launches;
+    for (int p = 0; p < 3; p++)
+        for (int e = 0; e < 3; e++) {
+            c0->counters.dslash_launches[p][e] += gr.per_launch.dslash_launches[p][e];
+            c0->counters.dslash_bytes[p][e] += gr.per_launch.dslash_bytes[p][e] * frac;
+            c0->counters.dslash_flops[p][e] += gr.per_launch.dslash_flops[p][e] * frac;
+        }
+}
+
+static void drop_graph(bq_ctx *c0, GraphRun *gr) {
+    if (gr->exec) {
+        cudaStreamSynchronize(c0->stream);
+        if (c0->timing) bq_fold_events(c0);
+        cudaGraphExecDestroy(gr->exec);
+        gr->exec = nullptr;
+        if (c0->ev_floor == gr->slot0 + gr->nslots) {
+            c0->ev_floor = gr->slot0;
+            c0->ev_used = gr->slot0;
+        }
+    }
+}
+
+static unsigned long long fnv(unsigned long long h, const void *p, size_t n) {
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; i++) h = (h ^ b[i]) * 1099511628211ull;
+    return h;
+}
+
 // --------------------------------------------------------------------------
 // the batched solver core
 
@@ -492,7 +643,9 @@ static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double 
         hscal[(size_t)i * S_NSCAL + S_SIGMA] = shifts ? shifts[i] : sp->shift;
     }
     UnitPlan plan;
-    BQ_TRY(build_units(c0, nsys, ctxs, PS, rhs_per_unit, &plan));
+    int mapping = rhs_per_unit;
+    if (nsys > 1 && mapping == 0) BQ_TRY(tune_mapping(c0, nsys, ctxs, PS, &mapping));
+    BQ_TRY(build_units(c0, nsys, ctxs, PS, mapping, &plan));
     BQ_CUDA_TRY(cudaMemcpyAsync(w->d_sys, hs.data(), sizeof(SysVec) * nsys, cudaMemcpyHostToDevice, s));
     BQ_CUDA_TRY(cudaMemcpyAsync(w->d_scal, hscal.data(), sizeof(double) * S_NSCAL * nsys, cudaMemcpyHostToDevice, s));
     BQ_CUDA_TRY(cudaStreamSynchronize(s));
@@ -548,23 +701,67 @@ static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double 
     const double delta = (PS == BQ_PREC_DOUBLE) ? 0.0 : sp->delta;
     const int check = sp->check_every > 0 ? sp->check_every : 1;
     int it = 0;
-    while (nactive > 0) {
-        const double frac = (double)nactive / nsys;
-        kb_update_p<PS, PR><<<G, RED_THREADS, 0, s>>>(ba_act);
+    // one iteration of the whole batch, queued on c0->stream
+    auto body = [&](double frac) -> int {
+        kb_update_p<PS, PR><<<G, RED_THREADS, 0, c0->stream>>>(ba_act);
         BQ_COUNT(c0);
         BQ_TRY(mdagm_batch(c0, PS, recon_s, 0, &plan, nsys, d_active, frac));
-        kb_pap<PS><<<G, RED_THREADS, 0, s>>>(ba_act);
+        kb_pap<PS><<<G, RED_THREADS, 0, c0->stream>>>(ba_act);
         BQ_COUNT(c0);
-        kb_update_xr<PS, PR><<<G, RED_THREADS, 0, s>>>(ba_act);
+        kb_update_xr<PS, PR><<<G, RED_THREADS, 0, c0->stream>>>(ba_act);
         BQ_COUNT(c0);
         BQ_LAUNCH_CHECK();
-        it++;
+        return BQ_OK;
+    };
+    // check_every iterations captured once as a CUDA graph on a private stream
+    // and launched on the library stream; the capture's counter increments
+    // describe one launch of the graph
+    GraphRun *gp = nullptr;
+    if (c0->use_graphs) {
+        // everything the captured launches depend on: tables, vectors, grid, timing mode
+        unsigned long long sig = 1469598103934665603ull;
+        for (int step = 0; step < 4; step++)
+            sig = fnv(sig, w->tables[step].data(), sizeof(DslashBatchTable) * w->tables[step].size());
+        sig = fnv(sig, hs.data(), sizeof(SysVec) * nsys);
+        const long long misc[10] = {nsys, PS, PR, check, c0->timing, (long long)(uintptr_t)w->d_sys,
+                                    (long long)(uintptr_t)w->d_scal, (long long)(uintptr_t)w->d_flags,
+                                    (long long)(uintptr_t)w->d_part, G.x};
+        sig = fnv(sig, misc, sizeof misc);
+        if (!(w->graph.exec && w->graph_sig == sig && w->graph_gen == c0->counter_gen)) {
+            drop_graph(c0, &w->graph);
+            int gs = capture_iterations(c0, check, body, &w->graph);
+            if (gs != BQ_OK) {
+                drop_graph(c0, &w->graph);
+                return gs;
+            }
+            w->graph_sig = sig;
+            w->graph_gen = c0->counter_gen;
+        }
+        gp = &w->graph;
+    }
+    GraphRun eager_only;
+    GraphRun &gr = gp ? *gp : eager_only;
+    while (nactive > 0) {
+        const double frac = (double)nactive / nsys;
+        int n_run = 1;
+        bool replayed = false;
+        if (gr.exec && it % check == 0 && it + check <= sp->max_iter) {
+            BQ_CUDA_TRY(cudaGraphLaunch(gr.exec, s));
+            credit_replay(c0, gr, frac);
+            n_run = check;
+            replayed = true;
+        } else {
+            BQ_TRY(body(frac));
+        }
+        it += n_run;
         for (int i = 0; i < nsys; i++)
             if (active[i] != 0.0) {
-                st[i].iterations++;
-                st[i].dslash_calls += 4;
+                st[i].iterations += n_run;
+                st[i].dslash_calls += 4 * n_run;
             }
         if (it % check != 0 && it < sp->max_iter) continue;
+        BQ_TRY(read_scal());
+        if (replayed && c0->timing) BQ_TRY(bq_fold_slots(c0, gr.slot0, gr.slot0 + gr.nslots));
         BQ_TRY(read_scal());
         int nupd = 0;
         for (int i = 0; i < nsys; i++) {
@@ -609,6 +806,7 @@ static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double 
             BQ_TRY(upload_flags());
         }
     }
+    if (gr.exec && c0->timing) BQ_TRY(bq_fold_events(c0));
     return status;
 }
 
@@ -667,8 +865,7 @@ static int check_solver_params(const bq_solver_params *sp) {
 // native) and x (initial guess) in slots [0, nsys) of c0's batch workspace.
 int bq_cg_batch_core(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double *shifts, const bq_solver_params *sp,
                      bool have_x0, bq_solver_stats *st) {
-    const int rpu = nsys < DSLASH_UNIT_RHS ? nsys : DSLASH_UNIT_RHS;
-    return cg_batch_dispatch(c0, nsys, ctxs, shifts, sp, have_x0, rpu, st);
+    return cg_batch_dispatch(c0, nsys, ctxs, shifts, sp, have_x0, 0, st);
 }
 
 extern "C" int bq_solve_cg_batch(bq_ctx *const *ctxs, int nsys, double *const *x, const double *const *b, int where,
@@ -726,8 +923,7 @@ extern "C" int bq_solve_cg_batch(bq_ctx *const *ctxs, int nsys, double *const *x
         }
     }
     if (status == BQ_OK) {
-        const int rpu = nsys < DSLASH_UNIT_RHS ? nsys : DSLASH_UNIT_RHS;
-        status = cg_batch_dispatch(c0, nsys, ctxs, nullptr, sp, false, rpu, st);
+        status = cg_batch_dispatch(c0, nsys, ctxs, nullptr, sp, false, 0, st);
     }
     for (int i = 0; i < nsys && (status == BQ_OK || status == BQ_ERR_NOT_CONVERGED); i++) {
         bq_ctx *c = ctxs[i];

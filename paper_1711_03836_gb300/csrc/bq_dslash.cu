@@ -190,9 +190,17 @@ __global__ void __launch_bounds__(128) k_dslash_batch(const __grid_constant__ Ds
     int u = 0;
     while (u + 1 < tab.nunits && tab.block0[u + 1] <= (int)blockIdx.x) u++;
     const DslashUnit &U = tab.units[u];
-    const int lr = U.log2R;
-    const int t = ((int)blockIdx.x - tab.block0[u]) * blockDim.x + threadIdx.x;
-    const int r = t & ((1 << lr) - 1), h = t >> lr;
+    const int bl = (int)blockIdx.x - tab.block0[u];
+    int r, h;
+    if (U.interleave) {  // block bl: rhs bl % nr, sites of block bl / nr (neighbours in time share the links in L2)
+        r = bl % U.nr;
+        h = (bl / U.nr) * blockDim.x + threadIdx.x;
+    } else {  // rhs t % R of site t / R: the R threads of a site share link loads inside the warp
+        const int lr = U.log2R;
+        const int t = bl * blockDim.x + threadIdx.x;
+        r = t & ((1 << lr) - 1);
+        h = t >> lr;
+    }
     if (r >= U.nr || h >= U.a.Vh) return;
     if (mask && mask[U.sys[r]] == 0.0) return;
     dslash_site<PREC, RECON, DAG, EPI>(U.a, U.in[r], U.out[r], U.xin[r], h);
@@ -264,10 +272,16 @@ int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_par
     int recon = c->links_recon[prec];
     int slot = -1;
     if (c->timing) {
-        if (c->ev_used == BQ_EV_PAIRS) BQ_TRY(bq_fold_events(c));
+        if (c->ev_used == BQ_EV_PAIRS) {
+            if (c->capturing) {
+                bq_set_error("too many timed launches inside one captured graph");
+                return BQ_ERR_STATE;
+            }
+            BQ_TRY(bq_fold_events(c));
+        }
         slot = c->ev_used++;
         c->ev_bucket[slot] = prec * 3 + epi;
-        BQ_CUDA_TRY(cudaEventRecord(c->ev[2 * slot], c->stream));
+        BQ_CUDA_TRY(bq_event_record(c, c->ev[2 * slot]));
     }
     if (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) {
         if (recon == 12) launch_dslash_pr<BQ_PREC_DF64, 12>(a, dagger, epi, grid, c->stream);
@@ -283,7 +297,7 @@ int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_par
         else launch_dslash_pr<BQ_PREC_HALF, 18>(a, dagger, epi, grid, c->stream);
     }
     BQ_LAUNCH_CHECK();
-    if (slot >= 0) BQ_CUDA_TRY(cudaEventRecord(c->ev[2 * slot + 1], c->stream));
+    if (slot >= 0) BQ_CUDA_TRY(bq_event_record(c, c->ev[2 * slot + 1]));
     const double site_bytes = dslash_site_bytes(prec, recon, epi), site_flops = dslash_site_flops(epi);
     BQ_COUNT(c);
     c->counters.dslash_launches[prec][epi]++;
@@ -292,16 +306,29 @@ int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_par
     return BQ_OK;
 }
 
-int bq_fold_events(bq_ctx *c) {
-    if (!c->ev_used) return BQ_OK;
-    BQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    for (int i = 0; i < c->ev_used; i++) {
+// inside a stream capture the record becomes an external event-record node,
+// which is re-recorded at every launch of the graph
+cudaError_t bq_event_record(bq_ctx *c, cudaEvent_t ev) {
+    return c->capturing ? cudaEventRecordWithFlags(ev, c->stream, cudaEventRecordExternal) : cudaEventRecord(ev, c->stream);
+}
+
+// add the elapsed times of slots [a, b) to the counters (stream synchronised by the caller)
+int bq_fold_slots(bq_ctx *c, int a, int b) {
+    for (int i = a; i < b; i++) {
         float ms = 0.f;
         BQ_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]));
-        int b = c->ev_bucket[i];
-        c->counters.dslash_ms[b / 3][b % 3] += ms;
+        int k = c->ev_bucket[i];
+        c->counters.dslash_ms[k / 3][k % 3] += ms;
     }
-    c->ev_used = 0;
+    return BQ_OK;
+}
+
+// fold the eagerly recorded slots [ev_floor, ev_used); slots below ev_floor belong to a captured graph
+int bq_fold_events(bq_ctx *c) {
+    if (c->ev_used == c->ev_floor) return BQ_OK;
+    BQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    BQ_TRY(bq_fold_slots(c, c->ev_floor, c->ev_used));
+    c->ev_used = c->ev_floor;
     return BQ_OK;
 }
 
@@ -309,6 +336,8 @@ extern "C" int bq_reset_counters(bq_ctx *c, int timing) {
     if (!c) return BQ_ERR_ARG;
     if (c->ev_used) BQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
     c->ev_used = 0;
+    c->ev_floor = 0;
+    c->counter_gen++;
     memset(&c->counters, 0, sizeof c->counters);
     if (timing && !c->ev) {
         c->ev = (cudaEvent_t *)calloc(2 * BQ_EV_PAIRS, sizeof(cudaEvent_t));
@@ -376,10 +405,16 @@ int bq_dslash_batch_launch(bq_ctx *c, int prec, int recon, const DslashBatchTabl
     const int nblocks = tab->block0[tab->nunits];
     int slot = -1;
     if (c->timing) {
-        if (c->ev_used == BQ_EV_PAIRS) BQ_TRY(bq_fold_events(c));
+        if (c->ev_used == BQ_EV_PAIRS) {
+            if (c->capturing) {
+                bq_set_error("too many timed launches inside one captured graph");
+                return BQ_ERR_STATE;
+            }
+            BQ_TRY(bq_fold_events(c));
+        }
         slot = c->ev_used++;
         c->ev_bucket[slot] = prec * 3 + epi;
-        BQ_CUDA_TRY(cudaEventRecord(c->ev[2 * slot], c->stream));
+        BQ_CUDA_TRY(bq_event_record(c, c->ev[2 * slot]));
     }
     cudaStream_t s = c->stream;
     if (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) {
@@ -396,7 +431,7 @@ int bq_dslash_batch_launch(bq_ctx *c, int prec, int recon, const DslashBatchTabl
         else launch_batch_pr<BQ_PREC_HALF, 18>(*tab, mask, nblocks, dagger, epi, s);
     }
     BQ_LAUNCH_CHECK();
-    if (slot >= 0) BQ_CUDA_TRY(cudaEventRecord(c->ev[2 * slot + 1], c->stream));
+    if (slot >= 0) BQ_CUDA_TRY(bq_event_record(c, c->ev[2 * slot + 1]));
     BQ_COUNT(c);
     c->counters.dslash_launches[prec][epi]++;
     c->counters.dslash_bytes[prec][epi] += site_bytes_total;

@@ -96,6 +96,7 @@ extern "C" int bq_create(bq_ctx **out, const int dims[4], void *stream) {
     c->params.t_bc = -1.0;
     c->params.charge = 0.0;
     for (int p = 0; p < BQ_NPREC; p++) c->recon[p] = BQ_RECON_18;
+    c->use_graphs = 1;
     int s = bq_alloc((void **)&c->red_partials, sizeof(double) * 8 * 4096);
     if (s == BQ_OK) s = bq_alloc((void **)&c->red_ticket, sizeof(unsigned int) * 16);
     if (s == BQ_OK) s = bq_alloc((void **)&c->dev_flag, sizeof(int) * 16);
@@ -134,6 +135,7 @@ extern "C" int bq_destroy(bq_ctx *c) {
         for (int i = 0; i < 2 * BQ_EV_PAIRS; i++) cudaEventDestroy(c->ev[i]);
         free(c->ev);
     }
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     free(c);
     return BQ_OK;
 }
@@ -151,6 +153,12 @@ extern "C" int bq_set_params(bq_ctx *c, const bq_params *p) {
     int links_changed = p->charge != c->params.charge && c->A_u1;
     c->params = *p;
     invalidate_derived(c, links_changed, clover_changed);
+    return BQ_OK;
+}
+
+extern "C" int bq_set_cuda_graphs(bq_ctx *c, int enable) {
+    if (!c) return BQ_ERR_ARG;
+    c->use_graphs = enable ? 1 : 0;
     return BQ_OK;
 }
 

@@ -617,11 +617,18 @@ struct bq_ctx {
     cudaEvent_t *ev;               // 2 * BQ_EV_PAIRS events, created on first use
     int ev_bucket[4096];
     int ev_used;
+    int ev_floor;    // slots below this belong to a captured graph (folded after each launch of it)
+    int capturing;   // the library stream is being captured into a graph
+    cudaStream_t cap_stream;  // private stream used for graph capture
+    int use_graphs;           // capture the solver iteration as a CUDA graph
+    int counter_gen;          // bumped by bq_reset_counters: cached graphs re-captured
 };
 
 enum { BQ_EV_PAIRS = 4096 };
 #define BQ_COUNT(c) ((c)->counters.launches++)
 int bq_fold_events(bq_ctx *c);
+int bq_fold_slots(bq_ctx *c, int a, int b);
+cudaError_t bq_event_record(bq_ctx *c, cudaEvent_t ev);
 
 // field preparation (bq_fields.cu)
 int bq_prepare_links(bq_ctx *c, int prec);
@@ -662,7 +669,8 @@ struct DslashUnit {
     const void *xin[DSLASH_UNIT_RHS];
     int sys[DSLASH_UNIT_RHS];  // mask index of each rhs
     int nr;                    // right-hand sides in use
-    int log2R;                 // threads per site = 1 << log2R >= nr
+    int log2R;                 // warp-interleaved: threads per site = 1 << log2R >= nr
+    int interleave;            // 0: rhs interleaved inside a warp; 1: consecutive blocks take the rhs in turn
 };
 
 // a batched launch passes its units by value (kernel parameter space, read
