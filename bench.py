@@ -71,9 +71,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="32^3x64", choices=sorted(WORKLOADS))
-    ap.add_argument("--inner", default="single", choices=["single", "half"])
+    ap.add_argument("--inner", default="single", choices=["single", "half", "double"],
+                    help="precision of the inner Krylov iteration (double = plain FP64 CG)")
     ap.add_argument("--delta", type=float, default=None, help="reliable-update threshold (default 1e-3 FP32, 0.1 FP16)")
     ap.add_argument("--check-every", type=int, default=8, help="iterations between host residual checks")
+    ap.add_argument("--fp64-arith", default="df64", choices=["native", "df64"],
+                    help="arithmetic of the FP64-storage operator kernels")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 CG, sweep, e2e and CPU baseline")
     ap.add_argument("--mode", default="cg", choices=["cg", "batch12", "multishift10", "ragged4"],
                     help="the timed step: one mixed CG solve (default), 12 point sources in one batched "
@@ -217,7 +220,8 @@ def workload_name(args):
     d = "x".join(str(x) for x in wl["dims"])
     return (f"{args.workload} ({d}) even-odd clover-Wilson, kappa {wl['kappa']}, c_SW {wl['csw']}, "
             f"links exp(i {wl['eps']} A) reunitarised, antiperiodic t; mixed-precision CG "
-            f"({args.inner} inner, 12-real links, FP64 reliable updates) to true residual 1e-10")
+            f"({args.inner} inner, 12-real links, FP64-storage reliable updates in {args.fp64_arith} arithmetic) "
+            f"to true residual 1e-10")
 
 
 # ------------------------------------------------------------------ our arm
@@ -252,12 +256,13 @@ def main():
     del U
     bqcd.bq_set_recon(ctx, "single", 12)
     bqcd.bq_set_recon(ctx, "half", 12)
+    bqcd.bq_set_fp64_arith(ctx, args.fp64_arith)
     bqcd.bq_build_clover(ctx)
     Vh = lat.Vh
     b = synth.gaussian_spinor(Vh, wl["seed"] + 1000 + rank)
     b_dev = torch.from_numpy(b).cuda()
     x_dev = torch.empty_like(b_dev)
-    delta = args.delta if args.delta is not None else (1e-3 if args.inner == "single" else 1e-1)
+    delta = args.delta if args.delta is not None else {"single": 1e-3, "half": 1e-1, "double": 0.0}[args.inner]
     solve_kw = dict(tol=1e-10, precision=args.inner, delta=delta, check_every=args.check_every, max_iter=20000)
 
     step, extra_ctxs = make_step(args, torch, bqcd, synth, lat, b_dev, x_dev, solve_kw)
@@ -265,11 +270,11 @@ def main():
         step()
     torch.cuda.synchronize()
 
-    # ---- timed region: K solves, inputs resident in HBM
+    # ---- timed region: K solves, inputs resident in HBM (launch counters on, no per-launch events)
     sampler = ClockSampler(None if world == 1 else local)
     barrier()
     torch.cuda.synchronize()
-    bqcd.bq_reset_counters(ctx, timing=True)
+    bqcd.bq_reset_counters(ctx, timing=False)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stats = []
     e0.record()
@@ -278,10 +283,17 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     barrier()
-    clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
+    cnt_value = bqcd.bq_get_counters(ctx)
+    total_bytes = sum(sum(r) for r in cnt_value["dslash_bytes"])
+    # ---- second timed region, same K solves, with CUDA events around every hopping-term launch
+    # (they cost a few microseconds per launch, so the value above is timed without them)
+    bqcd.bq_reset_counters(ctx, timing=True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
     cnt = bqcd.bq_get_counters(ctx)
-    total_bytes = sum(sum(r) for r in cnt["dslash_bytes"])
     ms_max, bytes_all = ms, total_bytes
     if world > 1:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
@@ -307,17 +319,18 @@ def main():
                 "traffic": traffic, "kernel": tag, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": per_launch_bytes, "launches": n_l,
-                "avg_launch_us": per_launch_ms * 1e3, "share_of_dslash_time": cnt["dslash_ms"][bp][be] / all_ms}
+                "avg_launch_us": per_launch_ms * 1e3, "share_of_dslash_time": cnt["dslash_ms"][bp][be] / all_ms,
+                "timing": "CUDA events around each launch, second timed pass of the same K steps"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": f"{'f32' if args.inner == 'single' else 'f16-storage/f32'}+f64",
+        "vs_baseline": None, "dtype": {"single": "f32+f64", "half": "f16-storage/f32+f64", "double": "f64"}[args.inner],
         "data": "synthetic",
         "config": {"workload": workload_name(args), "lattice": list(dims), "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (FP32 links 0.4 GB + clover 1.2 GB + FP64 links 1.2 GB)"},
         "roofline": roofline,
-        "gpu_launches": cnt["launches"],
+        "gpu_launches": cnt_value["launches"],
         "clocks": clocks,
         "solve": summarize(stats[-1]),
     }
@@ -453,21 +466,32 @@ def extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, mixed_ms, torch, bqcd):
     out["e2e"] = {"value": e2e_bytes / (t1 - t0) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": Vh * 192,
                   "d2h_bytes_per_step": Vh * 192, "ms_per_step": (t1 - t0) / n_e2e * 1e3}
 
-    # ---- plain FP64 CG on the same system
-    st64 = bqcd.bq_solve_cg(ctx, x_dev, b_dev, tol=1e-10, precision="double", check_every=8, max_iter=20000)
+    # ---- plain FP64 CG on the same system, with the FP64 units and with double-float arithmetic
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    st64 = bqcd.bq_solve_cg(ctx, x_dev, b_dev, tol=1e-10, precision="double", check_every=8, max_iter=20000)
-    e1.record()
-    torch.cuda.synchronize()
-    fp64_ms = e0.elapsed_time(e1)
-    out["cg"] = {"fp64_ms": fp64_ms, "mixed_ms": mixed_ms, "speedup_mixed_vs_fp64": fp64_ms / mixed_ms,
-                 "fp64_iterations": st64["iterations"], "fp64_true_residual": st64["true_residual"]}
+    fp64 = {}
+    for mode in ("native", "df64"):
+        bqcd.bq_set_fp64_arith(ctx, mode)
+        bqcd.bq_solve_cg(ctx, x_dev, b_dev, tol=1e-10, precision="double", check_every=8, max_iter=20000)
+        e0.record()
+        st64 = bqcd.bq_solve_cg(ctx, x_dev, b_dev, tol=1e-10, precision="double", check_every=8, max_iter=20000)
+        e1.record()
+        torch.cuda.synchronize()
+        fp64[mode] = (e0.elapsed_time(e1), st64)
+    bqcd.bq_set_fp64_arith(ctx, args.fp64_arith)
+    out["cg"] = {"fp64_native_ms": fp64["native"][0], "fp64_df64_ms": fp64["df64"][0], "mixed_ms": mixed_ms,
+                 "speedup_mixed_vs_fp64_native": fp64["native"][0] / mixed_ms,
+                 "speedup_mixed_vs_fp64_df64": fp64["df64"][0] / mixed_ms,
+                 "fp64_iterations": fp64["native"][1]["iterations"],
+                 "fp64_true_residual": fp64["native"][1]["true_residual"],
+                 "fp64_df64_true_residual": fp64["df64"][1]["true_residual"]}
 
     # ---- hopping-term bandwidth sweep (plain D_hop, inputs larger than L2)
     sweep = {}
-    for prec, recon in (("double", 18), ("double", 12), ("single", 18), ("single", 12), ("half", 18), ("half", 12)):
+    for prec, recon, arith in (("double", 18, "native"), ("double", 12, "native"), ("double", 18, "df64"),
+                               ("single", 18, None), ("single", 12, None), ("half", 18, None), ("half", 12, None)):
         bqcd.bq_set_recon(ctx, prec, recon)
+        if arith:
+            bqcd.bq_set_fp64_arith(ctx, arith)
         src = lat.pack(b, prec)
         dst = lat.spinor(prec)
         for _ in range(3):
@@ -481,13 +505,16 @@ def extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, mixed_ms, torch, bqcd):
         t = e0.elapsed_time(e1) / n * 1e-3
         pid = PREC_ID[prec]
         byts = (8 * link_b(pid, recon) + 2 * SPINOR_B[pid]) * Vh
-        sweep[f"{prec}_r{recon}"] = {"GB/s": byts / t / 1e9, "GFLOP/s": 1320.0 * Vh / t / 1e9, "us": t * 1e6}
+        sweep[f"{prec}_r{recon}" + (f"_{arith}" if arith else "")] = {
+            "GB/s": byts / t / 1e9, "GFLOP/s": 1320.0 * Vh / t / 1e9, "us": t * 1e6}
+    bqcd.bq_set_recon(ctx, "double", 18)
+    bqcd.bq_set_fp64_arith(ctx, args.fp64_arith)
     bqcd.bq_set_recon(ctx, "single", 12)
     bqcd.bq_set_recon(ctx, "half", 12)
     out["dslash_sweep"] = sweep
 
     for k, v in sweep.items():
-        if k.startswith("double"):
+        if k.startswith("double") and k.endswith("native"):
             # native FP64 is bound by the FP64 units: 1.25 TFLOP/s nominal on GB300
             v["frac_of_fp64_alu_1250"] = v["GFLOP/s"] / FP64_PEAK_GFLOPS
 

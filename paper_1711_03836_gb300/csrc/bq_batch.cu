@@ -457,7 +457,7 @@ static int build_units(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int ma
             tab.block0[tab.nunits + 1] = tab.block0[tab.nunits] + blocks;
             tab.nunits++;
             // links and clover once per site of the unit, spinors per rhs
-            const int recon = c->links_recon[prec];
+            const int recon = c->links_recon[(prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) ? 3 : prec];
             const double shared = 8.0 * link_bytes_per_link(prec, recon) + clover_bytes_per_site(prec);
             const double per_rhs = dslash_site_bytes(prec, recon, epi) - shared;
             bytes += (shared + per_rhs * u->nr) * (double)c->Vh;
@@ -629,7 +629,8 @@ static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double 
                         const bq_solver_params *sp, bool have_x0, int rhs_per_unit, bq_solver_stats *st) {
     BatchWork *w = c0->batch;
     cudaStream_t s = c0->stream;
-    const int recon_s = ctxs[0]->links_recon[PS], recon_d = ctxs[0]->links_recon[BQ_PREC_DOUBLE];
+    const int recon_s = ctxs[0]->links_recon[PS];
+    const int recon_d = ctxs[0]->links_recon[ctxs[0]->fp64_arith == BQ_FP64_DF64 ? 3 : BQ_PREC_DOUBLE];
     int maxVh = 0;
     for (int i = 0; i < nsys; i++) maxVh = ctxs[i]->Vh > maxVh ? ctxs[i]->Vh : maxVh;
     const dim3 G(red_grid(maxVh), nsys);

@@ -15,6 +15,10 @@
 
 #include "bq_internal.cuh"
 
+#ifndef DF64_MIN_BLOCKS
+#define DF64_MIN_BLOCKS 3
+#endif
+
 // (1 + S gamma_mu) psi = (h0, h1, ...) in the chiral basis: the projection ...
 template <int MU, int S, typename T>
 __device__ __forceinline__ void project(const cplx<T> p[12], cplx<T> h0[3], cplx<T> h1[3]) {
@@ -173,11 +177,185 @@ __device__ __forceinline__ void dslash_site(const DslashArgs &a, const void *in,
     }
 }
 
+
+// --------------------------------------------------------------------------
+// Double-float variant with the eight hops in a rolled loop. Unrolled, the
+// df64 hop code no longer fits the instruction cache (ncu: most issue slots
+// lost to instruction fetch); rolled, one copy serves all directions and the
+// direction-dependent projector becomes data: (1 + S gamma_mu) psi has upper
+// components h0 = psi0 + i^k0 psi_j0, h1 = psi1 + i^k1 psi_j1 and lower
+// components i^k2 u_m2, i^k3 u_m3 of the colour-multiplied pair (u0, u1).
+
+__device__ __forceinline__ df dneg(df x, bool n) { return n ? df(-x.hi, -x.lo) : x; }
+
+// z * i^k, k in 0..3
+__device__ __forceinline__ cplx<df> mul_ipow(cplx<df> z, int k) {
+    const bool sw = k & 1, nre = (k == 1 || k == 2), nim = (k >= 2);
+    cplx<df> w;
+    w.re = dneg(sw ? z.im : z.re, nre);
+    w.im = dneg(sw ? z.re : z.im, nim);
+    return w;
+}
+
+template <int RECON, bool DAG, int EPI>
+__device__ __forceinline__ void dslash_site_df64(const DslashArgs &a, const void *in, void *out, const void *xin,
+                                                 const int h) {
+    using T = df;
+    const int Lxh = a.Lxh, Vh = a.Vh;
+    const int xh = h % Lxh;
+    int r = h / Lxh;
+    const int y = r % a.L1;
+    r /= a.L1;
+    const int z = r % a.L2;
+    const int t = r / a.L2;
+    const int x = 2 * xh + ((a.parity + y + z + t) & 1);
+    const char *Lo = a.links + (size_t)a.parity * 4 * a.lblk;
+    const char *Li = a.links + (size_t)(1 - a.parity) * 4 * a.lblk;
+    constexpr int SF = DAG ? +1 : -1;
+    const int sy = Lxh, sz = Lxh * a.L1, st = sz * a.L2;
+    const T cf = T(t + 1 == a.L3 ? a.cf * a.bc : a.cf), cb = T(t == 0 ? a.cb * a.bc : a.cb);
+
+    cplx<T> acc[12];
+#pragma unroll
+    for (int c = 0; c < 12; c++) acc[c] = {T(0), T(0)};
+
+#pragma unroll 1
+    for (int d = 0; d < 8; d++) {
+        const int mu = d >> 1;
+        const bool back = d & 1;
+        const int S = back ? -SF : SF;
+        int hn;
+        switch (d) {
+            case 0: hn = h - xh + (((x + 1 == a.L0) ? 0 : x + 1) >> 1); break;
+            case 1: hn = h - xh + (((x == 0) ? a.L0 - 1 : x - 1) >> 1); break;
+            case 2: hn = (y + 1 == a.L1) ? h - (a.L1 - 1) * sy : h + sy; break;
+            case 3: hn = (y == 0) ? h + (a.L1 - 1) * sy : h - sy; break;
+            case 4: hn = (z + 1 == a.L2) ? h - (a.L2 - 1) * sz : h + sz; break;
+            case 5: hn = (z == 0) ? h + (a.L2 - 1) * sz : h - sz; break;
+            case 6: hn = (t + 1 == a.L3) ? h - (a.L3 - 1) * st : h + st; break;
+            default: hn = (t == 0) ? h + (a.L3 - 1) * st : h - st; break;
+        }
+        const char *lb = (back ? Li : Lo) + (size_t)mu * a.lblk;
+        const int hl = back ? hn : h;
+        // projector data
+        int j0, j1, k0, k1, m2, m3, k2, k3;
+        if (mu == 0) {
+            j0 = 3; j1 = 2; k0 = k1 = (S > 0) ? 3 : 1;
+            m2 = 1; m3 = 0; k2 = k3 = (S > 0) ? 1 : 3;
+        } else if (mu == 1) {
+            j0 = 3; j1 = 2; k0 = (S > 0) ? 2 : 0; k1 = (S > 0) ? 0 : 2;
+            m2 = 1; m3 = 0; k2 = (S > 0) ? 0 : 2; k3 = (S > 0) ? 2 : 0;
+        } else if (mu == 2) {
+            j0 = 2; j1 = 3; k0 = (S > 0) ? 3 : 1; k1 = (S > 0) ? 1 : 3;
+            m2 = 0; m3 = 1; k2 = (S > 0) ? 1 : 3; k3 = (S > 0) ? 3 : 1;
+        } else {
+            j0 = 2; j1 = 3; k0 = k1 = (S > 0) ? 0 : 2;
+            m2 = 0; m3 = 1; k2 = k3 = (S > 0) ? 0 : 2;
+        }
+        cplx<T> psi[12];
+        SpinorIO<BQ_PREC_DF64>::load(psi, in, hn, Vh);
+        cplx<T> h0[3], h1[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const cplx<T> pa = (j0 == 3) ? psi[9 + c] : psi[6 + c];
+            const cplx<T> pb = (j1 == 3) ? psi[9 + c] : psi[6 + c];
+            h0[c] = cadd(psi[c], mul_ipow(pa, k0));
+            h1[c] = cadd(psi[3 + c], mul_ipow(pb, k1));
+        }
+        cplx<T> U[9];
+        LinkIO<BQ_PREC_DF64, RECON>::load(U, lb, hl, Vh);
+        if (back) {  // U^dagger in registers, so that one mat-vec serves both directions
+#pragma unroll
+            for (int aa = 0; aa < 3; aa++) {
+                U[aa * 4] = cconj(U[aa * 4]);
+#pragma unroll
+                for (int b = aa + 1; b < 3; b++) {
+                    const cplx<T> tmp = U[aa * 3 + b];
+                    U[aa * 3 + b] = cconj(U[b * 3 + aa]);
+                    U[b * 3 + aa] = cconj(tmp);
+                }
+            }
+        }
+        cplx<T> u0[3], u1[3];
+#pragma unroll
+        for (int aa = 0; aa < 3; aa++) {
+            u0[aa] = {T(0), T(0)};
+            u1[aa] = {T(0), T(0)};
+#pragma unroll
+            for (int b = 0; b < 3; b++) {
+                u0[aa] = cfma(U[aa * 3 + b], h0[b], u0[aa]);
+                u1[aa] = cfma(U[aa * 3 + b], h1[b], u1[aa]);
+            }
+        }
+        if (mu == 3) {
+            const T coef = back ? cb : cf;
+#pragma unroll
+            for (int aa = 0; aa < 3; aa++) {
+                u0[aa] = cscale(coef, u0[aa]);
+                u1[aa] = cscale(coef, u1[aa]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            acc[c] = cadd(acc[c], u0[c]);
+            acc[3 + c] = cadd(acc[3 + c], u1[c]);
+            acc[6 + c] = cadd(acc[6 + c], mul_ipow(m2 ? u1[c] : u0[c], k2));
+            acc[9 + c] = cadd(acc[9 + c], mul_ipow(m3 ? u1[c] : u0[c], k3));
+        }
+    }
+
+    if (EPI == EPI_PLAIN) {
+        SpinorIO<BQ_PREC_DF64>::store(out, h, Vh, acc);
+    } else if (EPI == EPI_CLOVINV) {
+        cplx<T> o[12];
+        clover_apply_site<BQ_PREC_DF64>(o, acc, a.clov, h, Vh);
+        SpinorIO<BQ_PREC_DF64>::store(out, h, Vh, o);
+    } else {
+        cplx<T> xv[12], o[12];
+        SpinorIO<BQ_PREC_DF64>::load(xv, xin, h, Vh);
+        clover_apply_site<BQ_PREC_DF64>(o, xv, a.clov, h, Vh);
+        const T k = (T)a.k;
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            o[c].re = fma(-k, acc[c].re, o[c].re);
+            o[c].im = fma(-k, acc[c].im, o[c].im);
+        }
+        SpinorIO<BQ_PREC_DF64>::store(out, h, Vh, o);
+    }
+}
+
 template <int PREC, int RECON, bool DAG, int EPI>
-__global__ void __launch_bounds__(128) k_dslash(const DslashArgs a) {
+__device__ __forceinline__ void dslash_any(const DslashArgs &a, const void *in, void *out, const void *xin,
+                                           const int h) {
+    if (PREC == BQ_PREC_DF64)
+        dslash_site_df64<RECON, DAG, EPI>(a, in, out, xin, h);
+    else
+        dslash_site<PREC, RECON, DAG, EPI>(a, in, out, xin, h);
+}
+
+// double-float kernels carry ~2x the live state; without a cap they sit at 255
+// registers and two resident blocks, too few warps to hide their dependent chains
+#ifndef PLAIN_MIN_BLOCKS
+#define PLAIN_MIN_BLOCKS 5
+#endif
+template <int PREC>
+struct DslashMinBlocks {  // FP32 and FP16 storage: enough resident warps to cover memory latency
+    static constexpr int value = PLAIN_MIN_BLOCKS;
+};
+template <>
+struct DslashMinBlocks<BQ_PREC_DOUBLE> {  // FP64-unit bound: no cap
+    static constexpr int value = 1;
+};
+template <>
+struct DslashMinBlocks<BQ_PREC_DF64> {
+    static constexpr int value = DF64_MIN_BLOCKS;
+};
+
+template <int PREC, int RECON, bool DAG, int EPI>
+__global__ void __launch_bounds__(128, DslashMinBlocks<PREC>::value) k_dslash(const DslashArgs a) {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= a.Vh) return;
-    dslash_site<PREC, RECON, DAG, EPI>(a, a.in, a.out, a.xin, h);
+    dslash_any<PREC, RECON, DAG, EPI>(a, a.in, a.out, a.xin, h);
 }
 
 // Batched launch: the grid is cut into units (one lattice, up to DSLASH_UNIT_RHS
@@ -185,8 +363,20 @@ __global__ void __launch_bounds__(128) k_dslash(const DslashArgs a) {
 // the R threads of one site sit in the same warp and one link load serves all
 // R right-hand sides. mask[sys] == 0 skips a system (converged, or not due
 // for an update).
+#ifndef BATCH_MIN_BLOCKS
+#define BATCH_MIN_BLOCKS 5
+#endif
+template <int PREC>
+struct BatchMinBlocks {
+    static constexpr int value = BATCH_MIN_BLOCKS;
+};
+template <>
+struct BatchMinBlocks<BQ_PREC_DF64> {
+    static constexpr int value = DF64_MIN_BLOCKS;
+};
+
 template <int PREC, int RECON, bool DAG, int EPI>
-__global__ void __launch_bounds__(128) k_dslash_batch(const __grid_constant__ DslashBatchTable tab, const double *mask) {
+__global__ void __launch_bounds__(128, BatchMinBlocks<PREC>::value) k_dslash_batch(const __grid_constant__ DslashBatchTable tab, const double *mask) {
     int u = 0;
     while (u + 1 < tab.nunits && tab.block0[u + 1] <= (int)blockIdx.x) u++;
     const DslashUnit &U = tab.units[u];
@@ -203,7 +393,7 @@ __global__ void __launch_bounds__(128) k_dslash_batch(const __grid_constant__ Ds
     }
     if (r >= U.nr || h >= U.a.Vh) return;
     if (mask && mask[U.sys[r]] == 0.0) return;
-    dslash_site<PREC, RECON, DAG, EPI>(U.a, U.in[r], U.out[r], U.xin[r], h);
+    dslash_any<PREC, RECON, DAG, EPI>(U.a, U.in[r], U.out[r], U.xin[r], h);
 }
 
 template <int PREC>
@@ -243,17 +433,23 @@ static void launch_dslash_pr(const DslashArgs &a, bool dag, int epi, unsigned gr
     }
 }
 
+// storage of the links and clover a launch at precision prec reads
+static int field_store(const bq_ctx *c, int prec) {
+    return (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) ? (int)BQ_PREC_DF64 : prec;
+}
+
 int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_parity, int dagger, int epi,
                      const void *xin, double k) {
-    BQ_TRY(bq_prepare_links(c, prec));
-    if (epi != EPI_PLAIN) BQ_TRY(bq_prepare_clover(c, prec));
+    const int fs = field_store(c, prec);
+    BQ_TRY(bq_prepare_links(c, fs));
+    if (epi != EPI_PLAIN) BQ_TRY(bq_prepare_clover(c, fs));
     DslashArgs a;
     a.out = out;
     a.in = in;
-    a.links = links_ptr(c, prec);
-    a.lblk = links_block_bytes(c, prec);
-    a.clov = (epi == EPI_CLOVINV) ? clover_ptr(c, prec, out_parity, 1)
-           : (epi == EPI_XPAY)    ? clover_ptr(c, prec, out_parity, 0)
+    a.links = links_ptr(c, fs);
+    a.lblk = links_block_bytes(c, fs);
+    a.clov = (epi == EPI_CLOVINV) ? clover_ptr(c, fs, out_parity, 1)
+           : (epi == EPI_XPAY)    ? clover_ptr(c, fs, out_parity, 0)
                                   : nullptr;
     a.xin = xin;
     a.L0 = c->L[0];
@@ -269,7 +465,7 @@ int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_par
     a.bc = c->params.t_bc;
     a.k = k;
     unsigned grid = (unsigned)((c->Vh + 127) / 128);
-    int recon = c->links_recon[prec];
+    int recon = c->links_recon[fs];
     int slot = -1;
     if (c->timing) {
         if (c->ev_used == BQ_EV_PAIRS) {
@@ -372,15 +568,16 @@ static void launch_batch_pr(const DslashBatchTable &tab, const double *mask, int
 // Fill the lattice-level part of a unit for one launch type (fields of c at
 // precision prec, output parity, adjoint, epilogue); the rhs pointers are the caller's.
 int bq_dslash_unit_fill(bq_ctx *c, int prec, int out_parity, int dagger, int epi, double k, DslashArgs *a) {
-    BQ_TRY(bq_prepare_links(c, prec));
-    if (epi != EPI_PLAIN) BQ_TRY(bq_prepare_clover(c, prec));
+    const int fs = field_store(c, prec);
+    BQ_TRY(bq_prepare_links(c, fs));
+    if (epi != EPI_PLAIN) BQ_TRY(bq_prepare_clover(c, fs));
     a->out = nullptr;
     a->in = nullptr;
     a->xin = nullptr;
-    a->links = links_ptr(c, prec);
-    a->lblk = links_block_bytes(c, prec);
-    a->clov = (epi == EPI_CLOVINV) ? clover_ptr(c, prec, out_parity, 1)
-            : (epi == EPI_XPAY)    ? clover_ptr(c, prec, out_parity, 0)
+    a->links = links_ptr(c, fs);
+    a->lblk = links_block_bytes(c, fs);
+    a->clov = (epi == EPI_CLOVINV) ? clover_ptr(c, fs, out_parity, 1)
+            : (epi == EPI_XPAY)    ? clover_ptr(c, fs, out_parity, 0)
                                    : nullptr;
     a->L0 = c->L[0];
     a->L1 = c->L[1];
@@ -440,8 +637,9 @@ int bq_dslash_batch_launch(bq_ctx *c, int prec, int recon, const DslashBatchTabl
 }
 
 int bq_clover_launch(bq_ctx *c, int prec, void *out, const void *in, int parity, int inverse) {
-    BQ_TRY(bq_prepare_clover(c, prec));
-    const void *cl = clover_ptr(c, prec, parity, inverse);
+    const int fs = field_store(c, prec);
+    BQ_TRY(bq_prepare_clover(c, fs));
+    const void *cl = clover_ptr(c, fs, parity, inverse);
     unsigned grid = (unsigned)((c->Vh + 127) / 128);
     if (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64)
         k_clover<BQ_PREC_DF64><<<grid, 128, 0, c->stream>>>(out, in, cl, c->Vh);

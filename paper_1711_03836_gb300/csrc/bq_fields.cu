@@ -55,7 +55,7 @@ int bq_alloc(void **p, size_t bytes) {
 static int valid_prec(int p) { return p == BQ_PREC_DOUBLE || p == BQ_PREC_SINGLE || p == BQ_PREC_HALF; }
 
 static void invalidate_derived(bq_ctx *c, int links, int clover) {
-    for (int p = 0; p < BQ_NPREC; p++) {
+    for (int p = 0; p < BQ_NFIELD; p++) {
         if (links) c->links_valid[p] = 0;
         if (clover) c->clov_valid[p] = 0;
     }
@@ -120,9 +120,11 @@ extern "C" int bq_destroy(bq_ctx *c) {
     bq_batch_free(c);
     cudaFree(c->U_canon);
     cudaFree(c->A_u1);
-    for (int p = 0; p < BQ_NPREC; p++) {
+    for (int p = 0; p < BQ_NFIELD; p++) {
         cudaFree(c->links[p]);
         if (p != BQ_PREC_DOUBLE) cudaFree(c->clov[p]);
+    }
+    for (int p = 0; p < BQ_NPREC; p++) {
         cudaFree(c->tmp_odd[p]);
         cudaFree(c->tmp_even[p]);
     }
@@ -281,8 +283,9 @@ int bq_prepare_links(bq_ctx *c, int prec) {
         bq_set_error("gauge field not set");
         return BQ_ERR_STATE;
     }
-    if (c->links_valid[prec] && c->links_recon[prec] == c->recon[prec]) return BQ_OK;
-    int recon = c->recon[prec];
+    const int rp = (prec == BQ_PREC_DF64) ? BQ_PREC_DOUBLE : prec;  // df64 pairs follow the FP64 setting
+    if (c->links_valid[prec] && c->links_recon[prec] == c->recon[rp]) return BQ_OK;
+    int recon = c->recon[rp];
     size_t blk = link_bytes_per_link(prec, recon) * (size_t)c->Vh;
     if (c->links[prec] && c->links_recon[prec] != recon) {
         cudaFree(c->links[prec]);
@@ -298,8 +301,10 @@ int bq_prepare_links(bq_ctx *c, int prec) {
         if (recon == 12) PACK(BQ_PREC_DOUBLE, 12); else PACK(BQ_PREC_DOUBLE, 18);
     } else if (prec == BQ_PREC_SINGLE) {
         if (recon == 12) PACK(BQ_PREC_SINGLE, 12); else PACK(BQ_PREC_SINGLE, 18);
-    } else {
+    } else if (prec == BQ_PREC_HALF) {
         if (recon == 12) PACK(BQ_PREC_HALF, 12); else PACK(BQ_PREC_HALF, 18);
+    } else {
+        if (recon == 12) PACK(BQ_PREC_DF64, 12); else PACK(BQ_PREC_DF64, 18);
     }
 #undef PACK
     BQ_LAUNCH_CHECK();
@@ -503,7 +508,15 @@ __global__ void k_convert_clover(char *dst, const double2 *src, int Vh, int nblk
         r[2 * k] = v.x;
         r[2 * k + 1] = v.y;
     }
-    if (PREC == BQ_PREC_SINGLE) {
+    if (PREC == BQ_PREC_DF64) {
+        float4 *d = reinterpret_cast<float4 *>(dst) + (size_t)blk * 36 * Vh + h;
+        for (int k = 0; k < 36; k++) {
+            float4 v;
+            df_split(r[2 * k], v.x, v.y);
+            df_split(r[2 * k + 1], v.z, v.w);
+            d[(size_t)k * Vh] = v;
+        }
+    } else if (PREC == BQ_PREC_SINGLE) {
         float4 *d = reinterpret_cast<float4 *>(dst) + (size_t)blk * 18 * Vh + h;
         for (int k = 0; k < 18; k++)
             d[(size_t)k * Vh] = make_float4((float)r[4 * k], (float)r[4 * k + 1], (float)r[4 * k + 2], (float)r[4 * k + 3]);
@@ -546,7 +559,7 @@ extern "C" int bq_build_clover(bq_ctx *c) {
     c->clov_master_valid = 1;
     c->clov[BQ_PREC_DOUBLE] = (char *)c->clov_master;
     c->clov_valid[BQ_PREC_DOUBLE] = 1;
-    c->clov_valid[BQ_PREC_SINGLE] = c->clov_valid[BQ_PREC_HALF] = 0;
+    c->clov_valid[BQ_PREC_SINGLE] = c->clov_valid[BQ_PREC_HALF] = c->clov_valid[BQ_PREC_DF64] = 0;
     return BQ_OK;
 }
 
@@ -557,6 +570,8 @@ int bq_prepare_clover(bq_ctx *c, int prec) {
     unsigned grid = grid_for(4LL * c->Vh, 128);
     if (prec == BQ_PREC_SINGLE)
         k_convert_clover<BQ_PREC_SINGLE><<<grid, 128, 0, c->stream>>>(c->clov[prec], (const double2 *)c->clov_master, c->Vh, 4);
+    else if (prec == BQ_PREC_DF64)
+        k_convert_clover<BQ_PREC_DF64><<<grid, 128, 0, c->stream>>>(c->clov[prec], (const double2 *)c->clov_master, c->Vh, 4);
     else
         k_convert_clover<BQ_PREC_HALF><<<grid, 128, 0, c->stream>>>(c->clov[prec], (const double2 *)c->clov_master, c->Vh, 4);
     BQ_LAUNCH_CHECK();

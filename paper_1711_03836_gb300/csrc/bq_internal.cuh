@@ -118,12 +118,13 @@ struct Traits<BQ_PREC_HALF> {
 __host__ __device__ inline size_t spinor_bytes_per_site(int prec) {
     return prec == BQ_PREC_DOUBLE ? 192 : prec == BQ_PREC_SINGLE ? 96 : 52;
 }
+// (prec 3 = double-float pairs: two floats per real, the FP64 byte count)
 __host__ __device__ inline size_t link_bytes_per_link(int prec, int recon) {
     size_t reals = (recon == BQ_RECON_12) ? 12 : 18;
-    return reals * (prec == BQ_PREC_DOUBLE ? 8 : prec == BQ_PREC_SINGLE ? 4 : 2);
+    return reals * (prec == BQ_PREC_DOUBLE || prec == 3 ? 8 : prec == BQ_PREC_SINGLE ? 4 : 2);
 }
 __host__ __device__ inline size_t clover_bytes_per_site(int prec) {
-    return 72 * (prec == BQ_PREC_DOUBLE ? 8 : prec == BQ_PREC_SINGLE ? 4 : 2);
+    return 72 * (prec == BQ_PREC_DOUBLE || prec == 3 ? 8 : prec == BQ_PREC_SINGLE ? 4 : 2);
 }
 
 // --------------------------------------------------------------------------
@@ -505,37 +506,55 @@ struct SpinorIO<BQ_PREC_DF64> {
     }
 };
 
+// df64 links: each complex entry as float4 (re.hi, re.lo, im.hi, im.lo), [entry][Vh]
+__device__ __forceinline__ void df_split(double d, float &hi, float &lo) {
+    hi = __double2float_rn(d);
+    lo = __double2float_rn(d - (double)hi);
+}
+
 template <int RECON>
 struct LinkIO<BQ_PREC_DF64, RECON> {
     using T = df;
     static constexpr int NC = (RECON == 12) ? 6 : 9;
     __device__ static __forceinline__ void load(cplx<T> U[9], const char *blk, int h, int Vh) {
-        const double2 *p = reinterpret_cast<const double2 *>(blk);
+        const float4 *p = reinterpret_cast<const float4 *>(blk);
 #pragma unroll
         for (int c = 0; c < NC; c++) {
-            double2 v = ldg(p + (size_t)c * Vh + h);
-            U[c] = {df_from_double(v.x), df_from_double(v.y)};
+            float4 v = ldg(p + (size_t)c * Vh + h);
+            U[c] = {df(v.x, v.y), df(v.z, v.w)};
         }
         if (RECON == 12) reconstruct_row2(U);
     }
+    __device__ static __forceinline__ void store(char *blk, int h, int Vh, const double2 U[9]) {
+        float4 *p = reinterpret_cast<float4 *>(blk);
+#pragma unroll
+        for (int c = 0; c < NC; c++) {
+            float4 v;
+            df_split(U[c].x, v.x, v.y);
+            df_split(U[c].y, v.z, v.w);
+            p[(size_t)c * Vh + h] = v;
+        }
+    }
 };
 
+// df64 clover: the 72 reals of a site as 36 float4 (two hi/lo pairs each), [36][Vh];
+// block b = chunks 18b .. 18b+17 (3 chunks of diagonal, 15 complex entries)
 template <>
 struct CloverIO<BQ_PREC_DF64> {
     using T = df;
     __device__ static __forceinline__ void load_block(T d[6], cplx<T> o[15], const void *base, int b, int h,
                                                       int Vh) {
-        const double2 *p = static_cast<const double2 *>(base) + (size_t)(18 * b) * Vh + h;
+        const float4 *p = static_cast<const float4 *>(base) + (size_t)(18 * b) * Vh + h;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            double2 v = ldg(p + (size_t)k * Vh);
-            d[2 * k] = df_from_double(v.x);
-            d[2 * k + 1] = df_from_double(v.y);
+            float4 v = ldg(p + (size_t)k * Vh);
+            d[2 * k] = df(v.x, v.y);
+            d[2 * k + 1] = df(v.z, v.w);
         }
 #pragma unroll
         for (int k = 0; k < 15; k++) {
-            double2 v = ldg(p + (size_t)(3 + k) * Vh);
-            o[k] = {df_from_double(v.x), df_from_double(v.y)};
+            float4 v = ldg(p + (size_t)(3 + k) * Vh);
+            o[k] = {df(v.x, v.y), df(v.z, v.w)};
         }
     }
 };
@@ -572,7 +591,7 @@ __device__ __forceinline__ void clover_apply_site(cplx<T> out[12], const cplx<T>
 // --------------------------------------------------------------------------
 // context
 
-enum { BQ_NPREC = 3 };
+enum { BQ_NPREC = 3, BQ_NFIELD = 4 };  // field storages: the three precisions + df64 pairs
 
 struct SolverWork;  // defined in the solver translation unit
 struct BatchWork;   // defined in the batched solver translation unit
@@ -593,13 +612,13 @@ struct bq_ctx {
     int have_gauge;
 
     // derived native fields, rebuilt lazily
-    char *links[BQ_NPREC];
-    int links_recon[BQ_NPREC];
-    int links_valid[BQ_NPREC];
+    char *links[BQ_NFIELD];
+    int links_recon[BQ_NFIELD];
+    int links_valid[BQ_NFIELD];
     double *clov_master;           // FP64 packed, [parity][inverse] blocks of 72*Vh reals
     int clov_master_valid;
-    char *clov[BQ_NPREC];          // [parity][inverse] blocks at each precision
-    int clov_valid[BQ_NPREC];
+    char *clov[BQ_NFIELD];         // [parity][inverse] blocks at each precision
+    int clov_valid[BQ_NFIELD];
 
     // scratch
     char *tmp_odd[BQ_NPREC];
