@@ -294,14 +294,7 @@ def main():
     torch.cuda.synchronize()
     clocks = sampler.stop()
     cnt = bqcd.bq_get_counters(ctx)
-    ms_max, bytes_all = ms, total_bytes
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-        bt = torch.tensor([total_bytes], device="cuda", dtype=torch.float64)
-        dist.all_reduce(bt, op=dist.ReduceOp.SUM)
-        bytes_all = float(bt.item())
+    ms_max, bytes_all = aggregate_ranks(ms, total_bytes, "cuda") if world > 1 else (ms, total_bytes)
     value = bytes_all / (ms_max * 1e-3) / 1e9
 
     # dominant hopping-term kernel over the timed region (CUDA events around each launch)
@@ -411,6 +404,18 @@ def batched_extras(torch, bqcd):
     for l in lats:
         l.close()
     return out
+
+
+def aggregate_ranks(ms, nbytes, device):
+    """Replicas: the job's time is the slowest rank's, its work the sum over ranks."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    b = torch.tensor([float(nbytes)], device=device, dtype=torch.float64)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(b.item())
 
 
 def summarize(st):

@@ -52,37 +52,46 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _bind(lib):
+    """Declare the C signatures on a loaded oracle library."""
+    P = ctypes.POINTER(Params)
+    dp = ctypes.c_void_p
+    L = ctypes.c_long
+    i = ctypes.c_int
+    d = ctypes.c_double
+    sig = {
+        "or_gamma": (None, [i, dp]),
+        "or_dhop": (None, [P, dp, dp, dp, i, i, dp]),
+        "or_dhop_sites": (None, [P, dp, dp, dp, i, i, L, dp, dp]),
+        "or_clover_field": (None, [P, dp, i, dp]),
+        "or_clover_invert": (L, [L, dp, dp]),
+        "or_clover_apply": (None, [L, dp, dp, i, dp]),
+        "or_clover_sites": (i, [P, dp, i, i, L, dp, dp, dp]),
+        "or_mhat": (None, [P, dp, dp, dp, dp, dp, i, dp]),
+        "or_mdagm": (None, [P, dp, dp, dp, dp, dp, d, dp]),
+        "or_mhat_sites": (i, [P, dp, dp, dp, i, L, dp, dp]),
+        "or_cg": (i, [P, dp, dp, dp, dp, dp, d, d, i, dp]),
+        "or_num_threads": (i, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_LIB)
-            P = ctypes.POINTER(Params)
-            dp = ctypes.c_void_p
-            L = ctypes.c_long
-            i = ctypes.c_int
-            d = ctypes.c_double
-            sig = {
-                "or_gamma": (None, [i, dp]),
-                "or_dhop": (None, [P, dp, dp, dp, i, i, dp]),
-                "or_dhop_sites": (None, [P, dp, dp, dp, i, i, L, dp, dp]),
-                "or_clover_field": (None, [P, dp, i, dp]),
-                "or_clover_invert": (L, [L, dp, dp]),
-                "or_clover_apply": (None, [L, dp, dp, i, dp]),
-                "or_clover_sites": (i, [P, dp, i, i, L, dp, dp, dp]),
-                "or_mhat": (None, [P, dp, dp, dp, dp, dp, i, dp]),
-                "or_mdagm": (None, [P, dp, dp, dp, dp, dp, d, dp]),
-                "or_mhat_sites": (i, [P, dp, dp, dp, i, L, dp, dp]),
-                "or_cg": (i, [P, dp, dp, dp, dp, dp, d, d, i, dp]),
-                "or_num_threads": (i, []),
-            }
-            for name, (res, args) in sig.items():
-                f = getattr(lib, name)
-                f.restype = res
-                f.argtypes = args
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(_LIB))
     return _lib
+
+
+def load_library(path):
+    """Load another build of the oracle's C source (used by the mutation tests)."""
+    return _bind(ctypes.CDLL(path))
 
 
 def _ptr(a):
