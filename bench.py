@@ -41,6 +41,8 @@ sys.path.insert(0, ROOT)
 METRIC = "Dslash GB/s vs HBM peak; mixed/batched vs FP64 CG time to |r|/|b|<1e-10"
 
 WORKLOADS = {
+    "48^3x96": dict(dims=(48, 48, 48, 96), eps=0.15, kappa=0.1355, csw=1.9, mu=0.0, seed=5, u1_sigma=0.1,
+                    charges=(2.0 / 3.0, -1.0 / 3.0)),
     "32^3x64": dict(dims=(32, 32, 32, 64), eps=0.15, kappa=0.1355, csw=1.9, mu=0.0, seed=1),
     "24^3x48": dict(dims=(24, 24, 24, 48), eps=0.2, kappa=0.1350, csw=1.7, mu=0.0, seed=1),
     "20^3x40": dict(dims=(20, 20, 20, 40), eps=0.2, kappa=0.1350, csw=1.7, mu=0.0, seed=1),
@@ -78,9 +80,10 @@ def parse():
     ap.add_argument("--fp64-arith", default="df64", choices=["native", "df64"],
                     help="arithmetic of the FP64-storage operator kernels")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 CG, sweep, e2e and CPU baseline")
-    ap.add_argument("--mode", default="cg", choices=["cg", "batch12", "multishift10", "ragged4"],
+    ap.add_argument("--mode", default="cg", choices=["cg", "batch12", "multishift10", "ragged4", "qed2x4"],
                     help="the timed step: one mixed CG solve (default), 12 point sources in one batched "
-                         "solve, a 10-shift multishift solve, or a ragged batch of four lattices")
+                         "solve, a 10-shift multishift solve, a ragged batch of four lattices, or (48^3x96) "
+                         "4 Gaussian sources for each of the two QED flavours in one batched solve")
     return ap.parse_args()
 
 
@@ -173,8 +176,10 @@ def oracle_setup(wl):
     from paper_1711_03836_gb300 import synth
 
     U = synth.gauge_field(wl["dims"], wl["eps"], wl["seed"])
-    p = oracle.params(wl["dims"], kappa=wl["kappa"], csw=wl["csw"], mu=wl["mu"], t_bc=-1.0)
-    op = oracle.Operator(p, U)
+    A = synth.u1_field(wl["dims"], wl["u1_sigma"], wl["seed"] + 1) if "u1_sigma" in wl else None
+    charge = wl.get("charges", (0.0,))[0]
+    p = oracle.params(wl["dims"], kappa=wl["kappa"], csw=wl["csw"], mu=wl["mu"], t_bc=-1.0, charge=charge)
+    op = oracle.Operator(p, U, A)
     Vh = oracle.half_volume(p)
     b = synth.gaussian_spinor(Vh, wl["seed"] + 1000)
     return op, b, Vh
@@ -218,9 +223,12 @@ def run_reference(args):
 def workload_name(args):
     wl = WORKLOADS[args.workload]
     d = "x".join(str(x) for x in wl["dims"])
+    qed = (f" times U(1) phases exp(-i Q A_mu), sigma_A {wl['u1_sigma']}, Q in {list(wl['charges'])}"
+           if "u1_sigma" in wl else "")
     return (f"{args.workload} ({d}) even-odd clover-Wilson, kappa {wl['kappa']}, c_SW {wl['csw']}, "
-            f"links exp(i {wl['eps']} A) reunitarised, antiperiodic t; mixed-precision CG "
-            f"({args.inner} inner, 12-real links, FP64-storage reliable updates in {args.fp64_arith} arithmetic) "
+            f"links exp(i {wl['eps']} A) reunitarised{qed}, antiperiodic t; mixed-precision CG "
+            f"({args.inner} inner, {'18' if 'u1_sigma' in wl else '12'}-real links, FP64-storage reliable updates "
+            f"in {args.fp64_arith} arithmetic) "
             f"to true residual 1e-10")
 
 
@@ -250,12 +258,17 @@ def main():
     wl = WORKLOADS[args.workload]
     dims = wl["dims"]
     U = synth.gauge_field(dims, wl["eps"], wl["seed"])
-    lat = bqcd.Lattice(dims, wl["kappa"], wl["csw"], wl["mu"], -1.0)
+    A = synth.u1_field(dims, wl["u1_sigma"], wl["seed"] + 1) if "u1_sigma" in wl else None
+    charges = wl.get("charges", (0.0,))
+    lat = bqcd.Lattice(dims, wl["kappa"], wl["csw"], wl["mu"], -1.0, charges[0])
     ctx = lat.ctx
     bqcd.bq_set_gauge(ctx, U)
-    del U
-    bqcd.bq_set_recon(ctx, "single", 12)
-    bqcd.bq_set_recon(ctx, "half", 12)
+    if A is not None:
+        bqcd.bq_set_u1(ctx, A)
+    else:
+        bqcd.bq_set_recon(ctx, "single", 12)
+        bqcd.bq_set_recon(ctx, "half", 12)
+    field_inputs = (U, A)
     bqcd.bq_set_fp64_arith(ctx, args.fp64_arith)
     bqcd.bq_build_clover(ctx)
     Vh = lat.Vh
@@ -265,7 +278,8 @@ def main():
     delta = args.delta if args.delta is not None else {"single": 1e-3, "half": 1e-1, "double": 0.0}[args.inner]
     solve_kw = dict(tol=1e-10, precision=args.inner, delta=delta, check_every=args.check_every, max_iter=20000)
 
-    step, extra_ctxs = make_step(args, torch, bqcd, synth, lat, b_dev, x_dev, solve_kw)
+    step, extra_ctxs = make_step(args, torch, bqcd, synth, lat, b_dev, x_dev, solve_kw, field_inputs)
+    del field_inputs, U, A
     for _ in range(max(args.warmup, 0)):
         step()
     torch.cuda.synchronize()
@@ -426,9 +440,20 @@ def summarize(st):
             "converged": int(all(x["converged"] for x in sts))}
 
 
-def make_step(args, torch, bqcd, synth, lat, b_dev, x_dev, solve_kw):
+def make_step(args, torch, bqcd, synth, lat, b_dev, x_dev, solve_kw, field_inputs):
     """The timed step of each mode; returns (callable, extra lattices to close)."""
     ctx = lat.ctx
+    if args.mode == "qed2x4":
+        wl = WORKLOADS[args.workload]
+        U, A = field_inputs
+        other = bqcd.Lattice(wl["dims"], wl["kappa"], wl["csw"], wl["mu"], -1.0, wl["charges"][1])
+        bqcd.bq_set_gauge(other.ctx, U)
+        bqcd.bq_set_u1(other.ctx, A)
+        bqcd.bq_set_fp64_arith(other.ctx, args.fp64_arith)
+        bs = [torch.from_numpy(synth.gaussian_spinor(lat.Vh, 700 + i)).cuda() for i in range(8)]
+        xs = [torch.empty_like(b) for b in bs]
+        ctxs = [ctx] * 4 + [other.ctx] * 4
+        return (lambda: bqcd.bq_solve_cg_batch(ctxs, xs, bs, **solve_kw)), [other]
     if args.mode == "cg":
         return (lambda: bqcd.bq_solve_cg(ctx, x_dev, b_dev, **solve_kw)), []
     if args.mode == "batch12":

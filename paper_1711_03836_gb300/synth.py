@@ -6,8 +6,9 @@ This module only draws inputs; it contains none of the operator's arithmetic
 
 * links: U = exp(i eps A) with A = sum_a w_a lambda_a / 2, w_a ~ N(0, 1), drawn
   with numpy's PCG64 ``default_rng(seed)`` in lex order (site, mu, a); the
-  exponential comes from the Hermitian eigendecomposition, then U is projected
-  back onto SU(3) (Gram-Schmidt on rows 1-2, row 3 = conj(row1 x row2)).
+  exponential is torch's multithreaded matrix_exp on the CPU (scaling and
+  squaring), then U is projected back onto SU(3) (Gram-Schmidt on rows 1-2,
+  row 3 = conj(row1 x row2)).
 * U(1) angles A_mu(x) ~ N(0, sigma^2), i.i.d.
 * spinors: real and imaginary parts ~ N(0, 1), i.i.d. per component.
 
@@ -59,10 +60,11 @@ def reunitarise(U: np.ndarray) -> np.ndarray:
 
 def su3_near_identity(n: int, eps: float, rng: np.random.Generator) -> np.ndarray:
     """n matrices exp(i eps A), A Gaussian traceless Hermitian, reunitarised."""
+    import torch
+
     w = rng.standard_normal((n, 8))
     H = np.einsum("na,aij->nij", w, GELL_MANN / 2)
-    lam, vec = np.linalg.eigh(H)
-    U = (vec * np.exp(1j * eps * lam)[:, None, :]) @ vec.conj().transpose(0, 2, 1)
+    U = torch.linalg.matrix_exp(torch.from_numpy(1j * eps * H)).numpy()
     return reunitarise(U)
 
 
