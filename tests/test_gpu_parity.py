@@ -443,3 +443,34 @@ def test_config5_qed_48x96(bq):
         assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(bs[i].cpu().numpy())
     for lat in lats:
         lat.close()
+
+
+@pytest.mark.parametrize("cfg", ["32^3x64", "16^3x32 mu=0.1"])
+def test_apply_error_report(bq, cfg, capsys):
+    """States the per-apply error of every storage/arithmetic against the FP64
+    oracle (sampled sites, Mhat), and checks it against the tolerances."""
+    if cfg.startswith("32"):
+        dims, eps, kappa, csw, mu = (32, 32, 32, 64), 0.15, 0.1355, 1.9, 0.0
+    else:
+        dims, eps, kappa, csw, mu = (16, 16, 16, 32), 0.2, 0.1350, 1.7, 0.1
+    U = synth.gauge_field(dims, eps, 1)
+    lat = bq.Lattice(dims, kappa, csw, mu, -1.0)
+    bq.bq_set_gauge(lat.ctx, U)
+    p = oracle.params(dims, kappa=kappa, csw=csw, mu=mu, t_bc=-1.0)
+    psi = synth.gaussian_spinor(lat.Vh, 9)
+    sites = np.unique(np.random.default_rng(2).integers(0, lat.Vh, 64))
+    ref = oracle.mhat_sites(p, U, None, psi, sites)
+    lines = []
+    for prec, recon, arith in (("double", 18, "native"), ("double", 18, "df64"), ("double", 12, "df64"),
+                               ("single", 18, None), ("single", 12, None), ("half", 18, None), ("half", 12, None)):
+        bq.bq_set_recon(lat.ctx, prec, recon)
+        if arith:
+            bq.bq_set_fp64_arith(lat.ctx, arith)
+        out = lat.spinor(prec)
+        bq.bq_apply_mhat(lat.ctx, out, lat.pack(psi, prec), 0, prec)
+        err = rel(lat.unpack(out, prec)[sites], ref)
+        lines.append(f"APPLY-ERROR {cfg} {prec} r{recon} {arith or ''} {err:.3e}")
+        assert err < TOL[prec]
+    lat.close()
+    with capsys.disabled():
+        print("\n" + "\n".join(lines))
