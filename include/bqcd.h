@@ -53,6 +53,7 @@ enum { BQ_PREC_DOUBLE = 0, BQ_PREC_SINGLE = 1, BQ_PREC_HALF = 2 };
 enum { BQ_RECON_18 = 18, BQ_RECON_12 = 12 };
 enum { BQ_HOST = 0, BQ_DEVICE = 1 };
 enum { BQ_FP64_NATIVE = 0, BQ_FP64_DF64 = 1 };
+enum { BQ_SOLVER_CG = 0, BQ_SOLVER_BICGSTAB = 1 };
 
 typedef struct bq_ctx bq_ctx;
 
@@ -244,6 +245,27 @@ int bq_solve_cg_batch(bq_ctx *const *ctx, int nsys, double *const *x, const doub
 int bq_solve_multishift_cg(bq_ctx *ctx, double *const *x, const double *b, int where, int nshift,
                            const double *shifts, const bq_solver_params *params, bq_solver_stats *stats,
                            double *residuals);
+
+/* Full-lattice solve of M x = b, M = A - kappa D_hop (Eq. 1, Eq. 2), through
+ * the even-odd reduction (Section 4: the matrix is even-odd preconditioned):
+ *     bhat_e = b_e + kappa D_eo A_oo^{-1} b_o,   Mhat x_e = bhat_e,
+ *     x_o = A_oo^{-1} (b_o + kappa D_oe x_e).
+ * method BQ_SOLVER_CG solves Mhat x_e = bhat_e by (mixed-precision) CG on
+ * Mhat^dag Mhat with Mhat^dag bhat_e as right-hand side, restarted from the
+ * current x_e until the even residual meets the target; BQ_SOLVER_BICGSTAB
+ * (Section 4 lists BiCGstab) runs BiCGstab on Mhat itself, in FP64 or, for
+ * params->precision SINGLE/HALF, as FP64 defect correction around a BiCGstab
+ * in that precision which reduces its own residual by params->delta
+ * (0 = 1e-3) per outer step. params->shift must be 0.
+ * b_e, b_o, x_e, x_o: canonical spinors [V/2][4][3] complex of the even and
+ * odd parity, on the host or the device as `where` says; x is overwritten
+ * (the solve starts from 0). stats->true_residual = |b - M x| / |b| over both
+ * parities, computed in FP64 after the reconstruction; BQ_ERR_NOT_CONVERGED
+ * when it stays above params->tol (x then holds the last iterate), also when
+ * BiCGstab breaks down (rho or omega 0). b = 0 gives x = 0. Allocates and frees
+ * its own 18 half-lattice work vectors per call. */
+int bq_solve_full(bq_ctx *ctx, double *x_e, double *x_o, const double *b_e, const double *b_o, int where,
+                  int method, const bq_solver_params *params, bq_solver_stats *stats);
 
 #ifdef __cplusplus
 }

@@ -187,7 +187,8 @@ class Operator:
         self.U = _c128(U)
         self.A = None if A is None else np.ascontiguousarray(A, np.float64)
         self.Aee = clover_field(p, self.U, 0)
-        self.Aoo_inv = clover_invert(clover_field(p, self.U, 1))
+        self.Aoo = clover_field(p, self.U, 1)
+        self.Aoo_inv = clover_invert(self.Aoo)
 
     def mhat(self, psi, dagger=False):
         """Mhat psi = A_ee psi - kappa^2 D_eo A_oo^{-1} D_oe psi (or its adjoint)."""
@@ -215,6 +216,24 @@ class Operator:
     def multishift(self, b, shifts, tol=1e-10, maxiter=10000):
         """Multishift reference: one independent CG per shift."""
         return [self.cg(b, s, tol, maxiter)[0] for s in shifts]
+
+    def full(self, x_e, x_o):
+        """M x = (A - kappa D_hop) x on the whole lattice (Eq. 1, Eq. 2), as its
+        even and odd halves: (M x)_p = A_pp x_p - kappa D_{p,1-p} x_{1-p}."""
+        k = self.p.kappa
+        y_e = clover_apply(self.Aee, x_e) - k * dhop(self.p, self.U, self.A, x_o, 0)
+        y_o = clover_apply(self.Aoo, x_o) - k * dhop(self.p, self.U, self.A, x_e, 1)
+        return y_e, y_o
+
+    def solve_full(self, b_e, b_o, tol=1e-12, maxiter=20000):
+        """x with M x = b by block elimination of the odd sites: CG on
+        Mhat^dag Mhat x_e = Mhat^dag (b_e + kappa D_eo A_oo^{-1} b_o), then
+        x_o = A_oo^{-1} (b_o + kappa D_oe x_e)."""
+        k = self.p.kappa
+        bhat = _c128(b_e) + k * dhop(self.p, self.U, self.A, clover_apply(self.Aoo_inv, b_o), 0)
+        x_e, _ = self.cg(self.mhat(bhat, dagger=True), tol=tol, maxiter=maxiter)
+        x_o = clover_apply(self.Aoo_inv, _c128(b_o) + k * dhop(self.p, self.U, self.A, x_e, 1))
+        return x_e, x_o
 
 
 def mhat_sites(p, U, A, psi, sites, dagger=False):

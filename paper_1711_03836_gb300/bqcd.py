@@ -23,6 +23,8 @@ BQ_PREC_DOUBLE, BQ_PREC_SINGLE, BQ_PREC_HALF = 0, 1, 2
 BQ_RECON_18, BQ_RECON_12 = 18, 12
 BQ_HOST, BQ_DEVICE = 0, 1
 BQ_FP64_NATIVE, BQ_FP64_DF64 = 0, 1
+BQ_SOLVER_CG, BQ_SOLVER_BICGSTAB = 0, 1
+SOLVER_NAMES = {"cg": BQ_SOLVER_CG, "bicgstab": BQ_SOLVER_BICGSTAB, 0: 0, 1: 1}
 PREC_NAMES = {"double": 0, "single": 1, "half": 2, 0: 0, 1: 1, 2: 2}
 
 
@@ -108,6 +110,9 @@ _SIGS = {
                                               ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(bq_solver_params), ctypes.POINTER(bq_solver_stats),
                                               ctypes.POINTER(ctypes.c_double)]),
+    "bq_solve_full": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(bq_solver_params),
+                                     ctypes.POINTER(bq_solver_stats)]),
 }
 
 
@@ -334,6 +339,22 @@ def bq_solve_multishift_cg(ctx, xs, b, shifts, tol=1e-10, max_iter=20000, precis
     d = st.as_dict()
     d["residuals"] = list(res)
     return d
+
+
+def bq_solve_full(ctx, x_e, x_o, b_e, b_o, method="bicgstab", tol=1e-10, max_iter=20000, precision="double",
+                  delta=1e-3, check_every=8, raise_on_nonconvergence=True):
+    """Solve M x = b on the full lattice (even and odd halves, canonical, all host or all device)."""
+    ptrs = [_ptr_where(v) for v in (x_e, x_o, b_e, b_o)]
+    where = ptrs[0][1]
+    if any(w != where for _, w in ptrs):
+        raise ValueError("x_e, x_o, b_e, b_o must all be host or all be device buffers")
+    sp = bq_solver_params(tol, int(max_iter), PREC_NAMES[precision], delta, int(check_every), 0.0)
+    st = bq_solver_stats()
+    s = _lib_handle().bq_solve_full(ctx, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], where,
+                                    SOLVER_NAMES[method], ctypes.byref(sp), ctypes.byref(st))
+    if s != BQ_OK and (raise_on_nonconvergence or s != BQ_ERR_NOT_CONVERGED):
+        raise BqError(s, "bq_solve_full")
+    return st.as_dict()
 
 
 # ---------------------------------------------------------------- convenience

@@ -821,7 +821,7 @@ static int cg_batch_dispatch(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const do
 }
 
 // check a batch: same sloppy recon and FP64 arithmetic everywhere; fields prepared
-static int batch_prepare(int nsys, bq_ctx *const *ctxs, int ps) {
+int bq_batch_prepare(int nsys, bq_ctx *const *ctxs, int ps) {
     for (int i = 0; i < nsys; i++) {
         bq_ctx *c = ctxs[i];
         if (!c) {
@@ -882,7 +882,7 @@ extern "C" int bq_solve_cg_batch(bq_ctx *const *ctxs, int nsys, double *const *x
             return BQ_ERR_ARG;
         }
     const int ps = sp->precision, pr = (ps == BQ_PREC_HALF) ? BQ_PREC_SINGLE : ps;
-    BQ_TRY(batch_prepare(nsys, ctxs, ps));
+    BQ_TRY(bq_batch_prepare(nsys, ctxs, ps));
     bq_ctx *c0 = ctxs[0];
     BQ_TRY(bq_batch_reserve(c0, nsys, ctxs, ps, pr));
     bq_solver_stats *st = stats;

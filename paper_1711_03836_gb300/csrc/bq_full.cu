@@ -1,0 +1,404 @@
+// bq_full.cu -- the full-lattice system M x = b (M = A - kappa D_hop, Eq. 1-2)
+// through its even-odd reduction, and BiCGstab on Mhat (Section 3 lists
+// BiCGstab among BQCD's solvers; it needs no gamma_5-hermiticity, so it also
+// serves mu != 0, where Mhat^dag != gamma_5 Mhat gamma_5).
+//
+//   bhat_e = b_e + kappa D_eo A_oo^{-1} b_o
+//   Mhat x_e = bhat_e      (CG on Mhat^dag Mhat, or BiCGstab on Mhat)
+//   x_o = A_oo^{-1} (b_o + kappa D_oe x_e)
+//   r = b - M x on both parities, from two fused launches (A x - kappa D y).
+//
+// Mixed-precision BiCGstab is FP64 defect correction: r = bhat - Mhat x in
+// FP64, an FP32 (or FP16-storage) BiCGstab solves Mhat d = r until its own
+// residual fell by delta, x += d, repeat.
+#include <math.h>
+#include <string.h>
+
+#include <complex>
+
+#include "bq_reduce.cuh"
+
+using zc = std::complex<double>;
+
+// out = a x + b y + c z (complex coefficients; null operands are skipped; out may alias an operand)
+template <int P>
+__global__ void __launch_bounds__(256) k_caxpbypcz(void *out, double2 a, const void *x, double2 b, const void *y,
+                                                   double2 c, const void *z, int Vh) {
+    using T = typename Traits<P>::real;
+    const cplx<T> ca = {(T)a.x, (T)a.y}, cb = {(T)b.x, (T)b.y}, cc = {(T)c.x, (T)c.y};
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<T> o[12], v[12];
+#pragma unroll
+        for (int k = 0; k < 12; k++) o[k] = {T(0), T(0)};
+        if (x) {
+            SpinorIO<P>::load(v, x, h, Vh);
+#pragma unroll
+            for (int k = 0; k < 12; k++) o[k] = cfma(ca, v[k], o[k]);
+        }
+        if (y) {
+            SpinorIO<P>::load(v, y, h, Vh);
+#pragma unroll
+            for (int k = 0; k < 12; k++) o[k] = cfma(cb, v[k], o[k]);
+        }
+        if (z) {
+            SpinorIO<P>::load(v, z, h, Vh);
+#pragma unroll
+            for (int k = 0; k < 12; k++) o[k] = cfma(cc, v[k], o[k]);
+        }
+        SpinorIO<P>::store(out, h, Vh, o);
+    }
+}
+
+// out (precision PO) = in (precision PI)
+template <int PO, int PI>
+__global__ void __launch_bounds__(256) k_convert_spinor(void *out, const void *in, int Vh) {
+    using TI = typename Traits<PI>::real;
+    using TO = typename Traits<PO>::real;
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<TI> v[12];
+        cplx<TO> o[12];
+        SpinorIO<PI>::load(v, in, h, Vh);
+#pragma unroll
+        for (int k = 0; k < 12; k++) o[k] = {(TO)v[k].re, (TO)v[k].im};
+        SpinorIO<PO>::store(out, h, Vh, o);
+    }
+}
+
+// x (FP64) += d (precision PI)
+template <int PI>
+__global__ void __launch_bounds__(256) k_add_to_double(void *x, const void *d, int Vh) {
+    using TI = typename Traits<PI>::real;
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<double> xv[12];
+        cplx<TI> dv[12];
+        SpinorIO<BQ_PREC_DOUBLE>::load(xv, x, h, Vh);
+        SpinorIO<PI>::load(dv, d, h, Vh);
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            xv[k].re += (double)dv[k].re;
+            xv[k].im += (double)dv[k].im;
+        }
+        SpinorIO<BQ_PREC_DOUBLE>::store(x, h, Vh, xv);
+    }
+}
+
+int bq_dot_launch(bq_ctx *c, const void *a, const void *b, int prec, double *partials, unsigned int *ticket,
+                  double *out_dev);
+
+namespace {
+
+// FP64 vectors of the reduction and reconstruction, inner-precision vectors of BiCGstab
+struct FullWork {
+    char *be, *bo, *xe, *xo, *bh, *r, *to, *te, *ye;
+    char *ib, *ix, *ir, *ir0, *ip, *iv, *is, *it, *itmp;
+};
+
+int grid_of(const bq_ctx *c) {
+    int g = (c->Vh + 255) / 256;
+    return g < 1024 ? g : 1024;
+}
+
+int axpy3(bq_ctx *c, int prec, void *out, zc a, const void *x, zc b, const void *y, zc cc, const void *z) {
+    const double2 da = make_double2(a.real(), a.imag()), db = make_double2(b.real(), b.imag()),
+                  dc = make_double2(cc.real(), cc.imag());
+    const int G = grid_of(c);
+    if (prec == BQ_PREC_DOUBLE)
+        k_caxpbypcz<BQ_PREC_DOUBLE><<<G, 256, 0, c->stream>>>(out, da, x, db, y, dc, z, c->Vh);
+    else if (prec == BQ_PREC_SINGLE)
+        k_caxpbypcz<BQ_PREC_SINGLE><<<G, 256, 0, c->stream>>>(out, da, x, db, y, dc, z, c->Vh);
+    else
+        k_caxpbypcz<BQ_PREC_HALF><<<G, 256, 0, c->stream>>>(out, da, x, db, y, dc, z, c->Vh);
+    BQ_LAUNCH_CHECK();
+    BQ_COUNT(c);
+    return BQ_OK;
+}
+
+// <a, b> as a host complex number (synchronises the stream)
+int dotc(bq_ctx *c, int prec, const void *a, const void *b, zc *out) {
+    double *res = c->red_partials + 2 * RED_MAX_BLOCKS;
+    BQ_TRY(bq_dot_launch(c, a, b, prec, c->red_partials, c->red_ticket, res));
+    double h[2] = {0.0, 0.0};
+    BQ_CUDA_TRY(cudaMemcpyAsync(h, res, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    BQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    *out = zc(h[0], h[1]);
+    return BQ_OK;
+}
+
+int convert(bq_ctx *c, void *out, int po, const void *in, int pi) {
+    const int G = grid_of(c);
+    if (po == pi) {
+        BQ_CUDA_TRY(cudaMemcpyAsync(out, in, spinor_bytes_per_site(po) * (size_t)c->Vh, cudaMemcpyDeviceToDevice,
+                                    c->stream));
+        return BQ_OK;
+    }
+    if (po == BQ_PREC_SINGLE && pi == BQ_PREC_DOUBLE)
+        k_convert_spinor<BQ_PREC_SINGLE, BQ_PREC_DOUBLE><<<G, 256, 0, c->stream>>>(out, in, c->Vh);
+    else if (po == BQ_PREC_HALF && pi == BQ_PREC_DOUBLE)
+        k_convert_spinor<BQ_PREC_HALF, BQ_PREC_DOUBLE><<<G, 256, 0, c->stream>>>(out, in, c->Vh);
+    else {
+        bq_set_error("unsupported spinor conversion");
+        return BQ_ERR_ARG;
+    }
+    BQ_LAUNCH_CHECK();
+    BQ_COUNT(c);
+    return BQ_OK;
+}
+
+int add_to_double(bq_ctx *c, void *x, const void *d, int pd) {
+    const int G = grid_of(c);
+    if (pd == BQ_PREC_SINGLE) k_add_to_double<BQ_PREC_SINGLE><<<G, 256, 0, c->stream>>>(x, d, c->Vh);
+    else if (pd == BQ_PREC_HALF) k_add_to_double<BQ_PREC_HALF><<<G, 256, 0, c->stream>>>(x, d, c->Vh);
+    else k_add_to_double<BQ_PREC_DOUBLE><<<G, 256, 0, c->stream>>>(x, d, c->Vh);
+    BQ_LAUNCH_CHECK();
+    BQ_COUNT(c);
+    return BQ_OK;
+}
+
+// BiCGstab (van der Vorst) on Mhat x = b at precision prec, from x = 0, until
+// |r| <= tol_abs or max_iter iterations. Nine distinct vectors: b, x, r, r0,
+// p, v, s, t and the odd-parity temporary of Mhat. When |<r0, r>| falls below
+// 1e-6 |r0| |r| the shadow residual is replaced by r and the recurrences
+// restart; near the critical kappa this keeps the method from stagnating.
+struct Bicg {
+    void *b, *x, *r, *r0, *p, *v, *s, *t, *tmp_o;
+};
+
+int bicgstab(bq_ctx *c, int prec, const Bicg &w, double tol_abs, int max_iter, int *iters, double *dslash) {
+    const zc one(1, 0), zero(0, 0);
+    BQ_TRY(axpy3(c, prec, w.x, zero, nullptr, zero, nullptr, zero, nullptr));
+    BQ_TRY(axpy3(c, prec, w.r, one, w.b, zero, nullptr, zero, nullptr));
+    BQ_TRY(axpy3(c, prec, w.r0, one, w.b, zero, nullptr, zero, nullptr));
+    BQ_TRY(axpy3(c, prec, w.p, zero, nullptr, zero, nullptr, zero, nullptr));
+    BQ_TRY(axpy3(c, prec, w.v, zero, nullptr, zero, nullptr, zero, nullptr));
+    zc rho(1, 0), alpha(1, 0), omega(1, 0), rr;
+    BQ_TRY(dotc(c, prec, w.r, w.r, &rr));
+    *iters = 0;
+    double r0n = rr.real();  // |r0|^2 of the current shadow residual
+    if (rr.real() <= tol_abs * tol_abs) return BQ_OK;
+    for (int k = 0; k < max_iter; k++) {
+        zc rho_new;
+        BQ_TRY(dotc(c, prec, w.r0, w.r, &rho_new));
+        if (!(std::abs(rho_new) == std::abs(rho_new))) {
+            bq_set_error("BiCGstab breakdown at iteration %d: <r0, r> is not finite", k);
+            return BQ_ERR_NOT_CONVERGED;
+        }
+        // r nearly orthogonal to the shadow residual: restart the recurrences
+        // with r0 = r (x and r carry over), which keeps <r0, r> = |r|^2 > 0
+        if (std::abs(rho_new) < 1e-6 * sqrt(r0n * rr.real())) {
+            BQ_TRY(axpy3(c, prec, w.r0, one, w.r, zero, nullptr, zero, nullptr));
+            BQ_TRY(axpy3(c, prec, w.p, zero, nullptr, zero, nullptr, zero, nullptr));
+            BQ_TRY(axpy3(c, prec, w.v, zero, nullptr, zero, nullptr, zero, nullptr));
+            BQ_TRY(dotc(c, prec, w.r0, w.r, &rho_new));
+            r0n = rho_new.real();
+            rho = alpha = omega = one;
+            if (!(r0n > 0)) {
+                bq_set_error("BiCGstab breakdown at iteration %d: |r|^2 = %.3e", k, r0n);
+                return BQ_ERR_NOT_CONVERGED;
+            }
+        }
+        const zc beta = (rho_new / rho) * (alpha / omega);
+        rho = rho_new;
+        BQ_TRY(axpy3(c, prec, w.p, one, w.r, beta, w.p, -beta * omega, w.v));  // p = r + beta (p - omega v)
+        BQ_TRY(bq_mhat_launch(c, prec, w.v, w.p, 0, w.tmp_o));                 // v = Mhat p
+        zc r0v;
+        BQ_TRY(dotc(c, prec, w.r0, w.v, &r0v));
+        alpha = rho / r0v;
+        BQ_TRY(axpy3(c, prec, w.s, one, w.r, -alpha, w.v, zero, nullptr));     // s = r - alpha v
+        BQ_TRY(bq_mhat_launch(c, prec, w.t, w.s, 0, w.tmp_o));                 // t = Mhat s
+        zc ts, tt;
+        BQ_TRY(dotc(c, prec, w.t, w.s, &ts));
+        BQ_TRY(dotc(c, prec, w.t, w.t, &tt));
+        omega = (tt.real() > 0) ? ts / tt : zero;
+        BQ_TRY(axpy3(c, prec, w.x, one, w.x, alpha, w.p, omega, w.s));        // x += alpha p + omega s
+        BQ_TRY(axpy3(c, prec, w.r, one, w.s, -omega, w.t, zero, nullptr));    // r = s - omega t
+        BQ_TRY(dotc(c, prec, w.r, w.r, &rr));
+        *dslash += 4;
+        *iters = k + 1;
+        if (!(rr.real() == rr.real())) {
+            bq_set_error("BiCGstab breakdown at iteration %d: NaN residual", k);
+            return BQ_ERR_NOT_CONVERGED;
+        }
+        if (rr.real() <= tol_abs * tol_abs) break;
+        if (omega == zero) {
+            bq_set_error("BiCGstab breakdown at iteration %d: omega = 0", k);
+            return BQ_ERR_NOT_CONVERGED;
+        }
+    }
+    return BQ_OK;
+}
+
+int alloc_full(bq_ctx *c, FullWork *w, int pin) {
+    const size_t b64 = spinor_bytes_per_site(BQ_PREC_DOUBLE) * (size_t)c->Vh;
+    const size_t bin = spinor_bytes_per_site(pin) * (size_t)c->Vh;
+    char **d64[] = {&w->be, &w->bo, &w->xe, &w->xo, &w->bh, &w->r, &w->to, &w->te, &w->ye};
+    for (auto p : d64) BQ_TRY(bq_alloc((void **)p, b64));
+    char **din[] = {&w->ib, &w->ix, &w->ir, &w->ir0, &w->ip, &w->iv, &w->is, &w->it, &w->itmp};
+    for (auto p : din) BQ_TRY(bq_alloc((void **)p, bin));
+    return BQ_OK;
+}
+
+void free_full(FullWork *w) {
+    char *ptrs[] = {w->be, w->bo, w->xe, w->xo, w->bh, w->r,  w->to, w->te, w->ye,
+                    w->ib, w->ix, w->ir, w->ir0, w->ip, w->iv, w->is, w->it, w->itmp};
+    for (auto p : ptrs) cudaFree(p);
+}
+
+// Mhat x_e = bhat by BiCGstab: FP64, or FP64 defect correction around a lower-precision BiCGstab
+int solve_mhat_bicgstab(bq_ctx *c, FullWork &w, const bq_solver_params *sp, double bb, bq_solver_stats *st) {
+    const int pin = sp->precision;
+    const zc one(1, 0), zero(0, 0);
+    BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.xe, zero, nullptr, zero, nullptr, zero, nullptr));
+    BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.r, one, w.bh, zero, nullptr, zero, nullptr));
+    zc rr;
+    BQ_TRY(dotc(c, BQ_PREC_DOUBLE, w.r, w.r, &rr));
+    const double target2 = sp->tol * sp->tol * bb;
+    const double delta = (sp->delta > 0 && sp->delta < 1) ? sp->delta : 1e-3;
+    const Bicg bw{w.ib, w.ix, w.ir, w.ir0, w.ip, w.iv, w.is, w.it, w.itmp};
+    int total = 0;
+    for (int outer = 0; outer < 100 && rr.real() > target2 && total < sp->max_iter; outer++) {
+        BQ_TRY(convert(c, w.ib, pin, w.r, BQ_PREC_DOUBLE));
+        // FP64 inner solve: straight to half the target; lower precision: reduce by delta
+        const double tol_in = (pin == BQ_PREC_DOUBLE) ? 0.5 * sqrt(target2)
+                                                      : fmax(delta * sqrt(rr.real()), 0.5 * sqrt(target2));
+        int its = 0;
+        BQ_TRY(bicgstab(c, pin, bw, tol_in, sp->max_iter - total, &its, &st->dslash_calls));
+        total += its;
+        if (pin == BQ_PREC_DOUBLE)
+            BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.xe, one, w.xe, one, w.ix, zero, nullptr));
+        else
+            BQ_TRY(add_to_double(c, w.xe, w.ix, pin));
+        BQ_TRY(bq_mhat_launch(c, BQ_PREC_DOUBLE, w.ye, w.xe, 0, w.to));  // r = bhat - Mhat x_e (FP64)
+        BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.r, one, w.bh, zc(-1, 0), w.ye, zero, nullptr));
+        BQ_TRY(dotc(c, BQ_PREC_DOUBLE, w.r, w.r, &rr));
+        st->reliable_updates++;
+        st->dslash_calls += 2;
+        if (its == 0) break;
+    }
+    st->iterations = total;
+    return BQ_OK;
+}
+
+// Mhat x_e = bhat by CG on the normal equations (batched core), restarted from
+// the current x_e until the even residual itself meets the target
+int solve_mhat_cg(bq_ctx *c, FullWork &w, const bq_solver_params *sp, double bb, bq_solver_stats *st) {
+    const zc one(1, 0), zero(0, 0);
+    bq_ctx *ctxs[1] = {c};
+    const int pin = sp->precision, pr = (pin == BQ_PREC_HALF) ? BQ_PREC_SINGLE : pin;
+    BQ_TRY(bq_batch_prepare(1, ctxs, pin));
+    BQ_TRY(bq_batch_reserve(c, 1, ctxs, pin, pr));
+    BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.xe, zero, nullptr, zero, nullptr, zero, nullptr));
+    BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.r, one, w.bh, zero, nullptr, zero, nullptr));
+    zc rr;
+    BQ_TRY(dotc(c, BQ_PREC_DOUBLE, w.r, w.r, &rr));
+    const double target2 = sp->tol * sp->tol * bb;
+    for (int round = 0; round < 20 && rr.real() > target2 && st->iterations < sp->max_iter; round++) {
+        // Mhat^dag Mhat d = Mhat^dag r; the normal-equation tolerance asks for a
+        // quarter of the remaining reduction of the even residual
+        BQ_TRY(bq_mhat_launch(c, BQ_PREC_DOUBLE, bq_batch_slot_b(c, 0), w.r, 1, w.to));
+        bq_solver_params cp = *sp;
+        cp.tol = fmin(0.5, fmax(1e-13, 0.25 * sqrt(target2 / rr.real())));
+        cp.max_iter = sp->max_iter - st->iterations;
+        bq_solver_stats cs;
+        memset(&cs, 0, sizeof cs);
+        int s2 = bq_cg_batch_core(c, 1, ctxs, nullptr, &cp, false, &cs);
+        if (s2 != BQ_OK && s2 != BQ_ERR_NOT_CONVERGED) return s2;
+        st->iterations += cs.iterations;
+        st->reliable_updates += cs.reliable_updates;
+        st->dslash_calls += cs.dslash_calls + 4;
+        BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.xe, one, w.xe, one, bq_batch_slot_x(c, 0), zero, nullptr));
+        BQ_TRY(bq_mhat_launch(c, BQ_PREC_DOUBLE, w.ye, w.xe, 0, w.to));
+        BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.r, one, w.bh, zc(-1, 0), w.ye, zero, nullptr));
+        BQ_TRY(dotc(c, BQ_PREC_DOUBLE, w.r, w.r, &rr));
+    }
+    return BQ_OK;
+}
+
+}  // namespace
+
+extern "C" int bq_solve_full(bq_ctx *c, double *x_e, double *x_o, const double *b_e, const double *b_o, int where,
+                             int method, const bq_solver_params *sp, bq_solver_stats *st) {
+    if (!c || !x_e || !x_o || !b_e || !b_o || !sp || !(where == BQ_HOST || where == BQ_DEVICE) ||
+        !(method == BQ_SOLVER_CG || method == BQ_SOLVER_BICGSTAB)) {
+        bq_set_error("bq_solve_full: bad arguments");
+        return BQ_ERR_ARG;
+    }
+    const int pin = sp->precision;
+    if (!(pin == BQ_PREC_DOUBLE || pin == BQ_PREC_SINGLE || pin == BQ_PREC_HALF) || !(sp->tol > 0) ||
+        sp->max_iter < 1 || sp->shift != 0.0 || sp->delta < 0 || sp->delta >= 1) {
+        bq_set_error("bq_solve_full: bad solver parameters (shift must be 0)");
+        return BQ_ERR_ARG;
+    }
+    if (!c->have_gauge) {
+        bq_set_error("gauge field not set");
+        return BQ_ERR_STATE;
+    }
+    bq_solver_stats local;
+    if (!st) st = &local;
+    memset(st, 0, sizeof *st);
+    FullWork w;
+    memset(&w, 0, sizeof w);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int status = alloc_full(c, &w, pin);
+    if (status == BQ_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+        bq_set_error("bq_solve_full: event creation failed");
+        status = BQ_ERR_CUDA;
+    }
+    const double kappa = c->params.kappa;
+    const zc one(1, 0), zero(0, 0);
+    auto run = [&]() -> int {
+        BQ_CUDA_TRY(cudaEventRecord(e0, c->stream));
+        BQ_TRY(bq_spinor_pack(c, w.be, b_e, BQ_PREC_DOUBLE, where));
+        BQ_TRY(bq_spinor_pack(c, w.bo, b_o, BQ_PREC_DOUBLE, where));
+        zc bbe, bbo;
+        BQ_TRY(dotc(c, BQ_PREC_DOUBLE, w.be, w.be, &bbe));
+        BQ_TRY(dotc(c, BQ_PREC_DOUBLE, w.bo, w.bo, &bbo));
+        const double bb = bbe.real() + bbo.real();
+        if (bb == 0.0) {
+            BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.xe, zero, nullptr, zero, nullptr, zero, nullptr));
+            BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.xo, zero, nullptr, zero, nullptr, zero, nullptr));
+            st->converged = 1;
+        } else {
+            // bhat_e = b_e + kappa D_eo A_oo^{-1} b_o
+            BQ_TRY(bq_clover_launch(c, BQ_PREC_DOUBLE, w.to, w.bo, 1, 1));
+            BQ_TRY(bq_dslash_launch(c, BQ_PREC_DOUBLE, w.te, w.to, 0, 0, EPI_PLAIN, nullptr, 0.0));
+            BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.bh, one, w.be, zc(kappa, 0), w.te, zero, nullptr));
+            st->dslash_calls += 1;
+            // the odd residual vanishes after the reconstruction, so |bhat - Mhat x_e| <= tol |b| is the goal
+            if (method == BQ_SOLVER_BICGSTAB) BQ_TRY(solve_mhat_bicgstab(c, w, sp, bb, st));
+            else BQ_TRY(solve_mhat_cg(c, w, sp, bb, st));
+            // x_o = A_oo^{-1} (b_o + kappa D_oe x_e)
+            BQ_TRY(bq_dslash_launch(c, BQ_PREC_DOUBLE, w.to, w.xe, 1, 0, EPI_PLAIN, nullptr, 0.0));
+            BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.to, one, w.bo, zc(kappa, 0), w.to, zero, nullptr));
+            BQ_TRY(bq_clover_launch(c, BQ_PREC_DOUBLE, w.xo, w.to, 1, 1));
+            // true residual of the full system: (M x)_p = A_pp x_p - kappa D x_{1-p}
+            BQ_TRY(bq_dslash_launch(c, BQ_PREC_DOUBLE, w.te, w.xo, 0, 0, EPI_XPAY, w.xe, kappa));
+            BQ_TRY(bq_dslash_launch(c, BQ_PREC_DOUBLE, w.to, w.xe, 1, 0, EPI_XPAY, w.xo, kappa));
+            BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.te, one, w.be, zc(-1, 0), w.te, zero, nullptr));
+            BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.to, one, w.bo, zc(-1, 0), w.to, zero, nullptr));
+            st->dslash_calls += 4;
+            zc re, ro;
+            BQ_TRY(dotc(c, BQ_PREC_DOUBLE, w.te, w.te, &re));
+            BQ_TRY(dotc(c, BQ_PREC_DOUBLE, w.to, w.to, &ro));
+            st->true_residual = sqrt((re.real() + ro.real()) / bb);
+            st->converged = st->true_residual <= sp->tol;
+        }
+        BQ_TRY(bq_spinor_unpack(c, x_e, w.xe, BQ_PREC_DOUBLE, where));
+        BQ_TRY(bq_spinor_unpack(c, x_o, w.xo, BQ_PREC_DOUBLE, where));
+        BQ_CUDA_TRY(cudaEventRecord(e1, c->stream));
+        BQ_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        st->seconds = ms * 1e-3;
+        return BQ_OK;
+    };
+    if (status == BQ_OK) status = run();
+    cudaStreamSynchronize(c->stream);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    free_full(&w);
+    if (status == BQ_OK && !st->converged) {
+        bq_set_error("full-system solve: true residual %.3e above tol", st->true_residual);
+        return BQ_ERR_NOT_CONVERGED;
+    }
+    return status;
+}

@@ -716,6 +716,7 @@ double dslash_site_bytes(int prec, int recon, int epi);
 double dslash_site_flops(int epi);
 
 // batched solver (bq_batch.cu)
+int bq_batch_prepare(int nsys, bq_ctx *const *ctxs, int ps);  // fields of every system at FP64 and ps
 int bq_batch_reserve(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int pr);
 void *bq_batch_slot_b(bq_ctx *c0, int s);
 void *bq_batch_slot_x(bq_ctx *c0, int s);

@@ -474,3 +474,60 @@ def test_apply_error_report(bq, cfg, capsys):
     lat.close()
     with capsys.disabled():
         print("\n" + "\n".join(lines))
+
+
+FULL_CASES = [
+    # (method, precision, mu, charge, delta)
+    ("bicgstab", "double", 0.1, 0.0, 1e-3),
+    ("bicgstab", "single", 0.1, 2.0 / 3.0, 1e-3),
+    ("bicgstab", "half", 0.0, 0.0, 1e-1),
+    ("cg", "single", 0.1, 0.0, 1e-3),
+    ("cg", "double", 0.0, -1.0 / 3.0, 1e-3),
+]
+
+
+@pytest.mark.parametrize("method,prec,mu,charge,delta", FULL_CASES)
+def test_full_system_solve(bq, method, prec, mu, charge, delta):
+    """M x = b on the whole lattice through the even-odd reduction: the FP64
+    residual |b - M x| / |b| from the oracle's M meets tol and x matches the
+    oracle's block-eliminated solution."""
+    dims = (6, 4, 6, 10)
+    recon = 12 if prec != "double" and not charge else 18
+    lat, U, A, p = make(bq, dims, kappa=0.13, csw=1.7, mu=mu, charge=charge, recon=recon, precision=prec)
+    op = oracle.Operator(p, U, A)
+    b_e, b_o = synth.gaussian_spinor(lat.Vh, 501), synth.gaussian_spinor(lat.Vh, 502)
+    x_e, x_o = np.empty_like(b_e), np.empty_like(b_o)
+    st = bq.bq_solve_full(lat.ctx, x_e, x_o, b_e, b_o, method=method, tol=1e-10, precision=prec, delta=delta)
+    y_e, y_o = op.full(x_e, x_o)
+    bn = np.sqrt(np.linalg.norm(b_e) ** 2 + np.linalg.norm(b_o) ** 2)
+    res = np.sqrt(np.linalg.norm(y_e - b_e) ** 2 + np.linalg.norm(y_o - b_o) ** 2) / bn
+    assert st["converged"] == 1 and res <= 1e-10, (st, res)
+    assert abs(st["true_residual"] - res) < 1e-11
+    xo_e, xo_o = op.solve_full(b_e, b_o, tol=1e-12)
+    assert rel(np.concatenate([x_e.ravel(), x_o.ravel()]), np.concatenate([xo_e.ravel(), xo_o.ravel()])) < 1e-8
+    lat.close()
+
+
+def test_full_system_device_buffers_and_zero_source(bq):
+    import torch
+
+    dims = (4, 4, 4, 6)
+    lat, U, A, p = make(bq, dims, kappa=0.12, csw=1.0, mu=0.05)
+    op = oracle.Operator(p, U)
+    b_e, b_o = synth.gaussian_spinor(lat.Vh, 511), np.zeros((lat.Vh, 4, 3), np.complex128)
+    dev = [torch.from_numpy(v).cuda() for v in (b_e, b_o)]
+    xs = [torch.full_like(dev[0], 7.0), torch.full_like(dev[1], 7.0)]
+    st = bq.bq_solve_full(lat.ctx, xs[0], xs[1], dev[0], dev[1], method="bicgstab", tol=1e-11)
+    x_e, x_o = xs[0].cpu().numpy(), xs[1].cpu().numpy()
+    y_e, y_o = op.full(x_e, x_o)
+    res = np.sqrt(np.linalg.norm(y_e - b_e) ** 2 + np.linalg.norm(y_o) ** 2) / np.linalg.norm(b_e)
+    assert st["converged"] and res <= 1e-11
+    # b = 0 gives x = 0 without iterating
+    z = np.zeros_like(b_e)
+    x_e, x_o = np.ones_like(b_e), np.ones_like(b_e)
+    st = bq.bq_solve_full(lat.ctx, x_e, x_o, z, z, method="cg")
+    assert st["converged"] and st["iterations"] == 0 and not x_e.any() and not x_o.any()
+    with pytest.raises(bq.BqError) as e:
+        bq.bq_solve_full(lat.ctx, x_e, x_o, b_e, b_o, method="bicgstab", tol=1e-10, max_iter=2)
+    assert e.value.status == bq.BQ_ERR_NOT_CONVERGED
+    lat.close()

@@ -56,6 +56,28 @@ def test_free_field_plane_wave(dims, t_bc, mu_chem):
             assert rel(got, expect[synth.half_sites(dims, out_par)]) < 1e-13
 
 
+@pytest.mark.parametrize("mu_chem,kappa", [(0.0, 0.125), (0.15, 0.11)])
+def test_free_field_full_operator(mu_chem, kappa):
+    """Without clover term (c_SW = 0, A = 1) the full matrix on exp(i p.x) u is
+    (1 - kappa (a - i gamma.b)) u exp(i p.x), on the even and odd halves."""
+    dims = (4, 2, 6, 8)
+    rng = np.random.default_rng(17)
+    U = synth.unit_gauge(dims)
+    p_ = oracle.params(dims, kappa=kappa, csw=0.0, mu=mu_chem, t_bc=-1.0)
+    op = oracle.Operator(p_, U)
+    gam = chiral_gammas()
+    ev, od = synth.half_sites(dims, 0), synth.half_sites(dims, 1)
+    for trial in range(3):
+        n = rng.integers(0, 8, 4)
+        u = rng.standard_normal((4, 3)) + 1j * rng.standard_normal((4, 3))
+        psi, p = plane_wave(dims, n, u, -1.0)
+        Dp, _, _ = free_dirac_symbol(p, mu_chem, gam)
+        expect = np.einsum("st,xta->xsa", np.eye(4) - kappa * Dp, psi)
+        y_e, y_o = op.full(psi[ev], psi[od])
+        assert rel(y_e, expect[ev]) < 1e-13
+        assert rel(y_o, expect[od]) < 1e-13
+
+
 @pytest.mark.parametrize("mu_chem,kappa", [(0.0, 0.125), (0.1, 0.2)])
 def test_free_field_mhat_spectrum(mu_chem, kappa):
     """Dense spectrum of Mhat on 4^4 (U=1, antiperiodic t) equals the closed form
@@ -272,6 +294,32 @@ def test_cg_matches_dense_solve():
     cond = np.linalg.cond(K)
     assert rel(x.ravel(), xd) < cond * 1e-10
     assert rel(op.mdagm(x), b) <= 1e-10 * 1.01
+
+
+@pytest.mark.parametrize("mu_chem,charge", [(0.0, 0.0), (0.1, 2.0 / 3.0)])
+def test_full_solve_matches_dense(mu_chem, charge):
+    """The block-eliminated full solve equals a dense solve of M on 4^4, and the
+    Schur complement of M's odd block is Mhat."""
+    dims = (4, 4, 4, 4)
+    p_, U, A = _random_setup(dims, mu_chem=mu_chem, charge=charge, csw=1.2, kappa=0.125)
+    op = oracle.Operator(p_, U, A)
+    Vh = oracle.half_volume(p_)
+    n = Vh * 12
+    Mfull = np.empty((2 * n, 2 * n), complex)
+    for j in range(2 * n):
+        e = np.zeros(2 * n, complex)
+        e[j] = 1
+        y_e, y_o = op.full(e[:n].reshape(Vh, 4, 3), e[n:].reshape(Vh, 4, 3))
+        Mfull[:, j] = np.concatenate([y_e.ravel(), y_o.ravel()])
+    S = Mfull[:n, :n] - Mfull[:n, n:] @ np.linalg.solve(Mfull[n:, n:], Mfull[n:, :n])
+    assert np.abs(S - dense(op.mhat, Vh)).max() < 1e-12
+    b_e, b_o = synth.gaussian_spinor(Vh, 81), synth.gaussian_spinor(Vh, 82)
+    x_e, x_o = op.solve_full(b_e, b_o, tol=1e-12)
+    xd = np.linalg.solve(Mfull, np.concatenate([b_e.ravel(), b_o.ravel()]))
+    got = np.concatenate([x_e.ravel(), x_o.ravel()])
+    assert rel(got, xd) < np.linalg.cond(Mfull) * 1e-11
+    y_e, y_o = op.full(x_e, x_o)
+    assert rel(np.concatenate([y_e.ravel(), y_o.ravel()]), np.concatenate([b_e.ravel(), b_o.ravel()])) < 1e-10
 
 
 def test_multishift_matches_spectral_sum():
