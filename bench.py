@@ -420,6 +420,32 @@ def batched_extras(torch, bqcd):
     return out
 
 
+def full_system_extras(torch, bqcd):
+    """M x = b on the whole 24^3x48 lattice with chemical potential mu = 0.1
+    (Mhat not gamma_5-hermitian): BiCGstab on Mhat against CG on Mhat^dag Mhat,
+    both mixed (FP32 inner, FP64 outer) and BiCGstab in plain FP64, to a true
+    full-lattice FP64 residual 1e-10."""
+    from paper_1711_03836_gb300 import synth
+
+    wl = WORKLOADS["24^3x48"]
+    lat = bqcd.Lattice(wl["dims"], wl["kappa"], wl["csw"], 0.1, -1.0)
+    bqcd.bq_set_gauge(lat.ctx, synth.gauge_field(wl["dims"], wl["eps"], wl["seed"]))
+    bqcd.bq_set_recon(lat.ctx, "single", 12)
+    b_e = torch.from_numpy(synth.gaussian_spinor(lat.Vh, 601)).cuda()
+    b_o = torch.from_numpy(synth.gaussian_spinor(lat.Vh, 602)).cuda()
+    x_e, x_o = torch.empty_like(b_e), torch.empty_like(b_o)
+    out = {}
+    for name, method, prec in (("bicgstab_mixed", "bicgstab", "single"), ("cg_normal_mixed", "cg", "single"),
+                               ("bicgstab_fp64", "bicgstab", "double")):
+        kw = dict(method=method, tol=1e-10, precision=prec, delta=1e-3 if method == "cg" else 1e-2)
+        bqcd.bq_solve_full(lat.ctx, x_e, x_o, b_e, b_o, **kw)
+        st, ms = _timed(torch, lambda: bqcd.bq_solve_full(lat.ctx, x_e, x_o, b_e, b_o, **kw))
+        out[name] = {"ms": ms, "iterations": st["iterations"], "dslash_calls": st["dslash_calls"],
+                     "true_residual": st["true_residual"]}
+    lat.close()
+    return {"full_system_24^3x48_mu0.1": out}
+
+
 def aggregate_ranks(ms, nbytes, device):
     """Replicas: the job's time is the slowest rank's, its work the sum over ranks."""
     import torch
@@ -550,6 +576,7 @@ def extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, mixed_ms, torch, bqcd):
 
     # ---- batching (row a9) and multishift (row a8), each against the same work done one system at a time
     out["batched"] = batched_extras(torch, bqcd)
+    out.update(full_system_extras(torch, bqcd))
 
     # ---- CPU oracle on the host cores (bounded sample: 2 Mhat^dag Mhat applies)
     import oracle

@@ -150,6 +150,31 @@ int bq_set_u1(bq_ctx *ctx, const double *A, int where);
  * BQ_ERR_CLOVER_SINGULAR if a block has no inverse. */
 int bq_build_clover(bq_ctx *ctx);
 
+/* Stout smearing of the hopping term's links (Section 2, QCD+QED: the
+ * fermion action of Eq. 5 hops with singly iterated stout links; Morningstar
+ * and Peardon, Phys. Rev. D 69 (2004) 054501). With n_iter > 0 and rho > 0
+ * the hopping term uses U^(n), U^(k+1)_mu(x) = exp(X) U^(k)_mu(x), where X is
+ * the traceless anti-Hermitian part of Omega = C U^(k)_mu(x)^dag and
+ * C = rho sum_{nu != mu} of the upper and lower staples (isotropic rho, links
+ * periodic in every direction). The clover term keeps the unsmeared links.
+ * A setting of the context: it follows later bq_set_gauge calls; computed on
+ * the device on first use. n_iter = 0 or rho = 0 switches smearing off.
+ * 0 <= rho <= 1, 0 <= n_iter <= 64, else BQ_ERR_ARG. */
+int bq_set_stout(bq_ctx *ctx, double rho, int n_iter);
+
+/* Copy the links the hopping term uses (smeared when bq_set_stout is on,
+ * otherwise the gauge field as set) in the canonical layout [V][4][3][3]
+ * complex into U (host or device). BQ_ERR_STATE without a gauge field. */
+int bq_get_hop_links(bq_ctx *ctx, double *U, int where);
+
+/* log det of the clover term (Eq. 2) summed over the sites of one parity:
+ * *logdet = sum_x log|det A(x)| in FP64 (LU with partial pivoting of each
+ * 6x6 chirality block), *negative (may be NULL) = number of blocks whose
+ * determinant is negative. For the even-odd preconditioned action the
+ * fermion determinant carries det A_oo, i.e. parity 1.
+ * BQ_ERR_CLOVER_SINGULAR if a block is singular. */
+int bq_clover_logdet(bq_ctx *ctx, int parity, double *logdet, int *negative);
+
 /* Reset the counters; timing != 0 also brackets every hopping-term launch with
  * CUDA events on the library stream (adds a few microseconds per launch). */
 int bq_reset_counters(bq_ctx *ctx, int timing);

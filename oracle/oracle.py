@@ -4,7 +4,11 @@ TEST INFRASTRUCTURE.  Each function names the part of arXiv:1711.03836 it
 follows; the arithmetic lives in the C file and is written from the
 definitions (Eq. 1 hopping term with chemical potential, Eq. 2 clover term,
 Eq. 5 U(1) phases, the even-odd Schur complement of M = A - kappa D_hop,
-textbook CG).  Fields use the canonical host layouts:
+textbook CG).  Stout smearing of the hopping links (Eq. 5's singly iterated
+stout links, after Morningstar and Peardon 2004) and the clover log det are
+written here in numpy: staples by array shifts, exp(iQ) by the eigen-
+decomposition of the Hermitian Q, log det by numpy's slogdet of each site's
+12x12 clover matrix.  Fields use the canonical host layouts:
 
   links   U[V][4][3][3] complex128, site lex = x + Lx*(y + Ly*(z + Lz*t))
   U(1)    A[V][4] float64 (or None)
@@ -179,15 +183,65 @@ def clover_sites(p, U, parity, psi, sites, inverse=False):
     return out
 
 
-class Operator:
-    """The even-odd operator of one gauge field: clover blocks built once."""
+def stout(dims, U, rho, n_iter=1):
+    """n_iter stout steps of every link (Morningstar and Peardon 2004):
+    C_mu(x) = rho sum_{nu != mu} [U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
+                                  + U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)],
+    Omega = C_mu(x) U_mu(x)^dag, Q = (i/2)(Omega^dag - Omega) - (i/6) tr(Omega^dag - Omega),
+    U'_mu(x) = exp(iQ) U_mu(x); links periodic in every direction."""
+    Lx, Ly, Lz, Lt = dims
+    W = _c128(U).reshape(Lt, Lz, Ly, Lx, 4, 3, 3)
+    ax = {0: 3, 1: 2, 2: 1, 3: 0}
 
-    def __init__(self, p: Params, U, A=None):
+    def at(F, mu, d):
+        """F(x + d mu-hat)."""
+        return np.roll(F, -d, axis=ax[mu])
+
+    def dag(F):
+        return np.conj(np.swapaxes(F, -1, -2))
+
+    for _ in range(n_iter):
+        out = np.empty_like(W)
+        for mu in range(4):
+            Umu = W[..., mu, :, :]
+            C = np.zeros_like(Umu)
+            for nu in range(4):
+                if nu == mu:
+                    continue
+                Unu = W[..., nu, :, :]
+                C += Unu @ at(Umu, nu, 1) @ dag(at(Unu, mu, 1))
+                Unu_m = at(Unu, nu, -1)
+                C += dag(Unu_m) @ at(Umu, nu, -1) @ at(Unu_m, mu, 1)
+            Om = rho * C @ dag(Umu)
+            D = dag(Om) - Om
+            Q = 0.5j * D - (1j / 6.0) * np.trace(D, axis1=-2, axis2=-1)[..., None, None] * np.eye(3)
+            Q = 0.5 * (Q + dag(Q))  # Hermitian up to rounding; eigh reads one triangle
+            q, Wv = np.linalg.eigh(Q)
+            expQ = (Wv * np.exp(1j * q)[..., None, :]) @ dag(Wv)
+            out[..., mu, :, :] = expQ @ Umu
+        W = out
+    return W.reshape(np.shape(U))
+
+
+def clover_logdet(p, U, parity):
+    """(sum over the sites of `parity` of log|det A(x)|, number of sites with
+    det A(x) < 0), A(x) the 12x12 clover matrix of Eq. 2."""
+    sign, ld = np.linalg.slogdet(clover_field(p, U, parity))
+    return float(np.sum(ld)), int(np.sum(sign.real < 0))
+
+
+class Operator:
+    """The even-odd operator of one gauge field: clover blocks built once.
+    U_hop (optional) replaces U in the hopping term (stout-smeared links); the
+    clover term is always built from U."""
+
+    def __init__(self, p: Params, U, A=None, U_hop=None):
         self.p = p
-        self.U = _c128(U)
+        self.U_thin = _c128(U)
+        self.U = self.U_thin if U_hop is None else _c128(U_hop)
         self.A = None if A is None else np.ascontiguousarray(A, np.float64)
-        self.Aee = clover_field(p, self.U, 0)
-        self.Aoo = clover_field(p, self.U, 1)
+        self.Aee = clover_field(p, self.U_thin, 0)
+        self.Aoo = clover_field(p, self.U_thin, 1)
         self.Aoo_inv = clover_invert(self.Aoo)
 
     def mhat(self, psi, dagger=False):

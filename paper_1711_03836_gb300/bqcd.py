@@ -110,6 +110,10 @@ _SIGS = {
                                               ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(bq_solver_params), ctypes.POINTER(bq_solver_stats),
                                               ctypes.POINTER(ctypes.c_double)]),
+    "bq_set_stout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]),
+    "bq_get_hop_links": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "bq_clover_logdet": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int)]),
     "bq_solve_full": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(bq_solver_params),
                                      ctypes.POINTER(bq_solver_stats)]),
@@ -339,6 +343,25 @@ def bq_solve_multishift_cg(ctx, xs, b, shifts, tol=1e-10, max_iter=20000, precis
     d = st.as_dict()
     d["residuals"] = list(res)
     return d
+
+
+def bq_set_stout(ctx, rho, n_iter=1):
+    _check(_lib_handle().bq_set_stout(ctx, float(rho), int(n_iter)), "bq_set_stout")
+
+
+def bq_get_hop_links(ctx, U):
+    """Links of the hopping term into U ([V][4][3][3] complex128, host or device)."""
+    p, w = _ptr_where(U)
+    _check(_lib_handle().bq_get_hop_links(ctx, p, w), "bq_get_hop_links")
+    return U
+
+
+def bq_clover_logdet(ctx, parity):
+    """(sum over the parity's sites of log|det A(x)|, number of blocks with det < 0)."""
+    ld = ctypes.c_double()
+    neg = ctypes.c_int()
+    _check(_lib_handle().bq_clover_logdet(ctx, int(parity), ctypes.byref(ld), ctypes.byref(neg)), "bq_clover_logdet")
+    return ld.value, neg.value
 
 
 def bq_solve_full(ctx, x_e, x_o, b_e, b_o, method="bicgstab", tol=1e-10, max_iter=20000, precision="double",

@@ -11,7 +11,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#include "bq_internal.cuh"
+#include "bq_geo.cuh"
 
 // --------------------------------------------------------------------------
 // errors
@@ -55,6 +55,7 @@ int bq_alloc(void **p, size_t bytes) {
 static int valid_prec(int p) { return p == BQ_PREC_DOUBLE || p == BQ_PREC_SINGLE || p == BQ_PREC_HALF; }
 
 static void invalidate_derived(bq_ctx *c, int links, int clover) {
+    if (links && clover) c->U_hop_valid = 0;  // a new gauge field
     for (int p = 0; p < BQ_NFIELD; p++) {
         if (links) c->links_valid[p] = 0;
         if (clover) c->clov_valid[p] = 0;
@@ -119,6 +120,7 @@ extern "C" int bq_destroy(bq_ctx *c) {
     bq_solver_free(c);
     bq_batch_free(c);
     cudaFree(c->U_canon);
+    cudaFree(c->U_hop);
     cudaFree(c->A_u1);
     for (int p = 0; p < BQ_NFIELD; p++) {
         cudaFree(c->links[p]);
@@ -223,36 +225,7 @@ extern "C" int bq_set_u1(bq_ctx *c, const double *A, int where) {
 // --------------------------------------------------------------------------
 // geometry helper for setup kernels (full-lattice lex index)
 
-struct Geo {
-    int L0, L1, L2, L3;
-    long long V;
-    int Vh;
-};
 
-__device__ __forceinline__ void lex_coords(const Geo &g, long long lex, int c[4]) {
-    c[0] = (int)(lex % g.L0);
-    lex /= g.L0;
-    c[1] = (int)(lex % g.L1);
-    lex /= g.L1;
-    c[2] = (int)(lex % g.L2);
-    c[3] = (int)(lex / g.L2);
-}
-__device__ __forceinline__ long long lex_of(const Geo &g, const int c[4]) {
-    return c[0] + (long long)g.L0 * (c[1] + (long long)g.L1 * (c[2] + (long long)g.L2 * c[3]));
-}
-__device__ __forceinline__ long long lex_step(const Geo &g, long long lex, int mu, int dir) {
-    int c[4];
-    lex_coords(g, lex, c);
-    const int Ls[4] = {g.L0, g.L1, g.L2, g.L3};
-    c[mu] += dir;
-    if (c[mu] < 0) c[mu] += Ls[mu];
-    if (c[mu] >= Ls[mu]) c[mu] -= Ls[mu];
-    return lex_of(g, c);
-}
-
-static Geo geo_of(const bq_ctx *c) { return Geo{c->L[0], c->L[1], c->L[2], c->L[3], c->V, c->Vh}; }
-
-static unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 // --------------------------------------------------------------------------
 // links
@@ -296,7 +269,13 @@ int bq_prepare_links(bq_ctx *c, int prec) {
     Geo g = geo_of(c);
     unsigned grid = grid_for(c->V, 128);
     double q = c->params.charge;
-#define PACK(P, R) k_pack_links<P, R><<<grid, 128, 0, c->stream>>>(c->links[prec], blk, c->U_canon, c->A_u1, q, g)
+    // the hopping term takes the stout-smeared links when smearing is set, the clover term the thin ones
+    const double2 *Usrc = c->U_canon;
+    if (c->stout_iter > 0) {
+        BQ_TRY(bq_prepare_hop_links(c));
+        Usrc = c->U_hop;
+    }
+#define PACK(P, R) k_pack_links<P, R><<<grid, 128, 0, c->stream>>>(c->links[prec], blk, Usrc, c->A_u1, q, g)
     if (prec == BQ_PREC_DOUBLE) {
         if (recon == 12) PACK(BQ_PREC_DOUBLE, 12); else PACK(BQ_PREC_DOUBLE, 18);
     } else if (prec == BQ_PREC_SINGLE) {
@@ -315,33 +294,6 @@ int bq_prepare_links(bq_ctx *c, int prec) {
 
 // --------------------------------------------------------------------------
 // clover term
-
-struct M3 {
-    cplx<double> a[9];
-};
-
-__device__ __forceinline__ M3 load_link(const double2 *U, long long lex, int mu) {
-    M3 m;
-    const double2 *p = U + (lex * 4 + mu) * 9;
-    for (int k = 0; k < 9; k++) m.a[k] = {p[k].x, p[k].y};
-    return m;
-}
-__device__ __forceinline__ M3 mdag(const M3 &x) {
-    M3 m;
-    for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 3; j++) m.a[i * 3 + j] = cconj(x.a[j * 3 + i]);
-    return m;
-}
-__device__ __forceinline__ M3 mmul(const M3 &x, const M3 &y) {
-    M3 m;
-    for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 3; j++) {
-            cplx<double> s = {0, 0};
-            for (int k = 0; k < 3; k++) s = cfma(x.a[i * 3 + k], y.a[k * 3 + j], s);
-            m.a[i * 3 + j] = s;
-        }
-    return m;
-}
 
 // traceless anti-Hermitian part of the clover-leaf sum in the mu-nu plane: (Q - Q^dag)/8 - trace/3
 __device__ void field_strength(const double2 *U, const Geo &g, long long x, int mu, int nu, M3 &F) {
@@ -373,34 +325,6 @@ __device__ void field_strength(const double2 *U, const Geo &g, long long x, int 
     F.a[0] = csub(F.a[0], tr);
     F.a[4] = csub(F.a[4], tr);
     F.a[8] = csub(F.a[8], tr);
-}
-
-// write a Hermitian 6x6 (given as full matrix) into packed FP64 storage of one block
-__device__ __forceinline__ void store_herm6(double2 *blk, int b, int h, int Vh, const cplx<double> B[36]) {
-    double2 *p = blk + (size_t)(18 * b) * Vh + h;
-    for (int k = 0; k < 3; k++) p[(size_t)k * Vh] = make_double2(B[(2 * k) * 7].re, B[(2 * k + 1) * 7].re);
-    int k = 0;
-    for (int i = 0; i < 6; i++)
-        for (int j = i + 1; j < 6; j++) {
-            p[(size_t)(3 + k) * Vh] = make_double2(B[i * 6 + j].re, B[i * 6 + j].im);
-            k++;
-        }
-}
-__device__ __forceinline__ void load_herm6(const double2 *blk, int b, int h, int Vh, cplx<double> B[36]) {
-    const double2 *p = blk + (size_t)(18 * b) * Vh + h;
-    for (int k = 0; k < 3; k++) {
-        double2 v = p[(size_t)k * Vh];
-        B[(2 * k) * 7] = {v.x, 0.0};
-        B[(2 * k + 1) * 7] = {v.y, 0.0};
-    }
-    int k = 0;
-    for (int i = 0; i < 6; i++)
-        for (int j = i + 1; j < 6; j++) {
-            double2 v = p[(size_t)(3 + k) * Vh];
-            B[i * 6 + j] = {v.x, v.y};
-            B[j * 6 + i] = {v.x, -v.y};
-            k++;
-        }
 }
 
 // A(x) per site. In the chiral basis sigma_{mu nu} is block diagonal; with

@@ -1,0 +1,229 @@
+// bq_gauge.cu -- gauge-side setup steps that precede a solve in the HMC:
+//   * stout smearing of the hopping-term links (Section 2, QCD+QED: the
+//     fermion action of Eq. 5 hops with singly iterated stout links Ũ), after
+//     Morningstar and Peardon, Phys. Rev. D 69 (2004) 054501;
+//   * log det A of the clover term (Eq. 2) on one parity, the even-odd
+//     preconditioned action's log det A_oo term.
+#include <math.h>
+
+#include "bq_geo.cuh"
+#include "bq_reduce.cuh"
+
+// exp(X) of a traceless anti-Hermitian 3x3 matrix: scaling and squaring of a
+// degree-14 Taylor polynomial (Moler and Van Loan, "Nineteen dubious ways to
+// compute the exponential of a matrix", method 3). X is halved until its
+// Frobenius norm is <= 1/2, where the truncation error is below 3e-17.
+__device__ M3 expm_su3(const M3 &X) {
+    double n2 = 0.0;
+    for (int k = 0; k < 9; k++) n2 += X.a[k].re * X.a[k].re + X.a[k].im * X.a[k].im;
+    int s = 0;
+    double scale = 1.0;
+    while (n2 * scale * scale > 0.25 && s < 40) {
+        scale *= 0.5;
+        s++;
+    }
+    M3 Y;
+    for (int k = 0; k < 9; k++) Y.a[k] = cscale(scale, X.a[k]);
+    // Horner: E = I + Y/1 (I + Y/2 (I + ... (I + Y/14)))
+    M3 E;
+    for (int k = 0; k < 9; k++) E.a[k] = {(k % 4 == 0) ? 1.0 : 0.0, 0.0};
+    for (int j = 14; j >= 1; j--) {
+        M3 T = mmul(Y, E);
+        for (int k = 0; k < 9; k++) {
+            E.a[k] = cscale(1.0 / j, T.a[k]);
+            if (k % 4 == 0) E.a[k].re += 1.0;
+        }
+    }
+    for (int q = 0; q < s; q++) E = mmul(E, E);
+    return E;
+}
+
+// one stout step for every link: C = rho sum_{nu != mu} (upper + lower staple),
+// Omega = C U^dag, X = traceless anti-Hermitian part of Omega
+// (= i Q with Q = (i/2)(Omega^dag - Omega) - (i/6) tr(Omega^dag - Omega)),
+// U' = exp(X) U. Links are periodic in every direction.
+__global__ void __launch_bounds__(128) k_stout_step(double2 *out, const double2 *in, Geo g, double rho) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.V * 4) return;
+    const long long x = idx >> 2;
+    const int mu = (int)(idx & 3);
+    const long long xpm = lex_step(g, x, mu, +1);
+    M3 C;
+    for (int k = 0; k < 9; k++) C.a[k] = {0.0, 0.0};
+    for (int nu = 0; nu < 4; nu++) {
+        if (nu == mu) continue;
+        const long long xpn = lex_step(g, x, nu, +1), xmn = lex_step(g, x, nu, -1);
+        const long long xmn_pm = lex_step(g, xmn, mu, +1);
+        // upper staple U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
+        M3 up = mmul(mmul(load_link(in, x, nu), load_link(in, xpn, mu)), mdag(load_link(in, xpm, nu)));
+        // lower staple U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)
+        M3 lo = mmul(mmul(mdag(load_link(in, xmn, nu)), load_link(in, xmn, mu)), load_link(in, xmn_pm, nu));
+        for (int k = 0; k < 9; k++) C.a[k] = cadd(C.a[k], cadd(up.a[k], lo.a[k]));
+    }
+    const M3 U = load_link(in, x, mu);
+    M3 Om = mmul(C, mdag(U));
+    M3 X;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            X.a[i * 3 + j] = cscale(0.5 * rho, csub(Om.a[i * 3 + j], cconj(Om.a[j * 3 + i])));
+    const cplx<double> tr = cscale(1.0 / 3.0, cadd(cadd(X.a[0], X.a[4]), X.a[8]));
+    X.a[0] = csub(X.a[0], tr);
+    X.a[4] = csub(X.a[4], tr);
+    X.a[8] = csub(X.a[8], tr);
+    const M3 Un = mmul(expm_su3(X), U);
+    double2 *p = out + (x * 4 + mu) * 9;
+    for (int k = 0; k < 9; k++) p[k] = make_double2(Un.a[k].re, Un.a[k].im);
+}
+
+int bq_prepare_hop_links(bq_ctx *c) {
+    if (c->U_hop_valid) return BQ_OK;
+    const size_t bytes = (size_t)c->V * 4 * 9 * sizeof(double2);
+    BQ_TRY(bq_alloc((void **)&c->U_hop, bytes));
+    double2 *tmp = nullptr;
+    if (c->stout_iter > 1) BQ_TRY(bq_alloc((void **)&tmp, bytes));
+    const Geo g = geo_of(c);
+    const unsigned grid = grid_for(c->V * 4, 128);
+    // ping-pong so that the last step writes U_hop
+    const double2 *src = c->U_canon;
+    int status = BQ_OK;
+    for (int it = 0; it < c->stout_iter; it++) {
+        double2 *dst = ((c->stout_iter - 1 - it) % 2 == 0) ? c->U_hop : tmp;
+        k_stout_step<<<grid, 128, 0, c->stream>>>(dst, src, g, c->stout_rho);
+        if (cudaGetLastError() != cudaSuccess) {
+            bq_set_error("stout smearing launch failed");
+            status = BQ_ERR_CUDA;
+            break;
+        }
+        BQ_COUNT(c);
+        src = dst;
+    }
+    if (tmp) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+    }
+    if (status == BQ_OK) c->U_hop_valid = 1;
+    return status;
+}
+
+extern "C" int bq_set_stout(bq_ctx *c, double rho, int n_iter) {
+    if (!c || !(rho >= 0.0 && rho <= 1.0) || n_iter < 0 || n_iter > 64) {
+        bq_set_error("bq_set_stout: need 0 <= rho <= 1 and 0 <= n_iter <= 64");
+        return BQ_ERR_ARG;
+    }
+    if (rho == 0.0) n_iter = 0;
+    if (c->stout_iter != n_iter || c->stout_rho != rho) {
+        c->stout_iter = n_iter;
+        c->stout_rho = rho;
+        c->U_hop_valid = 0;
+        for (int p = 0; p < BQ_NFIELD; p++) c->links_valid[p] = 0;
+    }
+    return BQ_OK;
+}
+
+extern "C" int bq_get_hop_links(bq_ctx *c, double *U, int where) {
+    if (!c || !U || !(where == BQ_HOST || where == BQ_DEVICE)) {
+        bq_set_error("bq_get_hop_links: bad arguments");
+        return BQ_ERR_ARG;
+    }
+    if (!c->have_gauge) {
+        bq_set_error("gauge field not set");
+        return BQ_ERR_STATE;
+    }
+    const double2 *src = c->U_canon;
+    if (c->stout_iter > 0) {
+        BQ_TRY(bq_prepare_hop_links(c));
+        src = c->U_hop;
+    }
+    BQ_CUDA_TRY(cudaMemcpyAsync(U, src, (size_t)c->V * 4 * 9 * sizeof(double2),
+                                where == BQ_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+    BQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return BQ_OK;
+}
+
+// --------------------------------------------------------------------------
+// log det of the clover term on one parity: per site and chirality block, LU
+// with partial pivoting of the 6x6 block in FP64; log|det| = sum log|pivot|,
+// and the block's determinant sign (real for a Hermitian block) from the
+// pivots' phases and the row swaps. Sums: [0] log|det|, [1] blocks with det < 0.
+
+__global__ void __launch_bounds__(RED_THREADS) k_clover_logdet(const double2 *blk, int Vh, double *partials,
+                                                               unsigned int *ticket, double *out) {
+    double v[2] = {0.0, 0.0};
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 2 * Vh; idx += gridDim.x * blockDim.x) {
+        const int h = idx % Vh, b = idx / Vh;
+        cplx<double> B[36];
+        load_herm6(blk, b, h, Vh, B);
+        double la = 0.0;
+        cplx<double> ph = {1.0, 0.0};
+        int swaps = 0;
+        for (int col = 0; col < 6; col++) {
+            int piv = col;
+            double best = hypot(B[col * 6 + col].re, B[col * 6 + col].im);
+            for (int r = col + 1; r < 6; r++) {
+                const double m = hypot(B[r * 6 + col].re, B[r * 6 + col].im);
+                if (m > best) {
+                    best = m;
+                    piv = r;
+                }
+            }
+            if (!(best > 0.0)) {
+                la = -INFINITY;
+                break;
+            }
+            if (piv != col) {
+                swaps++;
+                for (int j = 0; j < 6; j++) {
+                    const cplx<double> t = B[col * 6 + j];
+                    B[col * 6 + j] = B[piv * 6 + j];
+                    B[piv * 6 + j] = t;
+                }
+            }
+            const cplx<double> p = B[col * 6 + col];
+            la += log(best);
+            ph = cmul(ph, cplx<double>{p.re / best, p.im / best});
+            const double n2 = p.re * p.re + p.im * p.im;
+            const cplx<double> inv = {p.re / n2, -p.im / n2};
+            for (int r = col + 1; r < 6; r++) {
+                const cplx<double> f = cmul(B[r * 6 + col], inv);
+                for (int j = col; j < 6; j++) B[r * 6 + j] = csub(B[r * 6 + j], cmul(f, B[col * 6 + j]));
+            }
+        }
+        const double sg = (swaps & 1) ? -ph.re : ph.re;
+        v[0] += la;
+        v[1] += (sg < 0.0) ? 1.0 : 0.0;
+    }
+    double tot[2];
+    if (grid_sum(v, partials, ticket, tot) && threadIdx.x == 0) {
+        out[0] = tot[0];
+        out[1] = tot[1];
+    }
+}
+
+extern "C" int bq_clover_logdet(bq_ctx *c, int parity, double *logdet, int *negative) {
+    if (!c || !logdet || !(parity == 0 || parity == 1)) {
+        bq_set_error("bq_clover_logdet: bad arguments");
+        return BQ_ERR_ARG;
+    }
+    if (!c->have_gauge) {
+        bq_set_error("gauge field not set");
+        return BQ_ERR_STATE;
+    }
+    BQ_TRY(bq_prepare_clover(c, BQ_PREC_DOUBLE));
+    const size_t pblk = (size_t)36 * c->Vh;
+    const double2 *blk = reinterpret_cast<const double2 *>(c->clov_master) + (size_t)(parity * 2 + 0) * pblk;
+    double *res = c->red_partials + 2 * RED_MAX_BLOCKS;
+    k_clover_logdet<<<red_grid(2 * c->Vh), RED_THREADS, 0, c->stream>>>(blk, c->Vh, c->red_partials, c->red_ticket,
+                                                                          res);
+    BQ_LAUNCH_CHECK();
+    BQ_COUNT(c);
+    double h[2];
+    BQ_CUDA_TRY(cudaMemcpyAsync(h, res, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    BQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    *logdet = h[0];
+    if (negative) *negative = (int)h[1];
+    if (!(h[0] > -INFINITY)) {
+        bq_set_error("bq_clover_logdet: singular clover block");
+        return BQ_ERR_CLOVER_SINGULAR;
+    }
+    return BQ_OK;
+}

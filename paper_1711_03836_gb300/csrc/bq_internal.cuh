@@ -608,6 +608,10 @@ struct bq_ctx {
 
     // master fields (FP64, device)
     double2 *U_canon;  // [V][4][9]
+    double2 *U_hop;    // stout-smeared copy for the hopping term (stout_iter > 0), same layout
+    int U_hop_valid;
+    double stout_rho;
+    int stout_iter;
     double *A_u1;      // [V][4] or null
     int have_gauge;
 
@@ -652,6 +656,7 @@ cudaError_t bq_event_record(bq_ctx *c, cudaEvent_t ev);
 // field preparation (bq_fields.cu)
 int bq_prepare_links(bq_ctx *c, int prec);
 int bq_prepare_clover(bq_ctx *c, int prec);
+int bq_prepare_hop_links(bq_ctx *c);  // stout-smeared canonical links of the hopping term (bq_gauge.cu)
 int bq_alloc(void **p, size_t bytes);
 int bq_pack(bq_ctx *c, void *native, const double *canon_dev, int prec);
 int bq_unpack(bq_ctx *c, double *canon_dev, const void *native, int prec);

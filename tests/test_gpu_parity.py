@@ -531,3 +531,51 @@ def test_full_system_device_buffers_and_zero_source(bq):
         bq.bq_solve_full(lat.ctx, x_e, x_o, b_e, b_o, method="bicgstab", tol=1e-10, max_iter=2)
     assert e.value.status == bq.BQ_ERR_NOT_CONVERGED
     lat.close()
+
+
+@pytest.mark.parametrize("rho,n_iter", [(0.1, 1), (0.125, 3)])
+def test_stout_links_parity(bq, rho, n_iter):
+    """Stout-smeared links of the hopping term against the oracle, element by element."""
+    dims = (6, 4, 6, 10)
+    lat, U, A, p = make(bq, dims, eps=0.3)
+    bq.bq_set_stout(lat.ctx, rho, n_iter)
+    got = bq.bq_get_hop_links(lat.ctx, np.empty_like(U))
+    expect = oracle.stout(dims, U, rho, n_iter)
+    assert np.abs(got - expect).max() < 1e-13
+    bq.bq_set_stout(lat.ctx, 0.0, 0)
+    assert np.array_equal(bq.bq_get_hop_links(lat.ctx, np.empty_like(U)), U)
+    lat.close()
+
+
+@pytest.mark.parametrize("prec,recon,mu,charge", [("double", 18, 0.0, 0.0), ("double", 12, 0.1, 0.0),
+                                                  ("single", 12, 0.0, 0.0), ("double", 18, 0.0, 2.0 / 3.0),
+                                                  ("half", 18, 0.1, -1.0 / 3.0)])
+def test_stout_operator_parity(bq, prec, recon, mu, charge):
+    """Mhat with stout-smeared hopping links and the clover term from the thin links."""
+    dims = (6, 4, 6, 10)
+    lat, U, A, p = make(bq, dims, mu=mu, charge=charge, recon=recon, precision=prec)
+    bq.bq_set_stout(lat.ctx, 0.1, 1)
+    op = oracle.Operator(p, U, A, U_hop=oracle.stout(dims, U, 0.1, 1))
+    psi = synth.gaussian_spinor(lat.Vh, 41)
+    src, dst = lat.pack(psi, prec), lat.spinor(prec)
+    for dag in (False, True):
+        bq.bq_apply_mhat(lat.ctx, dst, src, dag, prec)
+        assert rel(lat.unpack(dst, prec), op.mhat(psi, dag)) < TOL[prec]
+    # a new gauge field is smeared again
+    U2 = synth.gauge_field(dims, 0.25, 9)
+    bq.bq_set_gauge(lat.ctx, U2)
+    op2 = oracle.Operator(p, U2, A, U_hop=oracle.stout(dims, U2, 0.1, 1))
+    bq.bq_apply_mhat(lat.ctx, dst, src, False, prec)
+    assert rel(lat.unpack(dst, prec), op2.mhat(psi)) < TOL[prec]
+    lat.close()
+
+
+@pytest.mark.parametrize("dims,eps", [((6, 4, 6, 10), 0.3), ((8, 8, 8, 8), 0.6)])
+def test_clover_logdet_parity(bq, dims, eps):
+    lat, U, A, p = make(bq, dims, kappa=0.1355, csw=1.9, eps=eps)
+    for par in (0, 1):
+        ld, neg = bq.bq_clover_logdet(lat.ctx, par)
+        ld_o, neg_o = oracle.clover_logdet(p, U, par)
+        assert abs(ld - ld_o) <= 1e-12 * max(1.0, abs(ld_o)) + 1e-10, (ld, ld_o)
+        assert neg == neg_o == 0
+    lat.close()

@@ -1,0 +1,96 @@
+"""Pins of the oracle's stout smearing and clover log det.
+
+Stout smearing (the singly iterated stout links of the QCD+QED fermion action,
+Eq. 5; Morningstar and Peardon 2004) is checked against a closed form on
+diagonal (abelian) SU(3) fields, where every matrix commutes and each link
+phase moves by the imaginary part of its staple sum; against gauge covariance;
+and against the group property of the result. The clover log det (Eq. 2) is
+checked against the closed form of a constant abelian field strength.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_03836_gb300 import synth
+from helpers import abelian_background, gauge_transform
+
+
+def _neighbour(dims, mu, d):
+    """lex index of x + d mu-hat for every lex site x (periodic)."""
+    c = synth.lex_coords(dims)
+    c[:, mu] = (c[:, mu] + d) % dims[mu]
+    return c[:, 0] + dims[0] * (c[:, 1] + dims[1] * (c[:, 2] + dims[2] * c[:, 3]))
+
+
+def test_stout_rho_zero_and_unit_gauge():
+    dims = (4, 2, 4, 6)
+    U = synth.gauge_field(dims, 0.3, 2)
+    assert np.array_equal(oracle.stout(dims, U, 0.0, 1), U)
+    one = synth.unit_gauge(dims)
+    assert np.abs(oracle.stout(dims, one, 0.2, 2) - one).max() < 1e-15
+
+
+@pytest.mark.parametrize("rho", [0.1, 0.25])
+def test_stout_abelian_closed_form(rho):
+    """Diagonal links diag(e^{i theta_a}), sum_a theta_a = 0: the smeared phase is
+    theta_a + Im w_a - (1/3) sum_b Im w_b with w_a = rho e^{-i theta_a(x,mu)} times
+    the sum of the staple phases."""
+    dims = (4, 6, 2, 4)
+    rng = np.random.default_rng(11)
+    V = synth.volume(dims)
+    th = rng.normal(0, 0.7, (V, 4, 3))
+    th -= th.mean(axis=2, keepdims=True)
+    U = np.zeros((V, 4, 3, 3), complex)
+    for a in range(3):
+        U[:, :, a, a] = np.exp(1j * th[:, :, a])
+    w = np.zeros((V, 4, 3), complex)
+    for mu in range(4):
+        for nu in range(4):
+            if nu == mu:
+                continue
+            xpn, xpm, xmn = _neighbour(dims, nu, 1), _neighbour(dims, mu, 1), _neighbour(dims, nu, -1)
+            xmn_pm = _neighbour(dims, mu, 1)[xmn]
+            up = th[:, nu] + th[xpn, mu] - th[xpm, nu]
+            lo = -th[xmn, nu] + th[xmn, mu] + th[xmn_pm, nu]
+            w[:, mu] += np.exp(1j * up) + np.exp(1j * lo)
+        w[:, mu] *= rho * np.exp(-1j * th[:, mu])
+    q = w.imag - w.imag.mean(axis=2, keepdims=True)
+    expect = np.zeros_like(U)
+    for a in range(3):
+        expect[:, :, a, a] = np.exp(1j * (th[:, :, a] + q[:, :, a]))
+    got = oracle.stout(dims, U, rho, 1)
+    assert np.abs(got - expect).max() < 1e-14
+
+
+def test_stout_gauge_covariance_and_group():
+    dims = (4, 4, 2, 6)
+    U = synth.gauge_field(dims, 0.4, 7)
+    G = synth.gauge_field(dims, 2.0, 8)[:, 0]
+    Ug, _ = gauge_transform(dims, U, None, G, None, 0.0)
+    S = oracle.stout(dims, U, 0.15, 2)
+    Sg = oracle.stout(dims, Ug, 0.15, 2)
+    expect, _ = gauge_transform(dims, S, None, G, None, 0.0)
+    assert np.abs(Sg - expect).max() < 1e-13
+    eye = np.eye(3)
+    assert np.abs(S @ np.conj(np.swapaxes(S, -1, -2)) - eye).max() < 1e-14
+    assert np.abs(np.linalg.det(S) - 1).max() < 1e-14
+    assert np.abs(S - U).max() > 1e-2  # smearing moved the links
+
+
+def test_clover_logdet_closed_form():
+    """Constant abelian field: A = 1 + i kappa c_SW sigma_{mu nu} x F, F = i diag(f_a),
+    sigma_{mu nu} has eigenvalues +-1 twice, so det A(x) = prod_a (1 - (kappa c_SW f_a)^2)^2."""
+    dims = (4, 6, 4, 8)
+    c = (1.0, 2.0, 0.0)
+    U, phi = abelian_background(dims, 0, 1, 1, c, "mu")
+    kappa, csw = 0.13, 1.9
+    p_ = oracle.params(dims, kappa=kappa, csw=csw)
+    f = np.sin(phi * np.array(c))
+    f -= f.mean()
+    per_site = 2 * np.sum(np.log(1 - (kappa * csw * f) ** 2))
+    for par in (0, 1):
+        ld, neg = oracle.clover_logdet(p_, U, par)
+        assert abs(ld - per_site * synth.volume(dims) / 2) < 1e-11 * abs(per_site * synth.volume(dims))
+        assert neg == 0
+    ld0, _ = oracle.clover_logdet(oracle.params(dims, kappa=kappa, csw=0.0), synth.gauge_field(dims, 0.3, 1), 0)
+    assert ld0 == 0.0
