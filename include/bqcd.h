@@ -271,6 +271,22 @@ int bq_solve_multishift_cg(bq_ctx *ctx, double *const *x, const double *b, int w
                            const double *shifts, const bq_solver_params *params, bq_solver_stats *stats,
                            double *residuals);
 
+/* Block multishift CG (Section 3 lists block multishift cg): the multishift
+ * solve above for nrhs right-hand sides b[r] at once. The Krylov phases of all
+ * right-hand sides run in lockstep, sharing one batched Mhat^dag Mhat per
+ * iteration (link and clover loads shared across the right-hand sides); then
+ * all nrhs * nshift shifted systems are refined together by the batched
+ * (mixed-precision) CG to a TRUE FP64 residual <= tol |b[r]|.
+ * x[r * nshift + k] receives the solution of (Mhat^dag Mhat + shifts[k]) x = b[r]
+ * (canonical even spinors, all host or all device as `where` says).
+ * stats (may be NULL) has nrhs entries: per right-hand side, iterations and
+ * Dslash calls of both phases and the worst true residual over its shifts;
+ * residuals (may be NULL) has nrhs * nshift entries. params->shift must be 0.
+ * Work vectors: nrhs * nshift solver slots on the context's device memory. */
+int bq_solve_multishift_cg_block(bq_ctx *ctx, int nrhs, double *const *x, const double *const *b, int where,
+                                 int nshift, const double *shifts, const bq_solver_params *params,
+                                 bq_solver_stats *stats, double *residuals);
+
 /* Full-lattice solve of M x = b, M = A - kappa D_hop (Eq. 1, Eq. 2), through
  * the even-odd reduction (Section 4: the matrix is even-odd preconditioned):
  *     bhat_e = b_e + kappa D_eo A_oo^{-1} b_o,   Mhat x_e = bhat_e,

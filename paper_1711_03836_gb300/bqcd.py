@@ -110,6 +110,10 @@ _SIGS = {
                                               ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(bq_solver_params), ctypes.POINTER(bq_solver_stats),
                                               ctypes.POINTER(ctypes.c_double)]),
+    "bq_solve_multishift_cg_block": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                                    ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
+                                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(bq_solver_params),
+                                                    ctypes.POINTER(bq_solver_stats), ctypes.POINTER(ctypes.c_double)]),
     "bq_set_stout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]),
     "bq_get_hop_links": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "bq_clover_logdet": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -343,6 +347,31 @@ def bq_solve_multishift_cg(ctx, xs, b, shifts, tol=1e-10, max_iter=20000, precis
     d = st.as_dict()
     d["residuals"] = list(res)
     return d
+
+
+def bq_solve_multishift_cg_block(ctx, xs, bs, shifts, tol=1e-10, max_iter=20000, precision="double", delta=1e-3,
+                                 check_every=8, raise_on_nonconvergence=True):
+    """(Mhat^dag Mhat + shifts[k]) xs[r][k] = bs[r] for every right-hand side r and shift k."""
+    nrhs, n = len(bs), len(shifts)
+    if len(xs) != nrhs or any(len(row) != n for row in xs):
+        raise ValueError("xs must hold one row of len(shifts) solutions per right-hand side")
+    ptrs = [_ptr_where(v) for v in bs] + [_ptr_where(v) for row in xs for v in row]
+    where = ptrs[0][1]
+    if any(w != where for _, w in ptrs):
+        raise ValueError("all right-hand sides and solutions must be host or all device buffers")
+    barr = (ctypes.c_void_p * nrhs)(*[p for p, _ in ptrs[:nrhs]])
+    xarr = (ctypes.c_void_p * (nrhs * n))(*[p for p, _ in ptrs[nrhs:]])
+    sarr = (ctypes.c_double * n)(*[float(v) for v in shifts])
+    res = (ctypes.c_double * (nrhs * n))()
+    sp = bq_solver_params(tol, int(max_iter), PREC_NAMES[precision], delta, int(check_every), 0.0)
+    st = (bq_solver_stats * nrhs)()
+    s = _lib_handle().bq_solve_multishift_cg_block(ctx, nrhs, xarr, barr, where, n, sarr, ctypes.byref(sp), st, res)
+    if s != BQ_OK and (raise_on_nonconvergence or s != BQ_ERR_NOT_CONVERGED):
+        raise BqError(s, "bq_solve_multishift_cg_block")
+    out = [st[r].as_dict() for r in range(nrhs)]
+    for r in range(nrhs):
+        out[r]["residuals"] = [res[r * n + k] for k in range(n)]
+    return out
 
 
 def bq_set_stout(ctx, rho, n_iter=1):

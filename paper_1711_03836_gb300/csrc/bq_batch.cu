@@ -28,7 +28,7 @@
 #include <new>
 #include <vector>
 
-#include "bq_reduce.cuh"
+#include "bq_ms.cuh"
 
 struct SysVec {
     void *b, *x, *r, *t;  // FP64 native
@@ -260,6 +260,49 @@ struct GraphRun {
     int slot0 = 0, nslots = 0;
 };
 
+// --------------------------------------------------------------------------
+// block multishift CG: several right-hand sides, each with its own shifted
+// Krylov recurrences (bodies in bq_ms.cuh), one grid row per right-hand side
+
+struct MSBArgs {
+    const MSPtrs *ptr;  // [nsys] per-shift solutions and directions
+    double *ms;         // [nsys][M_NTOTAL]
+};
+
+template <int PR>
+__global__ void __launch_bounds__(RED_THREADS) kbm_init(BArgs ba, MSBArgs m, int n, int base) {
+    BATCH_PROLOGUE
+    ms_init_body<PR>(sv.b, m.ptr[sy], n, base, Vh);
+}
+
+template <int PS, int PR>
+__global__ void __launch_bounds__(RED_THREADS) kbm_residual(BArgs ba, MSBArgs m, int n, int base) {
+    BATCH_PROLOGUE
+    double *ms = m.ms + (size_t)sy * M_NTOTAL;
+    const RedArgs ra{part, tick, scal, Vh};
+    ms_residual_body<PS, PR>(sv.Ap, sv.rs, ra, ms, n, base, ms[M_TOL2]);
+}
+
+template <int PS, int PR>
+__global__ void __launch_bounds__(RED_THREADS) kbm_update(BArgs ba, MSBArgs m, int n, int base) {
+    BATCH_PROLOGUE
+    ms_update_body<PS, PR>(sv.p, sv.rs, m.ptr[sy], m.ms + (size_t)sy * M_NTOTAL, scal, n, base, Vh);
+}
+
+// x (FP64) = y (precision PR)
+template <int PR>
+__global__ void __launch_bounds__(RED_THREADS) kbm_to_double(void *x, const void *y, int Vh) {
+    using TR = typename Traits<PR>::real;
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<TR> yv[12];
+        cplx<double> xv[12];
+        SpinorIO<PR>::load(yv, y, h, Vh);
+#pragma unroll
+        for (int c = 0; c < 12; c++) xv[c] = {(double)yv[c].re, (double)yv[c].im};
+        SpinorIO<BQ_PREC_DOUBLE>::store(x, h, Vh, xv);
+    }
+}
+
 struct BatchSlot {
     int Vh, ps, pr;
     char *b, *x, *r, *t, *rs, *xs, *p, *Ap, *to_s, *te_s, *to_d;
@@ -280,12 +323,20 @@ struct BatchWork {
     std::vector<DslashBatchTable> tables[8];
     cudaEvent_t e0, e1, t0, t1;
     // autotuned rhs mapping of the batched hopping term, cached per batch signature
-    unsigned long long tuned_sig;
-    int tuned_mapping;
+    enum { TUNE_CACHE = 4 };
+    unsigned long long tuned_sig[TUNE_CACHE];
+    int tuned_mapping[TUNE_CACHE];
+    int tuned_next;
     // instantiated graph of the iteration body, reused while its launch tables are unchanged
     GraphRun graph;
     unsigned long long graph_sig;
     int graph_gen;
+    // block multishift: per (rhs, shift) vectors at precision ms_prec, device pointer tables, scalars
+    std::vector<char *> ms_vec;  // [rhs][MS_MAX][2] (x, p)
+    int ms_prec, ms_Vh;
+    MSPtrs *d_msv;
+    double *d_ms, *h_ms;
+    int ms_cap;
 };
 
 static void free_slot(BatchSlot *s) {
@@ -321,6 +372,10 @@ void bq_batch_free(bq_ctx *c) {
     if (w->t0) cudaEventDestroy(w->t0);
     if (w->t1) cudaEventDestroy(w->t1);
     if (w->graph.exec) cudaGraphExecDestroy(w->graph.exec);
+    for (char *v : w->ms_vec) cudaFree(v);
+    cudaFree(w->d_msv);
+    cudaFree(w->d_ms);
+    cudaFreeHost(w->h_ms);
     delete w;
     c->batch = nullptr;
 }
@@ -497,7 +552,8 @@ static int mdagm_batch(bq_ctx *c0, int prec, int recon, int first_step, const Un
 // Autotuner of the batched hopping term: times one sloppy Mhat^dag Mhat of the
 // batch (after one warm-up) for each rhs mapping -- block-interleaved units and
 // warp-interleaved units of 2, 4 and 8 -- and keeps the fastest for this batch
-// (same contexts, same number of systems, same precision) on later calls.
+// (same contexts, same number of systems, same precision) on later calls; the
+// last few batch signatures are remembered.
 static int tune_mapping(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int *mapping) {
     BatchWork *w = c0->batch;
     unsigned long long sig = 1469598103934665603ull ^ (unsigned long long)nsys ^ ((unsigned long long)ps << 40);
@@ -507,10 +563,11 @@ static int tune_mapping(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int *
         if (i > 0) run = (ctxs[i] == ctxs[i - 1]) ? run + 1 : 1;
         maxrun = run > maxrun ? run : maxrun;
     }
-    if (w->tuned_sig == sig) {
-        *mapping = w->tuned_mapping;
-        return BQ_OK;
-    }
+    for (int e = 0; e < BatchWork::TUNE_CACHE; e++)
+        if (w->tuned_sig[e] == sig) {
+            *mapping = w->tuned_mapping[e];
+            return BQ_OK;
+        }
     int cand[4] = {-1, 2, 4, 8};
     int ncand = 1;
     for (int k = 1; k < 4; k++)
@@ -536,8 +593,9 @@ static int tune_mapping(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int *
             best_m = cand[k];
         }
     }
-    w->tuned_sig = sig;
-    w->tuned_mapping = best_m;
+    w->tuned_sig[w->tuned_next] = sig;
+    w->tuned_mapping[w->tuned_next] = best_m;
+    w->tuned_next = (w->tuned_next + 1) % BatchWork::TUNE_CACHE;
     *mapping = best_m;
     return BQ_OK;
 }
@@ -971,4 +1029,245 @@ extern "C" int bq_solve_cg(bq_ctx *c, double *x, const double *b, int where, con
     double *xs[1] = {x};
     const double *bs[1] = {b};
     return bq_solve_cg_batch(ctxs, 1, xs, bs, where, sp, st);
+}
+
+// --------------------------------------------------------------------------
+// block multishift CG (Section 3 lists block multishift cg): the multishift
+// Krylov phase of every right-hand side in lockstep -- one batched
+// Mhat^dag Mhat per iteration for all of them (shared link loads), one grid
+// row per right-hand side in the BLAS steps -- then every (rhs, shift) pair
+// refined by the batched reliable-update CG to the true FP64 residual.
+
+template <int PS, int PR>
+static int ms_block_run(bq_ctx *c0, int nrhs, int n, const double *shifts, int base, double tol_ms,
+                        const bq_solver_params *sp, std::vector<int> &iters) {
+    BatchWork *w = c0->batch;
+    cudaStream_t s = c0->stream;
+    std::vector<bq_ctx *> ctxs(nrhs, c0);
+    const int Vh = c0->Vh;
+    const dim3 G(red_grid(Vh), nrhs);
+    // per (rhs, shift) solution and direction vectors
+    const size_t vb = spinor_bytes_per_site(PR) * (size_t)Vh;
+    if (w->ms_prec != PR || w->ms_Vh != Vh) {
+        for (char *v : w->ms_vec) cudaFree(v);
+        w->ms_vec.clear();
+        w->ms_prec = PR;
+        w->ms_Vh = Vh;
+    }
+    if ((int)w->ms_vec.size() < nrhs * MS_MAX * 2) w->ms_vec.resize((size_t)nrhs * MS_MAX * 2, nullptr);
+    std::vector<MSPtrs> hp(nrhs);
+    for (int r = 0; r < nrhs; r++) {
+        for (int k = 0; k < MS_MAX; k++) {
+            hp[r].x[k] = hp[r].p[k] = nullptr;
+            if (k >= n) continue;
+            char **xv = &w->ms_vec[((size_t)r * MS_MAX + k) * 2], **pv = xv + 1;
+            BQ_TRY(bq_alloc((void **)xv, vb));
+            hp[r].x[k] = *xv;
+            if (k != base) {
+                BQ_TRY(bq_alloc((void **)pv, vb));
+                hp[r].p[k] = *pv;
+            }
+        }
+    }
+    if (w->ms_cap < nrhs) {
+        cudaFree(w->d_msv);
+        cudaFree(w->d_ms);
+        cudaFreeHost(w->h_ms);
+        w->d_msv = nullptr;
+        w->d_ms = w->h_ms = nullptr;
+        w->ms_cap = 0;
+        BQ_TRY(bq_alloc((void **)&w->d_msv, sizeof(MSPtrs) * nrhs));
+        BQ_TRY(bq_alloc((void **)&w->d_ms, sizeof(double) * M_NTOTAL * nrhs));
+        BQ_CUDA_TRY(cudaMallocHost((void **)&w->h_ms, sizeof(double) * M_NTOTAL * nrhs));
+        w->ms_cap = nrhs;
+    }
+    // system tables, scalars (the base shift in S_SIGMA), the per-shift recurrences
+    std::vector<SysVec> hs(nrhs);
+    std::vector<double> hscal((size_t)S_NSCAL * nrhs, 0.0);
+    double *hms = w->h_ms;
+    memset(hms, 0, sizeof(double) * M_NTOTAL * nrhs);
+    for (int r = 0; r < nrhs; r++) {
+        BatchSlot *sl = &w->slot[r];
+        hs[r] = SysVec{sl->b, sl->x, sl->r, sl->t, sl->rs, sl->xs, sl->p, sl->Ap, sl->Vh};
+        hscal[(size_t)r * S_NSCAL + S_SIGMA] = shifts[base];
+        double *m = hms + (size_t)r * M_NTOTAL;
+        for (int k = 0; k < n; k++) {
+            m[M_ZETA * MS_MAX + k] = m[M_ZOLD * MS_MAX + k] = m[M_ACTIVE * MS_MAX + k] = 1.0;
+            m[M_SHIFT * MS_MAX + k] = shifts[k];
+        }
+        m[M_APREV] = 1.0;
+        m[M_NACTIVE] = n;
+    }
+    UnitPlan plan;
+    int mapping = -1;
+    if (nrhs > 1) BQ_TRY(tune_mapping(c0, nrhs, ctxs.data(), PS, &mapping));
+    BQ_TRY(build_units(c0, nrhs, ctxs.data(), PS, mapping, &plan));
+    BQ_CUDA_TRY(cudaMemcpyAsync(w->d_sys, hs.data(), sizeof(SysVec) * nrhs, cudaMemcpyHostToDevice, s));
+    BQ_CUDA_TRY(cudaMemcpyAsync(w->d_scal, hscal.data(), sizeof(double) * S_NSCAL * nrhs, cudaMemcpyHostToDevice, s));
+    BQ_CUDA_TRY(cudaMemcpyAsync(w->d_msv, hp.data(), sizeof(MSPtrs) * nrhs, cudaMemcpyHostToDevice, s));
+    double *active = w->h_flags;
+    for (int r = 0; r < nrhs; r++) active[r] = 1.0;
+    BQ_CUDA_TRY(cudaMemcpyAsync(w->d_flags, active, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    const BArgs ba{w->d_sys, w->d_scal, w->d_part, w->d_ticket, w->d_flags};
+    const MSBArgs mb{w->d_msv, w->d_ms};
+    kb_init<PS, PR><<<G, RED_THREADS, 0, s>>>(ba, 0);
+    BQ_COUNT(c0);
+    kbm_init<PR><<<G, RED_THREADS, 0, s>>>(ba, mb, n, base);
+    BQ_COUNT(c0);
+    BQ_LAUNCH_CHECK();
+    BQ_CUDA_TRY(cudaMemcpyAsync(w->h_scal, w->d_scal, sizeof(double) * S_NSCAL * nrhs, cudaMemcpyDeviceToHost, s));
+    BQ_CUDA_TRY(cudaStreamSynchronize(s));
+    int nactive = 0;
+    for (int r = 0; r < nrhs; r++) {
+        const double bb = w->h_scal[(size_t)r * S_NSCAL + S_BB];
+        hms[(size_t)r * M_NTOTAL + M_TOL2] = tol_ms * tol_ms * bb;
+        iters[r] = 0;
+        if (bb == 0.0) active[r] = 0.0;
+        else nactive++;
+    }
+    BQ_CUDA_TRY(cudaMemcpyAsync(w->d_ms, hms, sizeof(double) * M_NTOTAL * nrhs, cudaMemcpyHostToDevice, s));
+    BQ_CUDA_TRY(cudaMemcpyAsync(w->d_flags, active, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    const int recon_s = c0->links_recon[PS];
+    const int check = sp->check_every > 0 ? sp->check_every : 1;
+    int it = 0;
+    while (nactive > 0 && it < sp->max_iter) {
+        BQ_TRY(mdagm_batch(c0, PS, recon_s, 0, &plan, nrhs, w->d_flags, (double)nactive / nrhs));
+        kb_pap<PS><<<G, RED_THREADS, 0, s>>>(ba);
+        BQ_COUNT(c0);
+        kbm_residual<PS, PR><<<G, RED_THREADS, 0, s>>>(ba, mb, n, base);
+        BQ_COUNT(c0);
+        kbm_update<PS, PR><<<G, RED_THREADS, 0, s>>>(ba, mb, n, base);
+        BQ_COUNT(c0);
+        BQ_LAUNCH_CHECK();
+        it++;
+        for (int r = 0; r < nrhs; r++)
+            if (active[r] != 0.0) iters[r]++;
+        if (it % check != 0) continue;
+        BQ_CUDA_TRY(cudaMemcpyAsync(hms, w->d_ms, sizeof(double) * M_NTOTAL * nrhs, cudaMemcpyDeviceToHost, s));
+        BQ_CUDA_TRY(cudaStreamSynchronize(s));
+        int changed = 0;
+        for (int r = 0; r < nrhs; r++) {
+            if (active[r] == 0.0) continue;
+            const double na = hms[(size_t)r * M_NTOTAL + M_NACTIVE];
+            if (!(na == na)) {
+                bq_set_error("block multishift: right-hand side %d breakdown (NaN)", r);
+                return BQ_ERR_NOT_CONVERGED;
+            }
+            if (na == 0.0) {
+                active[r] = 0.0;
+                nactive--;
+                changed = 1;
+            }
+        }
+        if (changed)
+            BQ_CUDA_TRY(cudaMemcpyAsync(w->d_flags, active, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    }
+    return BQ_OK;
+}
+
+extern "C" int bq_solve_multishift_cg_block(bq_ctx *c, int nrhs, double *const *x, const double *const *b, int where,
+                                            int nshift, const double *shifts, const bq_solver_params *sp,
+                                            bq_solver_stats *stats, double *residuals) {
+    if (!c || nrhs < 1 || !x || !b || !shifts || !sp || !(where == BQ_HOST || where == BQ_DEVICE) || nshift < 1 ||
+        nshift > MS_MAX) {
+        bq_set_error("bq_solve_multishift_cg_block: bad arguments (nrhs >= 1, 1 <= nshift <= %d)", MS_MAX);
+        return BQ_ERR_ARG;
+    }
+    const int nsys = nrhs * nshift;
+    for (int j = 0; j < nsys; j++)
+        if (!x[j]) {
+            bq_set_error("bq_solve_multishift_cg_block: null solution pointer %d", j);
+            return BQ_ERR_ARG;
+        }
+    for (int r = 0; r < nrhs; r++)
+        if (!b[r]) {
+            bq_set_error("bq_solve_multishift_cg_block: null right-hand side %d", r);
+            return BQ_ERR_ARG;
+        }
+    for (int k = 0; k < nshift; k++)
+        if (!(shifts[k] >= 0.0)) {
+            bq_set_error("bq_solve_multishift_cg_block: negative shift %d", k);
+            return BQ_ERR_ARG;
+        }
+    BQ_TRY(check_solver_params(sp));
+    if (sp->shift != 0.0) {
+        bq_set_error("bq_solve_multishift_cg_block: params->shift must be 0 (shifts come in the array)");
+        return BQ_ERR_ARG;
+    }
+    const int ps = sp->precision, pr = (ps == BQ_PREC_HALF) ? BQ_PREC_SINGLE : ps;
+    std::vector<bq_ctx *> ctxs(nsys, c);
+    BQ_TRY(bq_batch_prepare(1, ctxs.data(), ps));
+    BQ_TRY(bq_batch_reserve(c, nsys, ctxs.data(), ps, pr));
+    BatchWork *w = c->batch;
+    std::vector<bq_solver_stats> local;
+    bq_solver_stats *st = stats;
+    if (!st) {
+        local.resize(nrhs);
+        st = local.data();
+    }
+    for (int r = 0; r < nrhs; r++) memset(&st[r], 0, sizeof st[r]);
+    BQ_CUDA_TRY(cudaEventRecord(w->e0, c->stream));
+    for (int r = 0; r < nrhs; r++) BQ_TRY(bq_spinor_pack(c, w->slot[r].b, b[r], BQ_PREC_DOUBLE, where));
+    int base = 0;
+    for (int k = 1; k < nshift; k++)
+        if (shifts[k] < shifts[base]) base = k;
+    // the sloppy Krylov spaces run to what their precision resolves; refinement does the rest
+    double tol_ms = ps == BQ_PREC_DOUBLE ? sp->tol : ps == BQ_PREC_SINGLE ? 1e-6 : 1e-3;
+    if (tol_ms < sp->tol) tol_ms = sp->tol;
+    std::vector<int> iters(nrhs, 0);
+    int status;
+    if (ps == BQ_PREC_DOUBLE)
+        status = ms_block_run<BQ_PREC_DOUBLE, BQ_PREC_DOUBLE>(c, nrhs, nshift, shifts, base, tol_ms, sp, iters);
+    else if (ps == BQ_PREC_SINGLE)
+        status = ms_block_run<BQ_PREC_SINGLE, BQ_PREC_SINGLE>(c, nrhs, nshift, shifts, base, tol_ms, sp, iters);
+    else
+        status = ms_block_run<BQ_PREC_HALF, BQ_PREC_SINGLE>(c, nrhs, nshift, shifts, base, tol_ms, sp, iters);
+    if (status != BQ_OK) return status;
+    // system j = r * nshift + k starts from the Krylov solution of (r, k); slots are
+    // filled from the highest j down, so slot r still holds b_r when it is read
+    const int G = red_grid(c->Vh);
+    std::vector<double> sh(nsys);
+    for (int j = nsys - 1; j >= 0; j--) {
+        const int r = j / nshift, k = j % nshift;
+        sh[j] = shifts[k];
+        const void *xk = w->ms_vec[((size_t)r * MS_MAX + k) * 2];
+        if (pr == BQ_PREC_DOUBLE)
+            kbm_to_double<BQ_PREC_DOUBLE><<<G, RED_THREADS, 0, c->stream>>>(w->slot[j].x, xk, c->Vh);
+        else
+            kbm_to_double<BQ_PREC_SINGLE><<<G, RED_THREADS, 0, c->stream>>>(w->slot[j].x, xk, c->Vh);
+        BQ_COUNT(c);
+        BQ_LAUNCH_CHECK();
+        if (r != j)
+            BQ_CUDA_TRY(cudaMemcpyAsync(w->slot[j].b, w->slot[r].b, spinor_bytes_per_site(BQ_PREC_DOUBLE) * c->Vh,
+                                        cudaMemcpyDeviceToDevice, c->stream));
+    }
+    std::vector<bq_solver_stats> rs(nsys);
+    int s2 = bq_cg_batch_core(c, nsys, ctxs.data(), sh.data(), sp, true, rs.data());
+    if (s2 != BQ_OK && s2 != BQ_ERR_NOT_CONVERGED) return s2;
+    int all = 1;
+    for (int r = 0; r < nrhs; r++) {
+        st[r].iterations = iters[r];
+        st[r].dslash_calls = 4.0 * iters[r];
+        st[r].converged = 1;
+    }
+    for (int j = 0; j < nsys; j++) {
+        const int r = j / nshift;
+        BQ_TRY(bq_spinor_unpack(c, x[j], w->slot[j].x, BQ_PREC_DOUBLE, where));
+        st[r].iterations += rs[j].iterations;
+        st[r].reliable_updates += rs[j].reliable_updates;
+        st[r].dslash_calls += rs[j].dslash_calls;
+        if (!rs[j].converged) st[r].converged = all = 0;
+        if (rs[j].true_residual > st[r].true_residual) st[r].true_residual = rs[j].true_residual;
+        if (residuals) residuals[j] = rs[j].true_residual;
+    }
+    float msec = 0.f;
+    BQ_CUDA_TRY(cudaEventRecord(w->e1, c->stream));
+    BQ_CUDA_TRY(cudaEventSynchronize(w->e1));
+    cudaEventElapsedTime(&msec, w->e0, w->e1);
+    for (int r = 0; r < nrhs; r++) st[r].seconds = msec * 1e-3;
+    if (!all) {
+        bq_set_error("block multishift refinement reached max_iter");
+        return BQ_ERR_NOT_CONVERGED;
+    }
+    return BQ_OK;
 }

@@ -173,6 +173,7 @@ int bicgstab(bq_ctx *c, int prec, const Bicg &w, double tol_abs, int max_iter, i
     zc rho(1, 0), alpha(1, 0), omega(1, 0), rr;
     BQ_TRY(dotc(c, prec, w.r, w.r, &rr));
     *iters = 0;
+    const double rr_start = rr.real();
     double r0n = rr.real();  // |r0|^2 of the current shadow residual
     if (rr.real() <= tol_abs * tol_abs) return BQ_OK;
     for (int k = 0; k < max_iter; k++) {
@@ -214,8 +215,11 @@ int bicgstab(bq_ctx *c, int prec, const Bicg &w, double tol_abs, int max_iter, i
         BQ_TRY(dotc(c, prec, w.r, w.r, &rr));
         *dslash += 4;
         *iters = k + 1;
-        if (!(rr.real() == rr.real())) {
-            bq_set_error("BiCGstab breakdown at iteration %d: NaN residual", k);
+        if (!(rr.real() <= 1e12 * rr_start)) {
+            // NaN, or growth by 1e6 in norm: past the critical kappa the spectrum of
+            // Mhat surrounds the origin and BiCGstab diverges (CG on Mhat^dag Mhat does not)
+            bq_set_error("BiCGstab diverged at iteration %d: |r|^2 = %.3e from %.3e (use the CG method)", k,
+                         rr.real(), rr_start);
             return BQ_ERR_NOT_CONVERGED;
         }
         if (rr.real() <= tol_abs * tol_abs) break;

@@ -579,3 +579,47 @@ def test_clover_logdet_parity(bq, dims, eps):
         assert abs(ld - ld_o) <= 1e-12 * max(1.0, abs(ld_o)) + 1e-10, (ld, ld_o)
         assert neg == neg_o == 0
     lat.close()
+
+
+@pytest.mark.parametrize("prec", ["double", "single", "half"])
+def test_block_multishift_cg(bq, prec):
+    """Three right-hand sides (one of them zero) x four shifts: every solution
+    against the oracle's CG of its own shifted system, and its FP64 residual."""
+    dims = (6, 4, 6, 10)
+    lat, U, A, p = make(bq, dims, kappa=0.13, csw=1.7, mu=0.0, recon=12 if prec != "double" else 18,
+                        precision=prec)
+    op = oracle.Operator(p, U)
+    bs = [synth.gaussian_spinor(lat.Vh, 800 + r) for r in range(2)] + [np.zeros((lat.Vh, 4, 3), np.complex128)]
+    shifts = [0.002, 0.03, 0.3, 1.0]
+    xs = [[np.empty_like(bs[0]) for _ in shifts] for _ in bs]
+    st = bq.bq_solve_multishift_cg_block(lat.ctx, xs, bs, shifts, tol=1e-10, precision=prec,
+                                         delta=1e-3 if prec != "half" else 1e-1)
+    for r, b in enumerate(bs):
+        assert st[r]["converged"] == 1
+        for k, sh in enumerate(shifts):
+            if not b.any():
+                assert not xs[r][k].any()
+                continue
+            res = np.linalg.norm(op.mdagm(xs[r][k], sh) - b) / np.linalg.norm(b)
+            assert res <= 1e-10 and abs(st[r]["residuals"][k] - res) < 1e-11, (r, k, res)
+            xo, _ = op.cg(b, sh, tol=1e-12)
+            assert rel(xs[r][k], xo) < 1e-8
+    lat.close()
+
+
+def test_block_multishift_matches_single_rhs(bq):
+    """One right-hand side through the block solver equals the multishift solver's result
+    within the solves' tolerance; device buffers."""
+    import torch
+
+    dims = (4, 4, 4, 6)
+    lat, U, A, p = make(bq, dims, kappa=0.12, csw=1.0, mu=0.0)
+    b = torch.from_numpy(synth.gaussian_spinor(lat.Vh, 71)).cuda()
+    shifts = [0.01, 0.1, 1.0]
+    xb = [[torch.empty_like(b) for _ in shifts]]
+    xm = [torch.empty_like(b) for _ in shifts]
+    bq.bq_solve_multishift_cg_block(lat.ctx, xb, [b], shifts, tol=1e-11, precision="single")
+    bq.bq_solve_multishift_cg(lat.ctx, xm, b, shifts, tol=1e-11, precision="single")
+    for k in range(len(shifts)):
+        assert rel(xb[0][k].cpu().numpy(), xm[k].cpu().numpy()) < 1e-9
+    lat.close()
