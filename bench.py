@@ -399,6 +399,19 @@ def batched_extras(torch, bqcd):
                                           for x, sh in zip(xk, shifts)])
     out["multishift_10_24^3x48"] = {"multishift_ms": ms_m, "separate_cg_ms": ms_10, "speedup": ms_10 / ms_m,
                                     "worst_true_residual": st_m["true_residual"]}
+    # block multishift: 4 right-hand sides x the same 10 shifts vs 4 multishift solves in turn
+    b4 = [torch.from_numpy(synth.gaussian_spinor(lat.Vh, 780 + r)).cuda() for r in range(4)]
+    x4 = [[torch.empty_like(b) for _ in shifts] for _ in b4]
+    mkw = dict(tol=1e-10, precision="single", delta=1e-3)
+    bqcd.bq_solve_multishift_cg_block(lat.ctx, x4, b4, shifts, **mkw)
+    st_bm, ms_bm = _timed(torch, lambda: bqcd.bq_solve_multishift_cg_block(lat.ctx, x4, b4, shifts, **mkw))
+    st_sm, ms_sm = _timed(torch, lambda: [bqcd.bq_solve_multishift_cg(lat.ctx, x4[r], b4[r], shifts, **mkw)
+                                          for r in range(4)])
+    out["block_multishift_4x10_24^3x48"] = {
+        "block_ms": ms_bm, "multishift_in_turn_ms": ms_sm, "speedup": ms_sm / ms_bm,
+        "worst_true_residual": max(s_["true_residual"] for s_ in st_bm),
+        "krylov_plus_refinement_iterations_max": max(s_["iterations"] for s_ in st_bm)}
+    del x4, b4
     lat.close()
     # ragged: 8^4, 12^4, 16^3x32, 20^3x40 in one batched solve
     lats, bs, xr = [], [], []
@@ -575,6 +588,23 @@ def extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, mixed_ms, torch, bqcd):
         if k.startswith("double") and k.endswith("native"):
             # native FP64 is bound by the FP64 units: 1.25 TFLOP/s nominal on GB300
             v["frac_of_fp64_alu_1250"] = v["GFLOP/s"] / FP64_PEAK_GFLOPS
+
+    # ---- gauge-side setup: one stout step of every link, clover log det of each parity
+    Vfull = 2 * Vh
+    U_dev = torch.empty((Vfull, 4, 3, 3), dtype=torch.complex128, device="cuda")
+    bqcd.bq_set_stout(ctx, 0.1, 1)
+    bqcd.bq_get_hop_links(ctx, U_dev)  # warm
+    bqcd.bq_set_stout(ctx, 0.0, 0)
+    bqcd.bq_set_stout(ctx, 0.1, 1)
+    _, ms_stout = _timed(torch, lambda: bqcd.bq_get_hop_links(ctx, U_dev))
+    bqcd.bq_set_stout(ctx, 0.0, 0)
+    _, ms_copy = _timed(torch, lambda: bqcd.bq_get_hop_links(ctx, U_dev))
+    del U_dev
+    bqcd.bq_clover_logdet(ctx, 1)
+    (ld, neg), ms_ld = _timed(torch, lambda: bqcd.bq_clover_logdet(ctx, 1))
+    out["gauge_setup"] = {"stout_step_ms": ms_stout - ms_copy, "stout_plus_link_copy_ms": ms_stout,
+                          "stout_GB/s_links_in_out": 2 * Vfull * 4 * 144 / ((ms_stout - ms_copy) * 1e-3) / 1e9,
+                          "clover_logdet_odd_ms": ms_ld, "clover_logdet_odd": ld, "negative_blocks": neg}
 
     # ---- batching (row a9) and multishift (row a8), each against the same work done one system at a time
     out["batched"] = batched_extras(torch, bqcd)

@@ -297,7 +297,9 @@ int bq_solve_multishift_cg_block(bq_ctx *ctx, int nrhs, double *const *x, const 
  * (Section 4 lists BiCGstab) runs BiCGstab on Mhat itself, in FP64 or, for
  * params->precision SINGLE/HALF, as FP64 defect correction around a BiCGstab
  * in that precision which reduces its own residual by params->delta
- * (0 = 1e-3) per outer step. params->shift must be 0.
+ * (0 = 1e-3) per outer step. params->shift must be 0. dagger = 1 solves
+ * M^dag x = b instead (M^dag = A - kappa D^dag, the same steps with D^dag and
+ * Mhat^dag).
  * b_e, b_o, x_e, x_o: canonical spinors [V/2][4][3] complex of the even and
  * odd parity, on the host or the device as `where` says; x is overwritten
  * (the solve starts from 0). stats->true_residual = |b - M x| / |b| over both
@@ -306,7 +308,24 @@ int bq_solve_multishift_cg_block(bq_ctx *ctx, int nrhs, double *const *x, const 
  * BiCGstab breaks down (rho or omega 0). b = 0 gives x = 0. Allocates and frees
  * its own 18 half-lattice work vectors per call. */
 int bq_solve_full(bq_ctx *ctx, double *x_e, double *x_o, const double *b_e, const double *b_o, int where,
-                  int method, const bq_solver_params *params, bq_solver_stats *stats);
+                  int method, int dagger, const bq_solver_params *params, bq_solver_stats *stats);
+
+/* Stochastic trace samples of the fermion matrix (Section 5 lists Tr M^{-1},
+ * Tr gamma_5 M^{-1} and Tr (M^dag M)^{-1} among the measurements). For each
+ * noise vector eta_n = (eta_e[n], eta_o[n]) (canonical even and odd halves,
+ * host or device as `where` says; Z2 or Gaussian noise drawn by the caller)
+ * x = M^{-1} eta and y = M^{-dag} eta are solved to a true full-lattice FP64
+ * residual <= params->tol |eta| (all 2 * nnoise reduced systems in one batched
+ * (mixed-precision) CG on Mhat^dag Mhat, restarted until each even residual
+ * meets the target), and
+ *   samples[5n + 0, 1] = Re, Im  eta^dag x            (-> Tr M^{-1})
+ *   samples[5n + 2, 3] = Re, Im  eta^dag gamma_5 x    (-> Tr gamma_5 M^{-1})
+ *   samples[5n + 4]    = |y|^2 = eta^dag (M^dag M)^{-1} eta
+ * are written; the mean over the noise estimates each trace when the noise has
+ * E[eta eta^dag] = 1. stats (may be NULL) has 2 * nnoise entries: the M solve
+ * of noise n at n, the M^dag solve at nnoise + n. params->shift must be 0. */
+int bq_trace_samples(bq_ctx *ctx, int nnoise, const double *const *eta_e, const double *const *eta_o, int where,
+                     const bq_solver_params *params, double *samples, bq_solver_stats *stats);
 
 #ifdef __cplusplus
 }

@@ -279,15 +279,39 @@ class Operator:
         y_o = clover_apply(self.Aoo, x_o) - k * dhop(self.p, self.U, self.A, x_e, 1)
         return y_e, y_o
 
-    def solve_full(self, b_e, b_o, tol=1e-12, maxiter=20000):
+    def full_dagger(self, x_e, x_o):
+        """M^dag x = (A - kappa D_hop^dag) x (A Hermitian), as even and odd halves."""
+        k = self.p.kappa
+        y_e = clover_apply(self.Aee, x_e) - k * dhop(self.p, self.U, self.A, x_o, 0, dagger=True)
+        y_o = clover_apply(self.Aoo, x_o) - k * dhop(self.p, self.U, self.A, x_e, 1, dagger=True)
+        return y_e, y_o
+
+    def solve_full(self, b_e, b_o, tol=1e-12, maxiter=20000, dagger=False):
         """x with M x = b by block elimination of the odd sites: CG on
         Mhat^dag Mhat x_e = Mhat^dag (b_e + kappa D_eo A_oo^{-1} b_o), then
-        x_o = A_oo^{-1} (b_o + kappa D_oe x_e)."""
+        x_o = A_oo^{-1} (b_o + kappa D_oe x_e). For M^dag x = b the same with
+        D^dag: Mhat^dag x_e = bhat by CG on Mhat^dag Mhat z = bhat, x_e = Mhat z."""
         k = self.p.kappa
-        bhat = _c128(b_e) + k * dhop(self.p, self.U, self.A, clover_apply(self.Aoo_inv, b_o), 0)
-        x_e, _ = self.cg(self.mhat(bhat, dagger=True), tol=tol, maxiter=maxiter)
-        x_o = clover_apply(self.Aoo_inv, _c128(b_o) + k * dhop(self.p, self.U, self.A, x_e, 1))
+        bhat = _c128(b_e) + k * dhop(self.p, self.U, self.A, clover_apply(self.Aoo_inv, b_o), 0, dagger=dagger)
+        if dagger:
+            z, _ = self.cg(bhat, tol=tol, maxiter=maxiter)
+            x_e = self.mhat(z)
+        else:
+            x_e, _ = self.cg(self.mhat(bhat, dagger=True), tol=tol, maxiter=maxiter)
+        x_o = clover_apply(self.Aoo_inv, _c128(b_o) + k * dhop(self.p, self.U, self.A, x_e, 1, dagger=dagger))
         return x_e, x_o
+
+    def trace_samples(self, eta_e, eta_o, tol=1e-12):
+        """(eta^dag M^{-1} eta, eta^dag gamma_5 M^{-1} eta, |M^{-dag} eta|^2) of one
+        noise vector: the summands of the stochastic estimates of Tr M^{-1},
+        Tr gamma_5 M^{-1} and Tr (M^dag M)^{-1}."""
+        x_e, x_o = self.solve_full(eta_e, eta_o, tol=tol)
+        y_e, y_o = self.solve_full(eta_e, eta_o, tol=tol, dagger=True)
+        g5 = np.array([1, 1, -1, -1], float)[None, :, None]
+        s1 = np.vdot(eta_e, x_e) + np.vdot(eta_o, x_o)
+        s2 = np.vdot(eta_e, g5 * x_e) + np.vdot(eta_o, g5 * x_o)
+        s3 = np.vdot(y_e, y_e).real + np.vdot(y_o, y_o).real
+        return np.array([s1, s2, s3])
 
 
 def mhat_sites(p, U, A, psi, sites, dagger=False):

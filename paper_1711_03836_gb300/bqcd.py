@@ -119,8 +119,12 @@ _SIGS = {
     "bq_clover_logdet": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int)]),
     "bq_solve_full": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                     ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(bq_solver_params),
-                                     ctypes.POINTER(bq_solver_stats)]),
+                                     ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(bq_solver_params), ctypes.POINTER(bq_solver_stats)]),
+    "bq_trace_samples": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                        ctypes.POINTER(bq_solver_params), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(bq_solver_stats)]),
 }
 
 
@@ -394,8 +398,8 @@ def bq_clover_logdet(ctx, parity):
 
 
 def bq_solve_full(ctx, x_e, x_o, b_e, b_o, method="bicgstab", tol=1e-10, max_iter=20000, precision="double",
-                  delta=1e-3, check_every=8, raise_on_nonconvergence=True):
-    """Solve M x = b on the full lattice (even and odd halves, canonical, all host or all device)."""
+                  delta=1e-3, check_every=8, dagger=False, raise_on_nonconvergence=True):
+    """Solve M x = b (or M^dag x = b) on the full lattice (even and odd halves, canonical, all host or all device)."""
     ptrs = [_ptr_where(v) for v in (x_e, x_o, b_e, b_o)]
     where = ptrs[0][1]
     if any(w != where for _, w in ptrs):
@@ -403,10 +407,38 @@ def bq_solve_full(ctx, x_e, x_o, b_e, b_o, method="bicgstab", tol=1e-10, max_ite
     sp = bq_solver_params(tol, int(max_iter), PREC_NAMES[precision], delta, int(check_every), 0.0)
     st = bq_solver_stats()
     s = _lib_handle().bq_solve_full(ctx, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], where,
-                                    SOLVER_NAMES[method], ctypes.byref(sp), ctypes.byref(st))
+                                    SOLVER_NAMES[method], int(bool(dagger)), ctypes.byref(sp), ctypes.byref(st))
     if s != BQ_OK and (raise_on_nonconvergence or s != BQ_ERR_NOT_CONVERGED):
         raise BqError(s, "bq_solve_full")
     return st.as_dict()
+
+
+def bq_trace_samples(ctx, etas_e, etas_o, tol=1e-10, max_iter=20000, precision="double", delta=1e-3,
+                     check_every=8, raise_on_nonconvergence=True):
+    """Per noise vector: (eta^dag M^-1 eta, eta^dag gamma_5 M^-1 eta, eta^dag (M^dag M)^-1 eta) as a
+    numpy array [nnoise, 3] (complex, complex, real), and the per-solve stats (M solves, then M^dag solves)."""
+    n = len(etas_e)
+    if len(etas_o) != n or n < 1:
+        raise ValueError("one odd half per even half, at least one noise vector")
+    pe = [_ptr_where(v) for v in etas_e]
+    po = [_ptr_where(v) for v in etas_o]
+    where = pe[0][1]
+    if any(w != where for _, w in pe + po):
+        raise ValueError("noise vectors must all be host or all be device buffers")
+    earr = (ctypes.c_void_p * n)(*[p for p, _ in pe])
+    oarr = (ctypes.c_void_p * n)(*[p for p, _ in po])
+    sp = bq_solver_params(tol, int(max_iter), PREC_NAMES[precision], delta, int(check_every), 0.0)
+    out = (ctypes.c_double * (5 * n))()
+    st = (bq_solver_stats * (2 * n))()
+    s = _lib_handle().bq_trace_samples(ctx, n, earr, oarr, where, ctypes.byref(sp), out, st)
+    if s != BQ_OK and (raise_on_nonconvergence or s != BQ_ERR_NOT_CONVERGED):
+        raise BqError(s, "bq_trace_samples")
+    v = np.array(out[:], dtype=np.float64).reshape(n, 5)
+    res = np.empty((n, 3), np.complex128)
+    res[:, 0] = v[:, 0] + 1j * v[:, 1]
+    res[:, 1] = v[:, 2] + 1j * v[:, 3]
+    res[:, 2] = v[:, 4]
+    return res, [st[i].as_dict() for i in range(2 * n)]
 
 
 # ---------------------------------------------------------------- convenience

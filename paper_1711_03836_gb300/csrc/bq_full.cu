@@ -7,6 +7,8 @@
 //   Mhat x_e = bhat_e      (CG on Mhat^dag Mhat, or BiCGstab on Mhat)
 //   x_o = A_oo^{-1} (b_o + kappa D_oe x_e)
 //   r = b - M x on both parities, from two fused launches (A x - kappa D y).
+// The adjoint system M^dag x = b (M^dag = A - kappa D^dag: projectors 1 -+ gamma
+// swapped and mu -> -mu) takes the same steps with D^dag and Mhat^dag.
 //
 // Mixed-precision BiCGstab is FP64 defect correction: r = bhat - Mhat x in
 // FP64, an FP32 (or FP16-storage) BiCGstab solves Mhat d = r until its own
@@ -15,6 +17,7 @@
 #include <string.h>
 
 #include <complex>
+#include <vector>
 
 #include "bq_reduce.cuh"
 
@@ -163,7 +166,7 @@ struct Bicg {
     void *b, *x, *r, *r0, *p, *v, *s, *t, *tmp_o;
 };
 
-int bicgstab(bq_ctx *c, int prec, const Bicg &w, double tol_abs, int max_iter, int *iters, double *dslash) {
+int bicgstab(bq_ctx *c, int prec, int dag, const Bicg &w, double tol_abs, int max_iter, int *iters, double *dslash) {
     const zc one(1, 0), zero(0, 0);
     BQ_TRY(axpy3(c, prec, w.x, zero, nullptr, zero, nullptr, zero, nullptr));
     BQ_TRY(axpy3(c, prec, w.r, one, w.b, zero, nullptr, zero, nullptr));
@@ -200,12 +203,12 @@ int bicgstab(bq_ctx *c, int prec, const Bicg &w, double tol_abs, int max_iter, i
         const zc beta = (rho_new / rho) * (alpha / omega);
         rho = rho_new;
         BQ_TRY(axpy3(c, prec, w.p, one, w.r, beta, w.p, -beta * omega, w.v));  // p = r + beta (p - omega v)
-        BQ_TRY(bq_mhat_launch(c, prec, w.v, w.p, 0, w.tmp_o));                 // v = Mhat p
+        BQ_TRY(bq_mhat_launch(c, prec, w.v, w.p, dag, w.tmp_o));               // v = Mhat p
         zc r0v;
         BQ_TRY(dotc(c, prec, w.r0, w.v, &r0v));
         alpha = rho / r0v;
         BQ_TRY(axpy3(c, prec, w.s, one, w.r, -alpha, w.v, zero, nullptr));     // s = r - alpha v
-        BQ_TRY(bq_mhat_launch(c, prec, w.t, w.s, 0, w.tmp_o));                 // t = Mhat s
+        BQ_TRY(bq_mhat_launch(c, prec, w.t, w.s, dag, w.tmp_o));               // t = Mhat s
         zc ts, tt;
         BQ_TRY(dotc(c, prec, w.t, w.s, &ts));
         BQ_TRY(dotc(c, prec, w.t, w.t, &tt));
@@ -248,7 +251,7 @@ void free_full(FullWork *w) {
 }
 
 // Mhat x_e = bhat by BiCGstab: FP64, or FP64 defect correction around a lower-precision BiCGstab
-int solve_mhat_bicgstab(bq_ctx *c, FullWork &w, const bq_solver_params *sp, double bb, bq_solver_stats *st) {
+int solve_mhat_bicgstab(bq_ctx *c, FullWork &w, int dag, const bq_solver_params *sp, double bb, bq_solver_stats *st) {
     const int pin = sp->precision;
     const zc one(1, 0), zero(0, 0);
     BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.xe, zero, nullptr, zero, nullptr, zero, nullptr));
@@ -265,13 +268,13 @@ int solve_mhat_bicgstab(bq_ctx *c, FullWork &w, const bq_solver_params *sp, doub
         const double tol_in = (pin == BQ_PREC_DOUBLE) ? 0.5 * sqrt(target2)
                                                       : fmax(delta * sqrt(rr.real()), 0.5 * sqrt(target2));
         int its = 0;
-        BQ_TRY(bicgstab(c, pin, bw, tol_in, sp->max_iter - total, &its, &st->dslash_calls));
+        BQ_TRY(bicgstab(c, pin, dag, bw, tol_in, sp->max_iter - total, &its, &st->dslash_calls));
         total += its;
         if (pin == BQ_PREC_DOUBLE)
             BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.xe, one, w.xe, one, w.ix, zero, nullptr));
         else
             BQ_TRY(add_to_double(c, w.xe, w.ix, pin));
-        BQ_TRY(bq_mhat_launch(c, BQ_PREC_DOUBLE, w.ye, w.xe, 0, w.to));  // r = bhat - Mhat x_e (FP64)
+        BQ_TRY(bq_mhat_launch(c, BQ_PREC_DOUBLE, w.ye, w.xe, dag, w.to));  // r = bhat - Mhat x_e (FP64)
         BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.r, one, w.bh, zc(-1, 0), w.ye, zero, nullptr));
         BQ_TRY(dotc(c, BQ_PREC_DOUBLE, w.r, w.r, &rr));
         st->reliable_updates++;
@@ -283,8 +286,10 @@ int solve_mhat_bicgstab(bq_ctx *c, FullWork &w, const bq_solver_params *sp, doub
 }
 
 // Mhat x_e = bhat by CG on the normal equations (batched core), restarted from
-// the current x_e until the even residual itself meets the target
-int solve_mhat_cg(bq_ctx *c, FullWork &w, const bq_solver_params *sp, double bb, bq_solver_stats *st) {
+// the current x_e until the even residual itself meets the target. For the
+// adjoint (dag = 1), Mhat^dag x_e = bhat is solved as Mhat^dag Mhat z = bhat,
+// x_e = Mhat z.
+int solve_mhat_cg(bq_ctx *c, FullWork &w, int dag, const bq_solver_params *sp, double bb, bq_solver_stats *st) {
     const zc one(1, 0), zero(0, 0);
     bq_ctx *ctxs[1] = {c};
     const int pin = sp->precision, pr = (pin == BQ_PREC_HALF) ? BQ_PREC_SINGLE : pin;
@@ -298,7 +303,11 @@ int solve_mhat_cg(bq_ctx *c, FullWork &w, const bq_solver_params *sp, double bb,
     for (int round = 0; round < 20 && rr.real() > target2 && st->iterations < sp->max_iter; round++) {
         // Mhat^dag Mhat d = Mhat^dag r; the normal-equation tolerance asks for a
         // quarter of the remaining reduction of the even residual
-        BQ_TRY(bq_mhat_launch(c, BQ_PREC_DOUBLE, bq_batch_slot_b(c, 0), w.r, 1, w.to));
+        if (dag)
+            BQ_CUDA_TRY(cudaMemcpyAsync(bq_batch_slot_b(c, 0), w.r, spinor_bytes_per_site(BQ_PREC_DOUBLE) * c->Vh,
+                                        cudaMemcpyDeviceToDevice, c->stream));
+        else
+            BQ_TRY(bq_mhat_launch(c, BQ_PREC_DOUBLE, bq_batch_slot_b(c, 0), w.r, 1, w.to));
         bq_solver_params cp = *sp;
         cp.tol = fmin(0.5, fmax(1e-13, 0.25 * sqrt(target2 / rr.real())));
         cp.max_iter = sp->max_iter - st->iterations;
@@ -309,8 +318,13 @@ int solve_mhat_cg(bq_ctx *c, FullWork &w, const bq_solver_params *sp, double bb,
         st->iterations += cs.iterations;
         st->reliable_updates += cs.reliable_updates;
         st->dslash_calls += cs.dslash_calls + 4;
-        BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.xe, one, w.xe, one, bq_batch_slot_x(c, 0), zero, nullptr));
-        BQ_TRY(bq_mhat_launch(c, BQ_PREC_DOUBLE, w.ye, w.xe, 0, w.to));
+        if (dag) {
+            BQ_TRY(bq_mhat_launch(c, BQ_PREC_DOUBLE, w.ye, bq_batch_slot_x(c, 0), 0, w.to));
+            BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.xe, one, w.xe, one, w.ye, zero, nullptr));
+        } else {
+            BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.xe, one, w.xe, one, bq_batch_slot_x(c, 0), zero, nullptr));
+        }
+        BQ_TRY(bq_mhat_launch(c, BQ_PREC_DOUBLE, w.ye, w.xe, dag, w.to));
         BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.r, one, w.bh, zc(-1, 0), w.ye, zero, nullptr));
         BQ_TRY(dotc(c, BQ_PREC_DOUBLE, w.r, w.r, &rr));
     }
@@ -320,9 +334,9 @@ int solve_mhat_cg(bq_ctx *c, FullWork &w, const bq_solver_params *sp, double bb,
 }  // namespace
 
 extern "C" int bq_solve_full(bq_ctx *c, double *x_e, double *x_o, const double *b_e, const double *b_o, int where,
-                             int method, const bq_solver_params *sp, bq_solver_stats *st) {
+                             int method, int dagger, const bq_solver_params *sp, bq_solver_stats *st) {
     if (!c || !x_e || !x_o || !b_e || !b_o || !sp || !(where == BQ_HOST || where == BQ_DEVICE) ||
-        !(method == BQ_SOLVER_CG || method == BQ_SOLVER_BICGSTAB)) {
+        !(method == BQ_SOLVER_CG || method == BQ_SOLVER_BICGSTAB) || !(dagger == 0 || dagger == 1)) {
         bq_set_error("bq_solve_full: bad arguments");
         return BQ_ERR_ARG;
     }
@@ -348,6 +362,7 @@ extern "C" int bq_solve_full(bq_ctx *c, double *x_e, double *x_o, const double *
         status = BQ_ERR_CUDA;
     }
     const double kappa = c->params.kappa;
+    const int dag = dagger;
     const zc one(1, 0), zero(0, 0);
     auto run = [&]() -> int {
         BQ_CUDA_TRY(cudaEventRecord(e0, c->stream));
@@ -362,21 +377,21 @@ extern "C" int bq_solve_full(bq_ctx *c, double *x_e, double *x_o, const double *
             BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.xo, zero, nullptr, zero, nullptr, zero, nullptr));
             st->converged = 1;
         } else {
-            // bhat_e = b_e + kappa D_eo A_oo^{-1} b_o
+            // bhat_e = b_e + kappa D_eo A_oo^{-1} b_o (D^dag for the adjoint; A is Hermitian)
             BQ_TRY(bq_clover_launch(c, BQ_PREC_DOUBLE, w.to, w.bo, 1, 1));
-            BQ_TRY(bq_dslash_launch(c, BQ_PREC_DOUBLE, w.te, w.to, 0, 0, EPI_PLAIN, nullptr, 0.0));
+            BQ_TRY(bq_dslash_launch(c, BQ_PREC_DOUBLE, w.te, w.to, 0, dag, EPI_PLAIN, nullptr, 0.0));
             BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.bh, one, w.be, zc(kappa, 0), w.te, zero, nullptr));
             st->dslash_calls += 1;
             // the odd residual vanishes after the reconstruction, so |bhat - Mhat x_e| <= tol |b| is the goal
-            if (method == BQ_SOLVER_BICGSTAB) BQ_TRY(solve_mhat_bicgstab(c, w, sp, bb, st));
-            else BQ_TRY(solve_mhat_cg(c, w, sp, bb, st));
+            if (method == BQ_SOLVER_BICGSTAB) BQ_TRY(solve_mhat_bicgstab(c, w, dag, sp, bb, st));
+            else BQ_TRY(solve_mhat_cg(c, w, dag, sp, bb, st));
             // x_o = A_oo^{-1} (b_o + kappa D_oe x_e)
-            BQ_TRY(bq_dslash_launch(c, BQ_PREC_DOUBLE, w.to, w.xe, 1, 0, EPI_PLAIN, nullptr, 0.0));
+            BQ_TRY(bq_dslash_launch(c, BQ_PREC_DOUBLE, w.to, w.xe, 1, dag, EPI_PLAIN, nullptr, 0.0));
             BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.to, one, w.bo, zc(kappa, 0), w.to, zero, nullptr));
             BQ_TRY(bq_clover_launch(c, BQ_PREC_DOUBLE, w.xo, w.to, 1, 1));
             // true residual of the full system: (M x)_p = A_pp x_p - kappa D x_{1-p}
-            BQ_TRY(bq_dslash_launch(c, BQ_PREC_DOUBLE, w.te, w.xo, 0, 0, EPI_XPAY, w.xe, kappa));
-            BQ_TRY(bq_dslash_launch(c, BQ_PREC_DOUBLE, w.to, w.xe, 1, 0, EPI_XPAY, w.xo, kappa));
+            BQ_TRY(bq_dslash_launch(c, BQ_PREC_DOUBLE, w.te, w.xo, 0, dag, EPI_XPAY, w.xe, kappa));
+            BQ_TRY(bq_dslash_launch(c, BQ_PREC_DOUBLE, w.to, w.xe, 1, dag, EPI_XPAY, w.xo, kappa));
             BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.te, one, w.be, zc(-1, 0), w.te, zero, nullptr));
             BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.to, one, w.bo, zc(-1, 0), w.to, zero, nullptr));
             st->dslash_calls += 4;
@@ -404,5 +419,236 @@ extern "C" int bq_solve_full(bq_ctx *c, double *x_e, double *x_o, const double *
         bq_set_error("full-system solve: true residual %.3e above tol", st->true_residual);
         return BQ_ERR_NOT_CONVERGED;
     }
+    return status;
+}
+
+// --------------------------------------------------------------------------
+// stochastic traces of the fermion matrix (Section 5 lists Tr M^{-1},
+// Tr gamma_5 M^{-1} and Tr (M^dag M)^{-1} among the measurements): for each
+// noise vector eta (both parities, given by the caller) x = M^{-1} eta and
+// y = M^{-dag} eta are solved, and the samples eta^dag x, eta^dag gamma_5 x and
+// |y|^2 = eta^dag (M^dag M)^{-1} eta returned; their means over the noise are
+// the estimates. All 2 * nnoise reduced systems go through the batched CG
+// together (x_e: Mhat^dag Mhat x_e = Mhat^dag r; y_e: Mhat^dag Mhat z = r,
+// y_e = Mhat z), restarted until each even residual meets tol |eta|.
+
+// [0..1] <a, b>, [2..3] <a, gamma_5 b> (gamma_5 = +1 on spins 0, 1 and -1 on 2, 3)
+__global__ void __launch_bounds__(RED_THREADS) k_dot_g5(const void *a, const void *b, double *partials,
+                                                        unsigned int *ticket, double *out, int Vh) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<double> av[12], bv[12];
+        SpinorIO<BQ_PREC_DOUBLE>::load(av, a, h, Vh);
+        SpinorIO<BQ_PREC_DOUBLE>::load(bv, b, h, Vh);
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            const double re = av[k].re * bv[k].re + av[k].im * bv[k].im;
+            const double im = av[k].re * bv[k].im - av[k].im * bv[k].re;
+            v[0] += re;
+            v[1] += im;
+            v[2] += k < 6 ? re : -re;
+            v[3] += k < 6 ? im : -im;
+        }
+    }
+    double tot[4];
+    if (grid_sum(v, partials, ticket, tot) && threadIdx.x == 0)
+        for (int k = 0; k < 4; k++) out[k] = tot[k];
+}
+
+namespace {
+
+int dot_g5(bq_ctx *c, const void *a, const void *b, double out[4]) {
+    double *res = c->red_partials + 4 * RED_MAX_BLOCKS;
+    k_dot_g5<<<red_grid(c->Vh), RED_THREADS, 0, c->stream>>>(a, b, c->red_partials, c->red_ticket, res, c->Vh);
+    BQ_LAUNCH_CHECK();
+    BQ_COUNT(c);
+    BQ_CUDA_TRY(cudaMemcpyAsync(out, res, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    BQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return BQ_OK;
+}
+
+struct TraceSys {
+    char *be, *bo;  // the noise vector (FP64 native, shared by the two systems of one noise)
+    char *bh, *xe, *xo, *r;
+    int dag;
+    double bb, rr;
+};
+
+}  // namespace
+
+extern "C" int bq_trace_samples(bq_ctx *c, int nnoise, const double *const *eta_e, const double *const *eta_o,
+                                int where, const bq_solver_params *sp, double *samples, bq_solver_stats *stats) {
+    if (!c || nnoise < 1 || !eta_e || !eta_o || !samples || !sp || !(where == BQ_HOST || where == BQ_DEVICE)) {
+        bq_set_error("bq_trace_samples: bad arguments");
+        return BQ_ERR_ARG;
+    }
+    for (int n = 0; n < nnoise; n++)
+        if (!eta_e[n] || !eta_o[n]) {
+            bq_set_error("bq_trace_samples: null noise vector %d", n);
+            return BQ_ERR_ARG;
+        }
+    const int pin = sp->precision;
+    if (!(pin == BQ_PREC_DOUBLE || pin == BQ_PREC_SINGLE || pin == BQ_PREC_HALF) || !(sp->tol > 0) ||
+        sp->max_iter < 1 || sp->shift != 0.0 || sp->delta < 0 || sp->delta >= 1) {
+        bq_set_error("bq_trace_samples: bad solver parameters (shift must be 0)");
+        return BQ_ERR_ARG;
+    }
+    if (!c->have_gauge) {
+        bq_set_error("gauge field not set");
+        return BQ_ERR_STATE;
+    }
+    const int nsys = 2 * nnoise;
+    std::vector<bq_solver_stats> local;
+    if (!stats) {
+        local.resize(nsys);
+        stats = local.data();
+    }
+    for (int s = 0; s < nsys; s++) memset(&stats[s], 0, sizeof stats[s]);
+    std::vector<bq_ctx *> ctxs(nsys, c);
+    BQ_TRY(bq_batch_prepare(1, ctxs.data(), pin));
+    BQ_TRY(bq_batch_prepare(1, ctxs.data(), BQ_PREC_DOUBLE));
+    const int pr = (pin == BQ_PREC_HALF) ? BQ_PREC_SINGLE : pin;
+    BQ_TRY(bq_batch_reserve(c, nsys, ctxs.data(), pin, pr));
+    const size_t b64 = spinor_bytes_per_site(BQ_PREC_DOUBLE) * (size_t)c->Vh;
+    std::vector<TraceSys> sy(nsys);
+    std::vector<char *> owned;
+    char *to = nullptr, *te = nullptr, *ye = nullptr;
+    int status = BQ_OK;
+    auto alloc = [&](char **p) -> int {
+        *p = nullptr;
+        int r = bq_alloc((void **)p, b64);
+        if (r == BQ_OK) owned.push_back(*p);
+        return r;
+    };
+    const double kappa = c->params.kappa;
+    const zc one(1, 0), zero(0, 0), mone(-1, 0);
+    auto run = [&]() -> int {
+        BQ_TRY(alloc(&to));
+        BQ_TRY(alloc(&te));
+        BQ_TRY(alloc(&ye));
+        for (int n = 0; n < nnoise; n++) {
+            TraceSys &a = sy[n], &d = sy[nnoise + n];
+            BQ_TRY(alloc(&a.be));
+            BQ_TRY(alloc(&a.bo));
+            d.be = a.be;
+            d.bo = a.bo;
+            a.dag = 0;
+            d.dag = 1;
+            BQ_TRY(bq_spinor_pack(c, a.be, eta_e[n], BQ_PREC_DOUBLE, where));
+            BQ_TRY(bq_spinor_pack(c, a.bo, eta_o[n], BQ_PREC_DOUBLE, where));
+            zc e2, o2;
+            BQ_TRY(dotc(c, BQ_PREC_DOUBLE, a.be, a.be, &e2));
+            BQ_TRY(dotc(c, BQ_PREC_DOUBLE, a.bo, a.bo, &o2));
+            a.bb = d.bb = e2.real() + o2.real();
+        }
+        for (int s = 0; s < nsys; s++) {
+            TraceSys &q = sy[s];
+            BQ_TRY(alloc(&q.bh));
+            BQ_TRY(alloc(&q.xe));
+            BQ_TRY(alloc(&q.xo));
+            BQ_TRY(alloc(&q.r));
+            // bhat = b_e + kappa D^(dag)_eo A_oo^{-1} b_o; x_e = 0; r = bhat
+            BQ_TRY(bq_clover_launch(c, BQ_PREC_DOUBLE, to, q.bo, 1, 1));
+            BQ_TRY(bq_dslash_launch(c, BQ_PREC_DOUBLE, te, to, 0, q.dag, EPI_PLAIN, nullptr, 0.0));
+            BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, q.bh, one, q.be, zc(kappa, 0), te, zero, nullptr));
+            BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, q.xe, zero, nullptr, zero, nullptr, zero, nullptr));
+            BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, q.r, one, q.bh, zero, nullptr, zero, nullptr));
+            zc rr;
+            BQ_TRY(dotc(c, BQ_PREC_DOUBLE, q.r, q.r, &rr));
+            q.rr = rr.real();
+            stats[s].dslash_calls += 1;
+        }
+        int done_iters = 0;
+        for (int round = 0; round < 20; round++) {
+            double tol_cg = 0.5;
+            int nact = 0;
+            for (int s = 0; s < nsys; s++) {
+                const TraceSys &q = sy[s];
+                const double t2 = sp->tol * sp->tol * q.bb;
+                void *slot_b = bq_batch_slot_b(c, s);
+                if (q.bb == 0.0 || q.rr <= t2) {
+                    BQ_CUDA_TRY(cudaMemsetAsync(slot_b, 0, b64, c->stream));
+                    continue;
+                }
+                nact++;
+                tol_cg = fmin(tol_cg, 0.25 * sqrt(t2 / q.rr));
+                if (q.dag)
+                    BQ_CUDA_TRY(cudaMemcpyAsync(slot_b, q.r, b64, cudaMemcpyDeviceToDevice, c->stream));
+                else
+                    BQ_TRY(bq_mhat_launch(c, BQ_PREC_DOUBLE, slot_b, q.r, 1, to));
+            }
+            if (nact == 0 || done_iters >= sp->max_iter) break;
+            bq_solver_params cp = *sp;
+            cp.tol = fmax(1e-13, tol_cg);
+            cp.max_iter = sp->max_iter - done_iters;
+            std::vector<bq_solver_stats> cs(nsys);
+            int s2 = bq_cg_batch_core(c, nsys, ctxs.data(), nullptr, &cp, false, cs.data());
+            if (s2 != BQ_OK && s2 != BQ_ERR_NOT_CONVERGED) return s2;
+            int round_max = 0;
+            for (int s = 0; s < nsys; s++) {
+                TraceSys &q = sy[s];
+                stats[s].iterations += cs[s].iterations;
+                stats[s].reliable_updates += cs[s].reliable_updates;
+                stats[s].dslash_calls += cs[s].dslash_calls;
+                round_max = cs[s].iterations > round_max ? cs[s].iterations : round_max;
+                if (cs[s].iterations == 0) continue;
+                void *d = bq_batch_slot_x(c, s);
+                if (q.dag) {
+                    BQ_TRY(bq_mhat_launch(c, BQ_PREC_DOUBLE, ye, d, 0, to));
+                    d = ye;
+                }
+                BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, q.xe, one, q.xe, one, d, zero, nullptr));
+                BQ_TRY(bq_mhat_launch(c, BQ_PREC_DOUBLE, ye, q.xe, q.dag, to));
+                BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, q.r, one, q.bh, mone, ye, zero, nullptr));
+                zc rr;
+                BQ_TRY(dotc(c, BQ_PREC_DOUBLE, q.r, q.r, &rr));
+                q.rr = rr.real();
+                stats[s].dslash_calls += q.dag ? 4 : 2;
+            }
+            done_iters += round_max;
+        }
+        // odd halves, true full residuals, samples
+        int all = 1;
+        for (int s = 0; s < nsys; s++) {
+            TraceSys &q = sy[s];
+            BQ_TRY(bq_dslash_launch(c, BQ_PREC_DOUBLE, to, q.xe, 1, q.dag, EPI_PLAIN, nullptr, 0.0));
+            BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, to, one, q.bo, zc(kappa, 0), to, zero, nullptr));
+            BQ_TRY(bq_clover_launch(c, BQ_PREC_DOUBLE, q.xo, to, 1, 1));
+            BQ_TRY(bq_dslash_launch(c, BQ_PREC_DOUBLE, te, q.xo, 0, q.dag, EPI_XPAY, q.xe, kappa));
+            BQ_TRY(bq_dslash_launch(c, BQ_PREC_DOUBLE, to, q.xe, 1, q.dag, EPI_XPAY, q.xo, kappa));
+            BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, te, one, q.be, mone, te, zero, nullptr));
+            BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, to, one, q.bo, mone, to, zero, nullptr));
+            zc re, ro;
+            BQ_TRY(dotc(c, BQ_PREC_DOUBLE, te, te, &re));
+            BQ_TRY(dotc(c, BQ_PREC_DOUBLE, to, to, &ro));
+            stats[s].dslash_calls += 4;
+            stats[s].true_residual = q.bb > 0 ? sqrt((re.real() + ro.real()) / q.bb) : 0.0;
+            stats[s].converged = stats[s].true_residual <= sp->tol;
+            if (!stats[s].converged) all = 0;
+        }
+        for (int n = 0; n < nnoise; n++) {
+            const TraceSys &a = sy[n], &d = sy[nnoise + n];
+            double ge[4], go[4];
+            BQ_TRY(dot_g5(c, a.be, a.xe, ge));
+            BQ_TRY(dot_g5(c, a.bo, a.xo, go));
+            zc ye2, yo2;
+            BQ_TRY(dotc(c, BQ_PREC_DOUBLE, d.xe, d.xe, &ye2));
+            BQ_TRY(dotc(c, BQ_PREC_DOUBLE, d.xo, d.xo, &yo2));
+            double *o = samples + (size_t)n * 5;
+            o[0] = ge[0] + go[0];
+            o[1] = ge[1] + go[1];
+            o[2] = ge[2] + go[2];
+            o[3] = ge[3] + go[3];
+            o[4] = ye2.real() + yo2.real();
+        }
+        if (!all) {
+            bq_set_error("bq_trace_samples: a solve stayed above tol");
+            return BQ_ERR_NOT_CONVERGED;
+        }
+        return BQ_OK;
+    };
+    status = run();
+    cudaStreamSynchronize(c->stream);
+    for (char *p : owned) cudaFree(p);
     return status;
 }

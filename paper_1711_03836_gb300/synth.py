@@ -138,3 +138,11 @@ def half_sites(dims, parity: int) -> np.ndarray:
     sel = lex[par == parity]
     assert np.all(sel // 2 == np.arange(len(sel)))
     return sel
+
+
+def z2_noise(n_sites: int, seed: int) -> np.ndarray:
+    """Complex Z2 x Z2 noise [n][4][3]: each component (+-1 +- i)/sqrt(2), so that
+    E[eta eta^dag] = 1 (the noise of stochastic trace estimates)."""
+    rng = np.random.default_rng(seed)
+    s = rng.integers(0, 2, (n_sites, 4, 3, 2)) * 2 - 1
+    return (s[..., 0] + 1j * s[..., 1]) / np.sqrt(2.0)

@@ -623,3 +623,40 @@ def test_block_multishift_matches_single_rhs(bq):
     for k in range(len(shifts)):
         assert rel(xb[0][k].cpu().numpy(), xm[k].cpu().numpy()) < 1e-9
     lat.close()
+
+
+@pytest.mark.parametrize("method,prec,mu", [("cg", "single", 0.1), ("bicgstab", "double", 0.1), ("cg", "half", 0.0)])
+def test_full_system_adjoint_solve(bq, method, prec, mu):
+    """M^dag x = b through the adjoint even-odd reduction, checked with the oracle's M^dag."""
+    dims = (6, 4, 6, 10)
+    lat, U, A, p = make(bq, dims, kappa=0.12, csw=1.7, mu=mu, recon=12 if prec != "double" else 18, precision=prec)
+    op = oracle.Operator(p, U)
+    b_e, b_o = synth.gaussian_spinor(lat.Vh, 521), synth.gaussian_spinor(lat.Vh, 522)
+    x_e, x_o = np.empty_like(b_e), np.empty_like(b_o)
+    st = bq.bq_solve_full(lat.ctx, x_e, x_o, b_e, b_o, method=method, tol=1e-10, precision=prec,
+                          delta=1e-1 if prec == "half" else 1e-3, dagger=True)
+    y_e, y_o = op.full_dagger(x_e, x_o)
+    bn = np.sqrt(np.linalg.norm(b_e) ** 2 + np.linalg.norm(b_o) ** 2)
+    res = np.sqrt(np.linalg.norm(y_e - b_e) ** 2 + np.linalg.norm(y_o - b_o) ** 2) / bn
+    assert st["converged"] == 1 and res <= 1e-10 and abs(st["true_residual"] - res) < 1e-11
+    xo_e, xo_o = op.solve_full(b_e, b_o, tol=1e-12, dagger=True)
+    assert rel(np.concatenate([x_e.ravel(), x_o.ravel()]), np.concatenate([xo_e.ravel(), xo_o.ravel()])) < 1e-8
+    lat.close()
+
+
+@pytest.mark.parametrize("prec,mu,charge", [("single", 0.0, 0.0), ("double", 0.1, 2.0 / 3.0)])
+def test_trace_samples(bq, prec, mu, charge):
+    """Per noise vector, the three trace samples against the oracle's (Z2 noise, four vectors)."""
+    dims = (6, 4, 6, 10)
+    lat, U, A, p = make(bq, dims, kappa=0.13, csw=1.7, mu=mu, charge=charge, precision=prec)
+    op = oracle.Operator(p, U, A)
+    etas = [(synth.z2_noise(lat.Vh, 900 + 2 * n), synth.z2_noise(lat.Vh, 901 + 2 * n)) for n in range(4)]
+    got, st = bq.bq_trace_samples(lat.ctx, [e for e, _ in etas], [o for _, o in etas], tol=1e-10, precision=prec)
+    assert all(s_["converged"] for s_ in st) and max(s_["true_residual"] for s_ in st) <= 1e-10
+    eta2 = 2 * lat.Vh * 12  # |eta|^2 of unit-modulus noise
+    for n, (e, o) in enumerate(etas):
+        ref = op.trace_samples(e, o, tol=1e-12)
+        for k in range(3):
+            # a solve to 1e-10 moves eta^dag x by at most cond(M) 1e-10 |eta|^2
+            assert abs(got[n, k] - ref[k]) <= 1e-7 * abs(ref[k]) + 1e-8 * eta2, (n, k, got[n, k], ref[k])
+    lat.close()

@@ -94,3 +94,55 @@ def test_clover_logdet_closed_form():
         assert neg == 0
     ld0, _ = oracle.clover_logdet(oracle.params(dims, kappa=kappa, csw=0.0), synth.gauge_field(dims, 0.3, 1), 0)
     assert ld0 == 0.0
+
+
+# ---------------------------------------------------------------- stochastic traces
+
+def _dense_full(op, Vh):
+    n = Vh * 12
+    M = np.empty((2 * n, 2 * n), complex)
+    for j in range(2 * n):
+        e = np.zeros(2 * n, complex)
+        e[j] = 1
+        y_e, y_o = op.full(e[:n].reshape(Vh, 4, 3), e[n:].reshape(Vh, 4, 3))
+        M[:, j] = np.concatenate([y_e.ravel(), y_o.ravel()])
+    return M
+
+
+@pytest.mark.parametrize("mu_chem,charge", [(0.0, 0.0), (0.2, 2.0 / 3.0)])
+def test_trace_samples_sum_to_dense_traces(mu_chem, charge):
+    """Summed over every unit vector (exact probing), the three samples give
+    Tr M^{-1}, Tr gamma_5 M^{-1} and Tr (M^dag M)^{-1} of the dense matrix; the
+    adjoint operator is the dense conjugate transpose."""
+    dims = (2, 2, 2, 4)
+    U = synth.gauge_field(dims, 0.4, 3)
+    A = synth.u1_field(dims, 0.1, 4) if charge else None
+    p_ = oracle.params(dims, kappa=0.12, csw=1.3, mu=mu_chem, t_bc=-1.0, charge=charge)
+    op = oracle.Operator(p_, U, A)
+    Vh = oracle.half_volume(p_)
+    n = Vh * 12
+    M = _dense_full(op, Vh)
+    rng = np.random.default_rng(5)
+    xe, xo = [rng.standard_normal((Vh, 4, 3)) + 1j * rng.standard_normal((Vh, 4, 3)) for _ in range(2)]
+    ye, yo = op.full_dagger(xe, xo)
+    got = np.concatenate([ye.ravel(), yo.ravel()])
+    assert np.abs(got - M.conj().T @ np.concatenate([xe.ravel(), xo.ravel()])).max() < 1e-12
+    tot = np.zeros(3, complex)
+    for j in range(2 * n):
+        e = np.zeros(2 * n, complex)
+        e[j] = 1
+        tot += op.trace_samples(e[:n].reshape(Vh, 4, 3), e[n:].reshape(Vh, 4, 3), tol=1e-13)
+    Mi = np.linalg.inv(M)
+    G5 = np.kron(np.eye(2 * Vh), np.kron(np.diag([1.0, 1.0, -1.0, -1.0]), np.eye(3)))
+    assert abs(tot[0] - np.trace(Mi)) < 1e-9 * abs(np.trace(Mi))
+    assert abs(tot[1] - np.trace(G5 @ Mi)) < 1e-9 * np.abs(Mi).sum()
+    sv = np.linalg.svd(M, compute_uv=False)
+    assert abs(tot[2] - np.sum(sv ** -2.0)) < 1e-9 * np.sum(sv ** -2.0)
+
+
+def test_z2_noise_moments():
+    eta = synth.z2_noise(20000, 3)
+    assert np.allclose(np.abs(eta), 1.0)
+    flat = eta.reshape(-1, 12)
+    C = flat.T @ flat.conj() / flat.shape[0]
+    assert np.abs(C - np.eye(12)).max() < 0.03
