@@ -64,12 +64,57 @@ __device__ __forceinline__ void accumulate(cplx<T> acc[12], const cplx<T> u0[3],
     }
 }
 
+// acc + G f u and acc + G i f u (G = +-1): one FMA per real component, the sign
+// folded into the multiplier
+template <int G, typename T>
+__device__ __forceinline__ cplx<T> cacc(cplx<T> acc, cplx<T> u, T f) {
+    return {fma(G * f, u.re, acc.re), fma(G * f, u.im, acc.im)};
+}
+template <int G, typename T>
+__device__ __forceinline__ cplx<T> cacc_i(cplx<T> acc, cplx<T> u, T f) {
+    return {fma(-G * f, u.im, acc.re), fma(G * f, u.re, acc.im)};
+}
+
+// the same reconstruction with the hop's contribution scaled by f (the neighbour's
+// FP16 storage scale times the time-hop coefficient) inside the accumulating FMAs
+template <int MU, int S, typename T>
+__device__ __forceinline__ void accumulate_scaled(cplx<T> acc[12], const cplx<T> u0[3], const cplx<T> u1[3], T f) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        acc[c] = cacc<1>(acc[c], u0[c], f);
+        acc[3 + c] = cacc<1>(acc[3 + c], u1[c], f);
+        if (MU == 0) {  // (i S u1, i S u0)
+            acc[6 + c] = cacc_i<S>(acc[6 + c], u1[c], f);
+            acc[9 + c] = cacc_i<S>(acc[9 + c], u0[c], f);
+        } else if (MU == 1) {  // (S u1, -S u0)
+            acc[6 + c] = cacc<S>(acc[6 + c], u1[c], f);
+            acc[9 + c] = cacc<-S>(acc[9 + c], u0[c], f);
+        } else if (MU == 2) {  // (i S u0, -i S u1)
+            acc[6 + c] = cacc_i<S>(acc[6 + c], u0[c], f);
+            acc[9 + c] = cacc_i<-S>(acc[9 + c], u1[c], f);
+        } else {  // (S u0, S u1)
+            acc[6 + c] = cacc<S>(acc[6 + c], u0[c], f);
+            acc[9 + c] = cacc<S>(acc[9 + c], u1[c], f);
+        }
+    }
+}
+
 template <int PREC, int RECON, int MU, int S, bool BACK, bool SCALE>
 __device__ __forceinline__ void hop(cplx<typename Traits<PREC>::real> acc[12], const void *in, int hn,
                                     const char *lblk, int hl, int Vh, typename Traits<PREC>::real coef) {
     using T = typename Traits<PREC>::real;
+    // FP16 storage: the projection and the colour products run on the stored
+    // (unit-scale) values; the site's scale enters with the accumulation
+    constexpr bool FOLD = SCALE || PREC == BQ_PREC_HALF;
     cplx<T> psi[12];
-    SpinorIO<PREC>::load(psi, in, hn, Vh);
+    T f = SCALE ? coef : T(1);
+    if constexpr (PREC == BQ_PREC_HALF) {
+        T n;
+        SpinorIO<PREC>::load_unscaled(psi, in, hn, Vh, n);
+        f *= n;
+    } else {
+        SpinorIO<PREC>::load(psi, in, hn, Vh);
+    }
     cplx<T> h0[3], h1[3];
     project<MU, S>(psi, h0, h1);
     cplx<T> U[9];
@@ -89,12 +134,11 @@ __device__ __forceinline__ void hop(cplx<typename Traits<PREC>::real> acc[12], c
                 u1[a] = cfma(U[a * 3 + b], h1[b], u1[a]);
             }
         }
-        if (SCALE) {
-            u0[a] = cscale(coef, u0[a]);
-            u1[a] = cscale(coef, u1[a]);
-        }
     }
-    accumulate<MU, S>(acc, u0, u1);
+    if constexpr (FOLD)
+        accumulate_scaled<MU, S>(acc, u0, u1, f);
+    else
+        accumulate<MU, S>(acc, u0, u1);
 }
 
 template <int PREC, int RECON, bool DAG, int EPI>
@@ -338,9 +382,16 @@ __device__ __forceinline__ void dslash_any(const DslashArgs &a, const void *in, 
 #ifndef PLAIN_MIN_BLOCKS
 #define PLAIN_MIN_BLOCKS 5
 #endif
+#ifndef HALF_MIN_BLOCKS
+#define HALF_MIN_BLOCKS PLAIN_MIN_BLOCKS
+#endif
 template <int PREC>
-struct DslashMinBlocks {  // FP32 and FP16 storage: enough resident warps to cover memory latency
+struct DslashMinBlocks {  // FP32 storage: enough resident warps to cover memory latency
     static constexpr int value = PLAIN_MIN_BLOCKS;
+};
+template <>
+struct DslashMinBlocks<BQ_PREC_HALF> {
+    static constexpr int value = HALF_MIN_BLOCKS;
 };
 template <>
 struct DslashMinBlocks<BQ_PREC_DOUBLE> {  // FP64-unit bound: no cap

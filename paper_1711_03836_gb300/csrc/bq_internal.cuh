@@ -203,6 +203,20 @@ struct SpinorIO<BQ_PREC_HALF> {
             s[4 * k + 3] = {d.x * n, d.y * n};
         }
     }
+    // the stored values (|component| <= 1) and the site's scale n: psi = n * s
+    __device__ static __forceinline__ void load_unscaled(cplx<T> s[12], const void *base, int h, int Vh, float &n) {
+        const uint4 *p = static_cast<const uint4 *>(base);
+        n = ldg(reinterpret_cast<const float *>(p + (size_t)3 * Vh) + h);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            uint4 v = ldg(p + (size_t)k * Vh + h);
+            float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
+            s[4 * k + 0] = {a.x, a.y};
+            s[4 * k + 1] = {b.x, b.y};
+            s[4 * k + 2] = {c.x, c.y};
+            s[4 * k + 3] = {d.x, d.y};
+        }
+    }
     __device__ static __forceinline__ void store(void *base, int h, int Vh, const cplx<T> s[12]) {
         uint4 *p = static_cast<uint4 *>(base);
         float *nrm = reinterpret_cast<float *>(p + (size_t)3 * Vh);
