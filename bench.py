@@ -457,8 +457,27 @@ def full_system_extras(torch, bqcd):
         st, ms = _timed(torch, lambda: bqcd.bq_solve_full(lat.ctx, x_e, x_o, b_e, b_o, **kw))
         out[name] = {"ms": ms, "iterations": st["iterations"], "dslash_calls": st["dslash_calls"],
                      "true_residual": st["true_residual"]}
+    # stochastic traces: 8 Z2 noise vectors (16 full-lattice solves) in one batched call
+    # against the same 16 solves one full-system solve at a time
+    etas = [(torch.from_numpy(synth.z2_noise(lat.Vh, 610 + 2 * n)).cuda(),
+             torch.from_numpy(synth.z2_noise(lat.Vh, 611 + 2 * n)).cuda()) for n in range(8)]
+    tkw = dict(tol=1e-10, precision="single", delta=1e-3)
+    bqcd.bq_trace_samples(lat.ctx, [e for e, _ in etas], [o for _, o in etas], **tkw)
+    (smp, tst), ms_t = _timed(torch, lambda: bqcd.bq_trace_samples(lat.ctx, [e for e, _ in etas],
+                                                                   [o for _, o in etas], **tkw))
+
+    def one_by_one():
+        for e, o in etas:
+            for dag in (False, True):
+                bqcd.bq_solve_full(lat.ctx, x_e, x_o, e, o, method="cg", dagger=dag, **tkw)
+    _, ms_seq = _timed(torch, one_by_one)
+    out_t = {"batched_ms": ms_t, "one_solve_at_a_time_ms": ms_seq, "speedup": ms_seq / ms_t,
+             "worst_true_residual": max(s_["true_residual"] for s_ in tst),
+             "Tr_Minv_estimate": [float(smp[:, 0].real.mean()), float(smp[:, 0].imag.mean())],
+             "Tr_g5Minv_estimate": [float(smp[:, 1].real.mean()), float(smp[:, 1].imag.mean())],
+             "Tr_MdagM_inv_estimate": float(smp[:, 2].real.mean())}
     lat.close()
-    return {"full_system_24^3x48_kappa0.12_mu0.1": out}
+    return {"full_system_24^3x48_kappa0.12_mu0.1": out, "traces_8_noise_24^3x48_kappa0.12_mu0.1": out_t}
 
 
 def aggregate_ranks(ms, nbytes, device):
