@@ -568,6 +568,15 @@ def extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, mixed_ms, torch, bqcd):
         torch.cuda.synchronize()
         fp64[mode] = (e0.elapsed_time(e1), st64)
     bqcd.bq_set_fp64_arith(ctx, args.fp64_arith)
+    # the same solve with FP16 storage in the inner iteration (12-real links, per-site FP32 scale)
+    half_kw = dict(tol=1e-10, precision="half", delta=3e-3, check_every=args.check_every, max_iter=20000)
+    bqcd.bq_solve_cg(ctx, x_dev, b_dev, **half_kw)
+    e0.record()
+    st_h = bqcd.bq_solve_cg(ctx, x_dev, b_dev, **half_kw)
+    e1.record()
+    torch.cuda.synchronize()
+    out["cg_fp16_inner"] = {"ms": e0.elapsed_time(e1), "delta": 3e-3, "iterations": st_h["iterations"],
+                            "reliable_updates": st_h["reliable_updates"], "true_residual": st_h["true_residual"]}
     out["cg"] = {"fp64_native_ms": fp64["native"][0], "fp64_df64_ms": fp64["df64"][0], "mixed_ms": mixed_ms,
                  "speedup_mixed_vs_fp64_native": fp64["native"][0] / mixed_ms,
                  "speedup_mixed_vs_fp64_df64": fp64["df64"][0] / mixed_ms,

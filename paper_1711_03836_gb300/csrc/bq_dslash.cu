@@ -301,10 +301,10 @@ __device__ __forceinline__ void dslash_site_df64(const DslashArgs &a, const void
         cplx<T> h0[3], h1[3];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            const cplx<T> pa = (j0 == 3) ? psi[9 + c] : psi[6 + c];
-            const cplx<T> pb = (j1 == 3) ? psi[9 + c] : psi[6 + c];
-            h0[c] = cadd(psi[c], mul_ipow(pa, k0));
-            h1[c] = cadd(psi[3 + c], mul_ipow(pb, k1));
+            const cplx<T> pa = mul_ipow((j0 == 3) ? psi[9 + c] : psi[6 + c], k0);
+            const cplx<T> pb = mul_ipow((j1 == 3) ? psi[9 + c] : psi[6 + c], k1);
+            h0[c] = {add_lazy(psi[c].re, pa.re), add_lazy(psi[c].im, pa.im)};
+            h1[c] = {add_lazy(psi[3 + c].re, pb.re), add_lazy(psi[3 + c].im, pb.im)};
         }
         cplx<T> U[9];
         LinkIO<BQ_PREC_DF64, RECON>::load(U, lb, hl, Vh);
@@ -320,16 +320,31 @@ __device__ __forceinline__ void dslash_site_df64(const DslashArgs &a, const void
                 }
             }
         }
+        // each colour component: a lazy sum of six products per real part (twelve
+        // independent sums per hop keep the FP32 pipe busy at three warps per scheduler)
         cplx<T> u0[3], u1[3];
 #pragma unroll
         for (int aa = 0; aa < 3; aa++) {
-            u0[aa] = {T(0), T(0)};
-            u1[aa] = {T(0), T(0)};
+            dfsum r0 = dfs_prod(U[aa * 3].re, h0[0].re), i0 = dfs_prod(U[aa * 3].re, h0[0].im);
+            dfsum r1 = dfs_prod(U[aa * 3].re, h1[0].re), i1 = dfs_prod(U[aa * 3].re, h1[0].im);
+            dfs_add_prod(r0, -U[aa * 3].im, h0[0].im);
+            dfs_add_prod(i0, U[aa * 3].im, h0[0].re);
+            dfs_add_prod(r1, -U[aa * 3].im, h1[0].im);
+            dfs_add_prod(i1, U[aa * 3].im, h1[0].re);
 #pragma unroll
-            for (int b = 0; b < 3; b++) {
-                u0[aa] = cfma(U[aa * 3 + b], h0[b], u0[aa]);
-                u1[aa] = cfma(U[aa * 3 + b], h1[b], u1[aa]);
+            for (int b = 1; b < 3; b++) {
+                const cplx<T> w = U[aa * 3 + b];
+                dfs_add_prod(r0, w.re, h0[b].re);
+                dfs_add_prod(r0, -w.im, h0[b].im);
+                dfs_add_prod(i0, w.re, h0[b].im);
+                dfs_add_prod(i0, w.im, h0[b].re);
+                dfs_add_prod(r1, w.re, h1[b].re);
+                dfs_add_prod(r1, -w.im, h1[b].im);
+                dfs_add_prod(i1, w.re, h1[b].im);
+                dfs_add_prod(i1, w.im, h1[b].re);
             }
+            u0[aa] = {dfs_done(r0), dfs_done(i0)};
+            u1[aa] = {dfs_done(r1), dfs_done(i1)};
         }
         if (mu == 3) {
             const T coef = back ? cb : cf;
@@ -341,12 +356,15 @@ __device__ __forceinline__ void dslash_site_df64(const DslashArgs &a, const void
         }
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            acc[c] = cadd(acc[c], u0[c]);
-            acc[3 + c] = cadd(acc[3 + c], u1[c]);
-            acc[6 + c] = cadd(acc[6 + c], mul_ipow(m2 ? u1[c] : u0[c], k2));
-            acc[9 + c] = cadd(acc[9 + c], mul_ipow(m3 ? u1[c] : u0[c], k3));
+            const cplx<T> l2 = mul_ipow(m2 ? u1[c] : u0[c], k2), l3 = mul_ipow(m3 ? u1[c] : u0[c], k3);
+            acc[c] = {add_lazy(acc[c].re, u0[c].re), add_lazy(acc[c].im, u0[c].im)};
+            acc[3 + c] = {add_lazy(acc[3 + c].re, u1[c].re), add_lazy(acc[3 + c].im, u1[c].im)};
+            acc[6 + c] = {add_lazy(acc[6 + c].re, l2.re), add_lazy(acc[6 + c].im, l2.im)};
+            acc[9 + c] = {add_lazy(acc[9 + c].re, l3.re), add_lazy(acc[9 + c].im, l3.im)};
         }
     }
+#pragma unroll
+    for (int c = 0; c < 12; c++) acc[c] = {normalise(acc[c].re), normalise(acc[c].im)};
 
     if (EPI == EPI_PLAIN) {
         SpinorIO<BQ_PREC_DF64>::store(out, h, Vh, acc);

@@ -469,6 +469,42 @@ __device__ __forceinline__ df fma(df a, df b, df c) {
     return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
 }
 
+// Lazy double-float sums. A running sum is kept as (s, c): s the FP32 sum of
+// the leading parts, each addition made error-free by two-sum, c the FP32 sum
+// of all rounding errors, product errors and low parts; it is normalised once
+// at the end. A sum of n products costs ~12 FP32 operations per product
+// instead of a normalised df fma (~15) per product.
+struct dfsum {
+    float s, c;
+};
+__device__ __forceinline__ dfsum dfs_prod(df a, df b) {  // a * b
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return {p, e};
+}
+__device__ __forceinline__ void dfs_add_prod(dfsum &z, df a, df b) {  // z += a * b
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const df t = two_sum(z.s, p);
+    z.s = t.hi;
+    z.c = __fadd_rn(z.c, __fadd_rn(e, t.lo));
+}
+__device__ __forceinline__ df dfs_done(dfsum z) {
+    const df t = two_sum(z.s, z.c);
+    return fast_two_sum(t.hi, t.lo);
+}
+// a + b without the final normalisation: the low part may exceed half an ulp
+// of the high part; products and later sums take it at full weight
+__device__ __forceinline__ df add_lazy(df a, df b) {
+    const df t = two_sum(a.hi, b.hi);
+    return df(t.hi, __fadd_rn(t.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df normalise(df a) { return fast_two_sum(a.hi, a.lo); }
+
 // exact split of an IEEE double into hi (its leading 24 significant bits,
 // truncated) and lo (the next 29 bits rounded to 24), with integer operations
 // only; |d| outside [2^-126, 2^128) maps to 0 / infinity
@@ -587,6 +623,29 @@ __device__ __forceinline__ void herm6_apply(const T d[6], const cplx<T> o[15], c
             y[j] = cfmac(o[k], x[i], y[j]);  // B[j][i] = conj(B[i][j])
             k++;
         }
+    }
+}
+
+// double-float: each output component as two lazy sums of 11 products
+template <>
+__device__ __forceinline__ void herm6_apply<df>(const df d[6], const cplx<df> o[15], const cplx<df> x[6],
+                                                cplx<df> y[6]) {
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        dfsum re = dfs_prod(d[i], x[i].re), im = dfs_prod(d[i], x[i].im);
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+            if (j == i) continue;
+            // packed upper triangle: entry (r, s), r < s, at r (11 - r) / 2 + s - r - 1
+            const int r = i < j ? i : j, q = i < j ? j : i;
+            const cplx<df> b = o[r * (11 - r) / 2 + q - r - 1];
+            const df bim = (i < j) ? b.im : -b.im;  // B[i][j] = conj(B[j][i]) below the diagonal
+            dfs_add_prod(re, b.re, x[j].re);
+            dfs_add_prod(re, -bim, x[j].im);
+            dfs_add_prod(im, b.re, x[j].im);
+            dfs_add_prod(im, bim, x[j].re);
+        }
+        y[i] = {dfs_done(re), dfs_done(im)};
     }
 }
 
