@@ -367,7 +367,7 @@ def _timed(torch, fn):
     return r, (time.perf_counter() - t0) * 1e3
 
 
-def batched_extras(torch, bqcd):
+def batched_extras(torch, bqcd, fp64_arith):
     """12 point sources and 10 RHMC shifts on 24^3x48, and a ragged set of four
     lattices: one batched solve against the same systems solved one at a time
     (mixed precision, FP32 inner, to a true FP64 residual 1e-10)."""
@@ -379,6 +379,7 @@ def batched_extras(torch, bqcd):
     lat = bqcd.Lattice(wl["dims"], wl["kappa"], wl["csw"], wl["mu"], -1.0)
     bqcd.bq_set_gauge(lat.ctx, synth.gauge_field(wl["dims"], wl["eps"], wl["seed"]))
     bqcd.bq_set_recon(lat.ctx, "single", 12)
+    bqcd.bq_set_fp64_arith(lat.ctx, fp64_arith)
     srcs = [torch.from_numpy(synth.point_source(lat.Vh, 0, s, c)).cuda() for s in range(4) for c in range(3)]
     xs = [torch.empty_like(b) for b in srcs]
     bqcd.bq_solve_cg_batch([lat.ctx] * 12, xs, srcs, **kw)  # warm
@@ -419,6 +420,7 @@ def batched_extras(torch, bqcd):
         l = bqcd.Lattice(dims, 0.1350, 1.7, 0.0, -1.0)
         bqcd.bq_set_gauge(l.ctx, synth.gauge_field(dims, 0.2, 1 + i))
         bqcd.bq_set_recon(l.ctx, "single", 12)
+        bqcd.bq_set_fp64_arith(l.ctx, fp64_arith)
         lats.append(l)
         bs.append(torch.from_numpy(synth.gaussian_spinor(l.Vh, 900 + i)).cuda())
         xr.append(torch.empty_like(bs[-1]))
@@ -433,7 +435,7 @@ def batched_extras(torch, bqcd):
     return out
 
 
-def full_system_extras(torch, bqcd):
+def full_system_extras(torch, bqcd, fp64_arith):
     """M x = b on the whole 24^3x48 lattice with chemical potential mu = 0.1
     (Mhat not gamma_5-hermitian): BiCGstab on Mhat against CG on Mhat^dag Mhat,
     both mixed (FP32 inner, FP64 outer) and BiCGstab in plain FP64, to a true
@@ -446,6 +448,7 @@ def full_system_extras(torch, bqcd):
     lat = bqcd.Lattice(wl["dims"], 0.12, wl["csw"], 0.1, -1.0)
     bqcd.bq_set_gauge(lat.ctx, synth.gauge_field(wl["dims"], wl["eps"], wl["seed"]))
     bqcd.bq_set_recon(lat.ctx, "single", 12)
+    bqcd.bq_set_fp64_arith(lat.ctx, fp64_arith)
     b_e = torch.from_numpy(synth.gaussian_spinor(lat.Vh, 601)).cuda()
     b_o = torch.from_numpy(synth.gaussian_spinor(lat.Vh, 602)).cuda()
     x_e, x_o = torch.empty_like(b_e), torch.empty_like(b_o)
@@ -532,6 +535,7 @@ def make_step(args, torch, bqcd, synth, lat, b_dev, x_dev, solve_kw, field_input
         bqcd.bq_set_gauge(l.ctx, synth.gauge_field(dims, 0.2, 1 + i))
         bqcd.bq_set_recon(l.ctx, "single", 12)
         bqcd.bq_set_recon(l.ctx, "half", 12)
+        bqcd.bq_set_fp64_arith(l.ctx, args.fp64_arith)
         lats.append(l)
         bs.append(torch.from_numpy(synth.gaussian_spinor(l.Vh, 900 + i)).cuda())
         xr.append(torch.empty_like(bs[-1]))
@@ -635,8 +639,8 @@ def extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, mixed_ms, torch, bqcd):
                           "clover_logdet_odd_ms": ms_ld, "clover_logdet_odd": ld, "negative_blocks": neg}
 
     # ---- batching (row a9) and multishift (row a8), each against the same work done one system at a time
-    out["batched"] = batched_extras(torch, bqcd)
-    out.update(full_system_extras(torch, bqcd))
+    out["batched"] = batched_extras(torch, bqcd, args.fp64_arith)
+    out.update(full_system_extras(torch, bqcd, args.fp64_arith))
 
     # ---- CPU oracle on the host cores (bounded sample: 2 Mhat^dag Mhat applies)
     import oracle

@@ -150,6 +150,15 @@ int bq_set_u1(bq_ctx *ctx, const double *A, int where);
  * BQ_ERR_CLOVER_SINGULAR if a block has no inverse. */
 int bq_build_clover(bq_ctx *ctx);
 
+/* How batched solves whose first context is ctx lay right-hand sides of one
+ * lattice onto threads in the hopping-term launches (Section 3, block solvers):
+ * 0 = autotuned on the first solve of each batch shape (default), -1 =
+ * consecutive blocks take the right-hand sides of the same sites in turn,
+ * -2 = 32 sites per block with one right-hand side per warp, R = 1..8 = the
+ * R right-hand sides of a site in adjacent threads of one warp. Results agree
+ * to rounding whatever the mapping. Other values: BQ_ERR_ARG. */
+int bq_set_batch_mapping(bq_ctx *ctx, int mapping);
+
 /* Stout smearing of the hopping term's links (Section 2, QCD+QED: the
  * fermion action of Eq. 5 hops with singly iterated stout links; Morningstar
  * and Peardon, Phys. Rev. D 69 (2004) 054501). With n_iter > 0 and rho > 0

@@ -114,6 +114,7 @@ _SIGS = {
                                                     ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
                                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(bq_solver_params),
                                                     ctypes.POINTER(bq_solver_stats), ctypes.POINTER(ctypes.c_double)]),
+    "bq_set_batch_mapping": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "bq_set_stout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]),
     "bq_get_hop_links": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "bq_clover_logdet": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -376,6 +377,11 @@ def bq_solve_multishift_cg_block(ctx, xs, bs, shifts, tol=1e-10, max_iter=20000,
     for r in range(nrhs):
         out[r]["residuals"] = [res[r * n + k] for k in range(n)]
     return out
+
+
+def bq_set_batch_mapping(ctx, mapping):
+    """0 autotuned, -1 block-interleaved, -2 one rhs per warp, 1..8 rhs interleaved in a warp."""
+    _check(_lib_handle().bq_set_batch_mapping(ctx, int(mapping)), "bq_set_batch_mapping")
 
 
 def bq_set_stout(ctx, rho, n_iter=1):

@@ -465,8 +465,8 @@ static int log2_ceil(int n) {
 }
 
 // steps 0-3 sloppy (prec ps), 4-7 FP64: D_oe+A^-1, A x - k D_eo, and the two adjoint ones
-// mapping < 0: block-interleaved units of up to DSLASH_UNIT_RHS rhs; mapping > 0:
-// warp-interleaved units of `mapping` rhs
+// mapping -1: block-interleaved units of up to DSLASH_UNIT_RHS rhs; -2: warp-per-rhs
+// units of up to DSLASH_UNIT_RHS rhs; mapping > 0: warp-interleaved units of `mapping` rhs
 static int build_units(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int mapping, UnitPlan *plan) {
     const int rhs_per_unit = mapping < 0 ? DSLASH_UNIT_RHS : mapping;
     BatchWork *w = c0->batch;
@@ -495,7 +495,7 @@ static int build_units(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int ma
             BQ_TRY(bq_dslash_unit_fill(c, prec, parity, dagger, epi, kk, &u->a));
             u->nr = e - s;
             u->log2R = log2_ceil(u->nr);
-            u->interleave = mapping < 0 ? 1 : 0;
+            u->interleave = mapping == -1 ? 1 : mapping == -2 ? 2 : 0;
             for (int q = 0; q < u->nr; q++) {
                 BatchSlot *sl = &w->slot[s + q];
                 void *pv[8][3] = {{sl->p, sl->to_s, nullptr},  {sl->to_s, sl->te_s, sl->p},
@@ -507,8 +507,9 @@ static int build_units(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int ma
                 u->xin[q] = pv[step][2];
                 u->sys[q] = s + q;
             }
-            const int blocks = u->interleave ? ((c->Vh + 127) / 128) * u->nr
-                                             : (int)(((long long)c->Vh * (1 << u->log2R) + 127) / 128);
+            const int blocks = u->interleave == 1   ? ((c->Vh + 127) / 128) * u->nr
+                               : u->interleave == 2 ? ((c->Vh + 31) / 32) * ((u->nr + 3) / 4)
+                                                    : (int)(((long long)c->Vh * (1 << u->log2R) + 127) / 128);
             tab.block0[tab.nunits + 1] = tab.block0[tab.nunits] + blocks;
             tab.nunits++;
             // links and clover once per site of the unit, spinors per rhs
@@ -550,8 +551,8 @@ static int mdagm_batch(bq_ctx *c0, int prec, int recon, int first_step, const Un
 }
 
 // Autotuner of the batched hopping term: times one sloppy Mhat^dag Mhat of the
-// batch (after one warm-up) for each rhs mapping -- block-interleaved units and
-// warp-interleaved units of 2, 4 and 8 -- and keeps the fastest for this batch
+// batch (after one warm-up) for each rhs mapping -- block-interleaved units,
+// warp-per-rhs units and warp-interleaved units of 2, 4 and 8 -- and keeps the fastest for this batch
 // (same contexts, same number of systems, same precision) on later calls; the
 // last few batch signatures are remembered.
 static int tune_mapping(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int *mapping) {
@@ -568,9 +569,9 @@ static int tune_mapping(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int *
             *mapping = w->tuned_mapping[e];
             return BQ_OK;
         }
-    int cand[4] = {-1, 2, 4, 8};
-    int ncand = 1;
-    for (int k = 1; k < 4; k++)
+    int cand[5] = {-1, -2, 2, 4, 8};
+    int ncand = 2;
+    for (int k = 2; k < 5; k++)
         if (cand[k] <= maxrun) cand[ncand++] = cand[k];
     double *h_on = w->h_flags;
     for (int i = 0; i < nsys; i++) h_on[i] = 1.0;
@@ -702,7 +703,7 @@ static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double 
         hscal[(size_t)i * S_NSCAL + S_SIGMA] = shifts ? shifts[i] : sp->shift;
     }
     UnitPlan plan;
-    int mapping = rhs_per_unit;
+    int mapping = rhs_per_unit ? rhs_per_unit : c0->batch_mapping;
     if (nsys > 1 && mapping == 0) BQ_TRY(tune_mapping(c0, nsys, ctxs, PS, &mapping));
     BQ_TRY(build_units(c0, nsys, ctxs, PS, mapping, &plan));
     BQ_CUDA_TRY(cudaMemcpyAsync(w->d_sys, hs.data(), sizeof(SysVec) * nsys, cudaMemcpyHostToDevice, s));
@@ -1099,8 +1100,8 @@ static int ms_block_run(bq_ctx *c0, int nrhs, int n, const double *shifts, int b
         m[M_NACTIVE] = n;
     }
     UnitPlan plan;
-    int mapping = -1;
-    if (nrhs > 1) BQ_TRY(tune_mapping(c0, nrhs, ctxs.data(), PS, &mapping));
+    int mapping = c0->batch_mapping ? c0->batch_mapping : -1;
+    if (nrhs > 1 && c0->batch_mapping == 0) BQ_TRY(tune_mapping(c0, nrhs, ctxs.data(), PS, &mapping));
     BQ_TRY(build_units(c0, nrhs, ctxs.data(), PS, mapping, &plan));
     BQ_CUDA_TRY(cudaMemcpyAsync(w->d_sys, hs.data(), sizeof(SysVec) * nrhs, cudaMemcpyHostToDevice, s));
     BQ_CUDA_TRY(cudaMemcpyAsync(w->d_scal, hscal.data(), sizeof(double) * S_NSCAL * nrhs, cudaMemcpyHostToDevice, s));
@@ -1269,5 +1270,14 @@ extern "C" int bq_solve_multishift_cg_block(bq_ctx *c, int nrhs, double *const *
         bq_set_error("block multishift refinement reached max_iter");
         return BQ_ERR_NOT_CONVERGED;
     }
+    return BQ_OK;
+}
+
+extern "C" int bq_set_batch_mapping(bq_ctx *c, int mapping) {
+    if (!c || !(mapping == 0 || mapping == -1 || mapping == -2 || (mapping >= 1 && mapping <= DSLASH_UNIT_RHS))) {
+        bq_set_error("bq_set_batch_mapping: mapping must be 0, -1, -2 or 1..%d", DSLASH_UNIT_RHS);
+        return BQ_ERR_ARG;
+    }
+    c->batch_mapping = mapping;
     return BQ_OK;
 }

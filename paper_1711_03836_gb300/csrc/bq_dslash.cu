@@ -428,9 +428,12 @@ __global__ void __launch_bounds__(128, DslashMinBlocks<PREC>::value) k_dslash(co
 }
 
 // Batched launch: the grid is cut into units (one lattice, up to DSLASH_UNIT_RHS
-// right-hand sides); inside a unit thread t serves site t / R of rhs t % R, so
-// the R threads of one site sit in the same warp and one link load serves all
-// R right-hand sides. mask[sys] == 0 skips a system (converged, or not due
+// right-hand sides). Three mappings of a unit: warp-interleaved (thread t serves
+// site t / R of rhs t % R, the R threads of one site in the same warp share
+// each link load), block-interleaved (consecutive blocks take the rhs of the
+// same sites in turn, links re-read from L2) and warp-per-rhs (a block covers
+// 32 sites, each warp one rhs: spinor loads coalesce as in a single solve and
+// the block's four warps share the links in L1). mask[sys] == 0 skips a system (converged, or not due
 // for an update).
 #ifndef BATCH_MIN_BLOCKS
 #define BATCH_MIN_BLOCKS 5
@@ -451,9 +454,13 @@ __global__ void __launch_bounds__(128, BatchMinBlocks<PREC>::value) k_dslash_bat
     const DslashUnit &U = tab.units[u];
     const int bl = (int)blockIdx.x - tab.block0[u];
     int r, h;
-    if (U.interleave) {  // block bl: rhs bl % nr, sites of block bl / nr (neighbours in time share the links in L2)
+    if (U.interleave == 1) {  // block bl: rhs bl % nr, sites of block bl / nr (neighbours in time share the links in L2)
         r = bl % U.nr;
         h = (bl / U.nr) * blockDim.x + threadIdx.x;
+    } else if (U.interleave == 2) {  // block: 32 sites, warp w takes rhs 4 g + w (the four warps share links in L1)
+        const int ng = (U.nr + 3) >> 2;
+        r = (bl % ng) * 4 + (int)(threadIdx.x >> 5);
+        h = (bl / ng) * 32 + (int)(threadIdx.x & 31);
     } else {  // rhs t % R of site t / R: the R threads of a site share link loads inside the warp
         const int lr = U.log2R;
         const int t = bl * blockDim.x + threadIdx.x;

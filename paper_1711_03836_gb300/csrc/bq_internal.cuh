@@ -717,6 +717,7 @@ struct bq_ctx {
     int capturing;   // the library stream is being captured into a graph
     cudaStream_t cap_stream;  // private stream used for graph capture
     int use_graphs;           // capture the solver iteration as a CUDA graph
+    int batch_mapping;        // rhs mapping of batched hopping-term launches (0: autotuned)
     int counter_gen;          // bumped by bq_reset_counters: cached graphs re-captured
 };
 
@@ -767,7 +768,8 @@ struct DslashUnit {
     int sys[DSLASH_UNIT_RHS];  // mask index of each rhs
     int nr;                    // right-hand sides in use
     int log2R;                 // warp-interleaved: threads per site = 1 << log2R >= nr
-    int interleave;            // 0: rhs interleaved inside a warp; 1: consecutive blocks take the rhs in turn
+    int interleave;            // 0: rhs interleaved inside a warp; 1: consecutive blocks take the rhs in turn;
+                               // 2: 32 sites per block, one rhs per warp
 };
 
 // a batched launch passes its units by value (kernel parameter space, read

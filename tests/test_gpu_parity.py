@@ -660,3 +660,32 @@ def test_trace_samples(bq, prec, mu, charge):
             # a solve to 1e-10 moves eta^dag x by at most cond(M) 1e-10 |eta|^2
             assert abs(got[n, k] - ref[k]) <= 1e-7 * abs(ref[k]) + 1e-8 * eta2, (n, k, got[n, k], ref[k])
     lat.close()
+
+
+@pytest.mark.parametrize("mapping", [-1, -2, 1, 2, 4, 8])
+@pytest.mark.parametrize("prec", ["single", "half"])
+def test_batched_rhs_mappings(bq, mapping, prec):
+    """Every mapping of right-hand sides onto threads (forced, not autotuned):
+    five Gaussian sources (a ragged last group for every mapping) against the oracle."""
+    dims = (6, 4, 6, 10)
+    lat, U, A, p = make(bq, dims, kappa=0.1350, csw=1.7, eps=0.2, mu=0.1, recon=12, precision=prec)
+    bq.bq_set_batch_mapping(lat.ctx, mapping)
+    op = oracle.Operator(p, U)
+    bs = [synth.gaussian_spinor(lat.Vh, 300 + i) for i in range(5)]
+    xs = [np.empty_like(b) for b in bs]
+    stats = bq.bq_solve_cg_batch([lat.ctx] * 5, xs, bs, tol=1e-10, precision=prec,
+                                 delta=1e-3 if prec == "single" else 1e-1)
+    for b, x, st in zip(bs, xs, stats):
+        res = np.linalg.norm(op.mdagm(x) - b) / np.linalg.norm(b)
+        assert st["converged"] and res <= 1e-10, res
+    # block multishift with the same forced mapping
+    shifts = [0.01, 0.5]
+    xm = [[np.empty_like(bs[0]) for _ in shifts] for _ in bs[:3]]
+    bq.bq_solve_multishift_cg_block(lat.ctx, xm, bs[:3], shifts, tol=1e-10, precision=prec,
+                                    delta=1e-3 if prec == "single" else 1e-1)
+    for r in range(3):
+        for k, sh in enumerate(shifts):
+            assert np.linalg.norm(op.mdagm(xm[r][k], sh) - bs[r]) / np.linalg.norm(bs[r]) <= 1e-10
+    with pytest.raises(bq.BqError):
+        bq.bq_set_batch_mapping(lat.ctx, 3 * 4)
+    lat.close()
