@@ -689,3 +689,51 @@ def test_batched_rhs_mappings(bq, mapping, prec):
     with pytest.raises(bq.BqError):
         bq.bq_set_batch_mapping(lat.ctx, 3 * 4)
     lat.close()
+
+
+def test_next_rows_error_codes(bq):
+    """Argument and state errors of the full-system, block multishift, stout,
+    log det and trace entry points come back as status codes."""
+    import ctypes
+
+    lat = bq.Lattice((4, 4, 4, 4), 0.12, 1.0)
+    z = np.zeros((lat.Vh, 4, 3), np.complex128)
+    x_e, x_o = np.empty_like(z), np.empty_like(z)
+    lib = bq._lib_handle()
+    for call in (lambda: bq.bq_solve_full(lat.ctx, x_e, x_o, z, z),
+                 lambda: bq.bq_clover_logdet(lat.ctx, 0),
+                 lambda: bq.bq_get_hop_links(lat.ctx, np.empty((2 * lat.Vh, 4, 3, 3), np.complex128)),
+                 lambda: bq.bq_trace_samples(lat.ctx, [z], [z])):
+        with pytest.raises(bq.BqError) as e:
+            call()
+        assert e.value.status == bq.BQ_ERR_STATE
+    bq.bq_set_gauge(lat.ctx, synth.gauge_field((4, 4, 4, 4), 0.2, 3))
+    for bad in ((-0.1, 1), (1.5, 1), (0.1, -1), (0.1, 65)):
+        with pytest.raises(bq.BqError) as e:
+            bq.bq_set_stout(lat.ctx, *bad)
+        assert e.value.status == bq.BQ_ERR_ARG
+    with pytest.raises(bq.BqError) as e:
+        bq.bq_clover_logdet(lat.ctx, 2)
+    assert e.value.status == bq.BQ_ERR_ARG
+    sp = bq.bq_solver_params(1e-10, 100, 0, 1e-3, 8, 0.0)
+    st = bq.bq_solver_stats()
+    p = z.ctypes.data
+    assert lib.bq_solve_full(lat.ctx, p, p, p, p, 0, 7, 0, ctypes.byref(sp), ctypes.byref(st)) == bq.BQ_ERR_ARG
+    assert lib.bq_solve_full(lat.ctx, p, p, p, p, 0, 0, 2, ctypes.byref(sp), ctypes.byref(st)) == bq.BQ_ERR_ARG
+    assert lib.bq_solve_full(lat.ctx, None, p, p, p, 0, 0, 0, ctypes.byref(sp), ctypes.byref(st)) == bq.BQ_ERR_ARG
+    sp_shift = bq.bq_solver_params(1e-10, 100, 0, 1e-3, 8, 0.5)
+    assert lib.bq_solve_full(lat.ctx, p, p, p, p, 0, 0, 0, ctypes.byref(sp_shift), ctypes.byref(st)) == bq.BQ_ERR_ARG
+    arr = (ctypes.c_void_p * 1)(p)
+    out = (ctypes.c_double * 5)()
+    assert lib.bq_trace_samples(lat.ctx, 0, arr, arr, 0, ctypes.byref(sp), out, None) == bq.BQ_ERR_ARG
+    sh = (ctypes.c_double * 33)(*([0.1] * 33))
+    xs = (ctypes.c_void_p * 33)(*([p] * 33))
+    assert lib.bq_solve_multishift_cg_block(lat.ctx, 1, xs, arr, 0, 33, sh, ctypes.byref(sp), None,
+                                            None) == bq.BQ_ERR_ARG
+    sh[0] = -1.0
+    assert lib.bq_solve_multishift_cg_block(lat.ctx, 1, xs, arr, 0, 2, sh, ctypes.byref(sp), None,
+                                            None) == bq.BQ_ERR_ARG
+    assert lib.bq_solve_multishift_cg_block(lat.ctx, 0, xs, arr, 0, 2, sh, ctypes.byref(sp), None,
+                                            None) == bq.BQ_ERR_ARG
+    assert b"bq_solve_multishift_cg_block" in lib.bq_last_error()
+    lat.close()
