@@ -138,6 +138,15 @@ def test_trace_samples_sum_to_dense_traces(mu_chem, charge):
     assert abs(tot[1] - np.trace(G5 @ Mi)) < 1e-9 * np.abs(Mi).sum()
     sv = np.linalg.svd(M, compute_uv=False)
     assert abs(tot[2] - np.sum(sv ** -2.0)) < 1e-9 * np.sum(sv ** -2.0)
+    # one Z2 noise vector, sample by sample: eta^dag M^-1 eta, eta^dag g5 M^-1 eta and
+    # eta^dag (M^dag M)^-1 eta (not (M M^dag)^-1, which has the same trace)
+    eta_e, eta_o = synth.z2_noise(Vh, 41), synth.z2_noise(Vh, 42)
+    eta = np.concatenate([eta_e.ravel(), eta_o.ravel()])
+    got = op.trace_samples(eta_e, eta_o, tol=1e-13)
+    expect = [np.vdot(eta, Mi @ eta), np.vdot(eta, G5 @ Mi @ eta), np.vdot(eta, np.linalg.solve(M.conj().T @ M, eta))]
+    for g, e in zip(got, expect):
+        assert abs(g - e) < 1e-8 * abs(expect[2])
+    assert abs(np.vdot(eta, np.linalg.solve(M @ M.conj().T, eta)) - expect[2]) > 1e-6 * abs(expect[2])
 
 
 def test_z2_noise_moments():
