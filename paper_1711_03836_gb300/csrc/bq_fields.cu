@@ -113,12 +113,14 @@ extern "C" int bq_create(bq_ctx **out, const int dims[4], void *stream) {
 }
 
 void bq_solver_free(bq_ctx *c);  // bq_solvers.cu
+void bq_full_free(bq_ctx *c);    // bq_full.cu
 
 extern "C" int bq_destroy(bq_ctx *c) {
     if (!c) return BQ_OK;
     cudaStreamSynchronize(c->stream);
     bq_solver_free(c);
     bq_batch_free(c);
+    bq_full_free(c);
     cudaFree(c->U_canon);
     cudaFree(c->U_hop);
     cudaFree(c->A_u1);
@@ -367,7 +369,8 @@ __global__ void k_build_clover(double2 *master, size_t pblk, const double2 *U, G
     }
 }
 
-// inverse of each 6x6 block (Gauss-Jordan with partial pivoting, FP64)
+// inverse of each 6x6 block (Gauss-Jordan with partial pivoting, FP64); a block
+// whose pivot falls below 1e-13 of its largest entry is reported as singular
 __global__ void k_invert_clover(double2 *master, size_t pblk, int Vh, int *flag) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 4 * Vh) return;
@@ -379,6 +382,9 @@ __global__ void k_invert_clover(double2 *master, size_t pblk, int Vh, int *flag)
     cplx<double> a[6][12];
     cplx<double> B[36];
     load_herm6(src, b, h, Vh, B);
+    // numerically singular: a pivot below 1e-13 of the block's largest entry
+    double scale = 0.0;
+    for (int k = 0; k < 36; k++) scale = fmax(scale, hypot(B[k].re, B[k].im));
     for (int i = 0; i < 6; i++)
         for (int j = 0; j < 6; j++) {
             a[i][j] = B[i * 6 + j];
@@ -394,7 +400,7 @@ __global__ void k_invert_clover(double2 *master, size_t pblk, int Vh, int *flag)
                 piv = r;
             }
         }
-        if (!(best > 1e-300)) {
+        if (!(best > 1e-13 * scale)) {
             atomicExch(flag, 1);
             return;
         }

@@ -17,6 +17,9 @@
 #include <string.h>
 
 #include <complex>
+#include <mutex>
+#include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "bq_reduce.cuh"
@@ -90,11 +93,19 @@ int bq_dot_launch(bq_ctx *c, const void *a, const void *b, int prec, double *par
 
 namespace {
 
-// FP64 vectors of the reduction and reconstruction, inner-precision vectors of BiCGstab
+// FP64 vectors of the reduction and reconstruction, inner-precision vectors of
+// BiCGstab, and the FP64 vectors of the trace samples; kept per context between
+// calls (no allocation inside repeated solves)
 struct FullWork {
     char *be, *bo, *xe, *xo, *bh, *r, *to, *te, *ye;
     char *ib, *ix, *ir, *ir0, *ip, *iv, *is, *it, *itmp;
+    int pin;  // precision of the inner vectors
+    cudaEvent_t e0, e1;
+    std::vector<char *> trace;
 };
+
+std::mutex g_full_lock;
+std::unordered_map<bq_ctx *, FullWork *> g_full;
 
 int grid_of(const bq_ctx *c) {
     int g = (c->Vh + 255) / 256;
@@ -234,20 +245,37 @@ int bicgstab(bq_ctx *c, int prec, int dag, const Bicg &w, double tol_abs, int ma
     return BQ_OK;
 }
 
-int alloc_full(bq_ctx *c, FullWork *w, int pin) {
+// the context's work vectors, inner vectors at precision pin
+int full_work(bq_ctx *c, int pin, FullWork **out) {
+    FullWork *w;
+    {
+        std::lock_guard<std::mutex> g(g_full_lock);
+        FullWork *&slot = g_full[c];
+        if (!slot) {
+            slot = new (std::nothrow) FullWork();
+            if (!slot) return BQ_ERR_NOMEM;
+            slot->pin = -1;
+        }
+        w = slot;
+    }
+    if (!w->e0) BQ_CUDA_TRY(cudaEventCreate(&w->e0));
+    if (!w->e1) BQ_CUDA_TRY(cudaEventCreate(&w->e1));
+    char **din[] = {&w->ib, &w->ix, &w->ir, &w->ir0, &w->ip, &w->iv, &w->is, &w->it, &w->itmp};
+    if (w->pin != pin) {
+        cudaStreamSynchronize(c->stream);
+        for (auto p : din) {
+            cudaFree(*p);
+            *p = nullptr;
+        }
+        w->pin = pin;
+    }
     const size_t b64 = spinor_bytes_per_site(BQ_PREC_DOUBLE) * (size_t)c->Vh;
     const size_t bin = spinor_bytes_per_site(pin) * (size_t)c->Vh;
     char **d64[] = {&w->be, &w->bo, &w->xe, &w->xo, &w->bh, &w->r, &w->to, &w->te, &w->ye};
     for (auto p : d64) BQ_TRY(bq_alloc((void **)p, b64));
-    char **din[] = {&w->ib, &w->ix, &w->ir, &w->ir0, &w->ip, &w->iv, &w->is, &w->it, &w->itmp};
     for (auto p : din) BQ_TRY(bq_alloc((void **)p, bin));
+    *out = w;
     return BQ_OK;
-}
-
-void free_full(FullWork *w) {
-    char *ptrs[] = {w->be, w->bo, w->xe, w->xo, w->bh, w->r,  w->to, w->te, w->ye,
-                    w->ib, w->ix, w->ir, w->ir0, w->ip, w->iv, w->is, w->it, w->itmp};
-    for (auto p : ptrs) cudaFree(p);
 }
 
 // Mhat x_e = bhat by BiCGstab: FP64, or FP64 defect correction around a lower-precision BiCGstab
@@ -353,14 +381,11 @@ extern "C" int bq_solve_full(bq_ctx *c, double *x_e, double *x_o, const double *
     bq_solver_stats local;
     if (!st) st = &local;
     memset(st, 0, sizeof *st);
-    FullWork w;
-    memset(&w, 0, sizeof w);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    int status = alloc_full(c, &w, pin);
-    if (status == BQ_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
-        bq_set_error("bq_solve_full: event creation failed");
-        status = BQ_ERR_CUDA;
-    }
+    FullWork *wp = nullptr;
+    int status = full_work(c, pin, &wp);
+    if (status != BQ_OK) return status;
+    FullWork &w = *wp;
+    cudaEvent_t e0 = w.e0, e1 = w.e1;
     const double kappa = c->params.kappa;
     const int dag = dagger;
     const zc one(1, 0), zero(0, 0);
@@ -410,11 +435,8 @@ extern "C" int bq_solve_full(bq_ctx *c, double *x_e, double *x_o, const double *
         st->seconds = ms * 1e-3;
         return BQ_OK;
     };
-    if (status == BQ_OK) status = run();
+    status = run();
     cudaStreamSynchronize(c->stream);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    free_full(&w);
     if (status == BQ_OK && !st->converged) {
         bq_set_error("full-system solve: true residual %.3e above tol", st->true_residual);
         return BQ_ERR_NOT_CONVERGED;
@@ -510,15 +532,21 @@ extern "C" int bq_trace_samples(bq_ctx *c, int nnoise, const double *const *eta_
     const int pr = (pin == BQ_PREC_HALF) ? BQ_PREC_SINGLE : pin;
     BQ_TRY(bq_batch_reserve(c, nsys, ctxs.data(), pin, pr));
     const size_t b64 = spinor_bytes_per_site(BQ_PREC_DOUBLE) * (size_t)c->Vh;
+    FullWork *wp = nullptr;
+    BQ_TRY(full_work(c, pin, &wp));
+    std::vector<char *> &pool = wp->trace;  // FP64 vectors, kept for later calls
+    size_t used = 0;
     std::vector<TraceSys> sy(nsys);
-    std::vector<char *> owned;
     char *to = nullptr, *te = nullptr, *ye = nullptr;
     int status = BQ_OK;
     auto alloc = [&](char **p) -> int {
-        *p = nullptr;
-        int r = bq_alloc((void **)p, b64);
-        if (r == BQ_OK) owned.push_back(*p);
-        return r;
+        if (used == pool.size()) {
+            char *q = nullptr;
+            BQ_TRY(bq_alloc((void **)&q, b64));
+            pool.push_back(q);
+        }
+        *p = pool[used++];
+        return BQ_OK;
     };
     const double kappa = c->params.kappa;
     const zc one(1, 0), zero(0, 0), mone(-1, 0);
@@ -649,6 +677,24 @@ extern "C" int bq_trace_samples(bq_ctx *c, int nnoise, const double *const *eta_
     };
     status = run();
     cudaStreamSynchronize(c->stream);
-    for (char *p : owned) cudaFree(p);
     return status;
+}
+
+// the context's full-system and trace work vectors (called by bq_destroy)
+void bq_full_free(bq_ctx *c) {
+    FullWork *w = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_full_lock);
+        auto it = g_full.find(c);
+        if (it == g_full.end()) return;
+        w = it->second;
+        g_full.erase(it);
+    }
+    char *ptrs[] = {w->be, w->bo, w->xe, w->xo, w->bh, w->r,  w->to, w->te, w->ye,
+                    w->ib, w->ix, w->ir, w->ir0, w->ip, w->iv, w->is, w->it, w->itmp};
+    for (auto p : ptrs) cudaFree(p);
+    for (char *p : w->trace) cudaFree(p);
+    if (w->e0) cudaEventDestroy(w->e0);
+    if (w->e1) cudaEventDestroy(w->e1);
+    delete w;
 }

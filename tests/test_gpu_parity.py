@@ -737,3 +737,40 @@ def test_next_rows_error_codes(bq):
                                             None) == bq.BQ_ERR_ARG
     assert b"bq_solve_multishift_cg_block" in lib.bq_last_error()
     lat.close()
+
+
+def test_failure_detection_singular_clover_and_nan_source(bq):
+    """Faults made on the host, reported as status codes, the context usable after:
+    a clover block made singular on purpose (constant abelian field with
+    kappa c_SW f_a = 1, so det A = prod (1 - (kappa c_SW f_a)^2)^2 = 0) and a NaN in
+    the source of a solve."""
+    from helpers import abelian_background
+
+    dims = (4, 6, 4, 8)
+    c = (1.0, 2.0, 0.0)
+    U, phi = abelian_background(dims, 0, 1, 1, c, "mu")
+    f = np.sin(phi * np.array(c))
+    f -= f.mean()
+    kappa = 0.13
+    csw = 1.0 / (kappa * np.abs(f).max())
+    lat = bq.Lattice(dims, kappa, csw, 0.0, -1.0)
+    bq.bq_set_gauge(lat.ctx, U)
+    psi = synth.gaussian_spinor(lat.Vh, 3)
+    out = lat.spinor("double")
+    with pytest.raises(bq.BqError) as e:
+        bq.bq_apply_mhat(lat.ctx, out, lat.pack(psi), 0, "double")
+    assert e.value.status == bq.BQ_ERR_CLOVER_SINGULAR
+    lat.close()
+    # NaN source: the solve stops with BQ_ERR_NOT_CONVERGED; the next solve works
+    lat, U, A, p = make(bq, (4, 4, 4, 6), kappa=0.12, csw=1.0)
+    b = synth.gaussian_spinor(lat.Vh, 4)
+    bad = b.copy()
+    bad[3, 1, 2] = np.nan
+    x = np.empty_like(b)
+    with pytest.raises(bq.BqError) as e:
+        bq.bq_solve_cg(lat.ctx, x, bad, tol=1e-10, precision="single")
+    assert e.value.status == bq.BQ_ERR_NOT_CONVERGED
+    st = bq.bq_solve_cg(lat.ctx, x, b, tol=1e-10, precision="single")
+    op = oracle.Operator(p, U)
+    assert st["converged"] and np.linalg.norm(op.mdagm(x) - b) / np.linalg.norm(b) <= 1e-10
+    lat.close()
