@@ -88,6 +88,241 @@ __global__ void __launch_bounds__(256) k_add_to_double(void *x, const void *d, i
     }
 }
 
+// --------------------------------------------------------------------------
+// BiCGstab with device-resident scalars (complex as re, im pairs)
+
+enum {
+    BI_RHO = 0,    // rho = <r0, r> of the current step (2)
+    BI_ALPHA = 2,  // alpha (2)
+    BI_OMEGA = 4,  // omega (2)
+    BI_BETA = 6,   // beta of the next direction update (2)
+    BI_RR = 8,     // |r|^2
+    BI_R0N = 9,    // |r0|^2
+    BI_RESTART = 10,  // 1: the next direction update restarts with r0 = r
+    BI_BREAK = 11,    // 1: <r0, v> or <t, t> vanished
+    BI_TOL2 = 12,     // stopping threshold on |r|^2
+    BI_DONE = 13,     // 1: |r|^2 <= BI_TOL2; every later kernel leaves the vectors alone
+    BI_ITERS = 14,    // iterations completed
+    BI_N = 16
+};
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+    const double n = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / n, (a.y * b.x - a.x * b.y) / n);
+}
+
+// x = 0, r = r0 = b, p = v = 0; |b|^2; rho = |b|^2, alpha = omega = 1, beta = 0
+template <int P>
+__global__ void __launch_bounds__(RED_THREADS) k_bi_init(const void *b, void *x, void *r, void *r0, void *p, void *v,
+                                                         double *partials, unsigned int *ticket, double *sc, int Vh,
+                                                         double tol2) {
+    using T = typename Traits<P>::real;
+    double acc[1] = {0.0};
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<T> bv[12], z[12];
+        SpinorIO<P>::load(bv, b, h, Vh);
+#pragma unroll
+        for (int k = 0; k < 12; k++) z[k] = {T(0), T(0)};
+        SpinorIO<P>::store(x, h, Vh, z);
+        SpinorIO<P>::store(p, h, Vh, z);
+        SpinorIO<P>::store(v, h, Vh, z);
+        SpinorIO<P>::store(r, h, Vh, bv);
+        SpinorIO<P>::store(r0, h, Vh, bv);
+        acc[0] += norm2_site(bv);
+    }
+    double tot[1];
+    if (grid_sum(acc, partials, ticket, tot) && threadIdx.x == 0) {
+        sc[BI_RHO] = tot[0];
+        sc[BI_RHO + 1] = 0.0;
+        sc[BI_ALPHA] = sc[BI_OMEGA] = 1.0;
+        sc[BI_ALPHA + 1] = sc[BI_OMEGA + 1] = 0.0;
+        sc[BI_BETA] = sc[BI_BETA + 1] = 0.0;
+        sc[BI_RR] = sc[BI_R0N] = tot[0];
+        sc[BI_RESTART] = sc[BI_BREAK] = 0.0;
+        sc[BI_TOL2] = tol2;
+        sc[BI_DONE] = (tot[0] <= tol2) ? 1.0 : 0.0;
+        sc[BI_ITERS] = 0.0;
+    }
+}
+
+// p = r + beta (p - omega v); on a restart p = r and r0 = r
+template <int P>
+__global__ void __launch_bounds__(RED_THREADS) k_bi_dir(void *p, const void *r, const void *v, void *r0,
+                                                        const double *sc, int Vh) {
+    using T = typename Traits<P>::real;
+    if (sc[BI_DONE] != 0.0) return;
+    const bool restart = sc[BI_RESTART] != 0.0;
+    const cplx<T> beta = {(T)sc[BI_BETA], (T)sc[BI_BETA + 1]};
+    const double2 bw = zmul(make_double2(sc[BI_BETA], sc[BI_BETA + 1]), make_double2(sc[BI_OMEGA], sc[BI_OMEGA + 1]));
+    const cplx<T> mbw = {(T)(-bw.x), (T)(-bw.y)};
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<T> rv[12];
+        SpinorIO<P>::load(rv, r, h, Vh);
+        if (restart) {
+            SpinorIO<P>::store(p, h, Vh, rv);
+            SpinorIO<P>::store(r0, h, Vh, rv);
+            continue;
+        }
+        cplx<T> pv[12], vv[12];
+        SpinorIO<P>::load(pv, p, h, Vh);
+        SpinorIO<P>::load(vv, v, h, Vh);
+#pragma unroll
+        for (int k = 0; k < 12; k++) pv[k] = cfma(mbw, vv[k], cfma(beta, pv[k], rv[k]));
+        SpinorIO<P>::store(p, h, Vh, pv);
+    }
+}
+
+// alpha = rho / <r0, v>
+template <int P>
+__global__ void __launch_bounds__(RED_THREADS) k_bi_alpha(const void *r0, const void *v, double *partials,
+                                                          unsigned int *ticket, double *sc, int Vh) {
+    using T = typename Traits<P>::real;
+    if (sc[BI_DONE] != 0.0) return;
+    double acc[2] = {0.0, 0.0};
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<T> a[12], b[12];
+        SpinorIO<P>::load(a, r0, h, Vh);
+        SpinorIO<P>::load(b, v, h, Vh);
+        T re = T(0), im = T(0);
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            re += a[k].re * b[k].re + a[k].im * b[k].im;
+            im += a[k].re * b[k].im - a[k].im * b[k].re;
+        }
+        acc[0] += (double)re;
+        acc[1] += (double)im;
+    }
+    double tot[2];
+    if (grid_sum(acc, partials, ticket, tot) && threadIdx.x == 0) {
+        if (tot[0] == 0.0 && tot[1] == 0.0) {
+            sc[BI_BREAK] = 1.0;
+            sc[BI_ALPHA] = sc[BI_ALPHA + 1] = 0.0;
+        } else {
+            const double2 al = zdiv(make_double2(sc[BI_RHO], sc[BI_RHO + 1]), make_double2(tot[0], tot[1]));
+            sc[BI_ALPHA] = al.x;
+            sc[BI_ALPHA + 1] = al.y;
+        }
+    }
+}
+
+// s = r - alpha v
+template <int P>
+__global__ void __launch_bounds__(RED_THREADS) k_bi_s(void *s, const void *r, const void *v, const double *sc, int Vh) {
+    using T = typename Traits<P>::real;
+    if (sc[BI_DONE] != 0.0) return;
+    const cplx<T> mal = {(T)(-sc[BI_ALPHA]), (T)(-sc[BI_ALPHA + 1])};
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<T> rv[12], vv[12];
+        SpinorIO<P>::load(rv, r, h, Vh);
+        SpinorIO<P>::load(vv, v, h, Vh);
+#pragma unroll
+        for (int k = 0; k < 12; k++) rv[k] = cfma(mal, vv[k], rv[k]);
+        SpinorIO<P>::store(s, h, Vh, rv);
+    }
+}
+
+// omega = <t, s> / <t, t>
+template <int P>
+__global__ void __launch_bounds__(RED_THREADS) k_bi_omega(const void *t, const void *s, double *partials,
+                                                          unsigned int *ticket, double *sc, int Vh) {
+    using T = typename Traits<P>::real;
+    if (sc[BI_DONE] != 0.0) return;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<T> tv[12], sv[12];
+        SpinorIO<P>::load(tv, t, h, Vh);
+        SpinorIO<P>::load(sv, s, h, Vh);
+        T re = T(0), im = T(0);
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            re += tv[k].re * sv[k].re + tv[k].im * sv[k].im;
+            im += tv[k].re * sv[k].im - tv[k].im * sv[k].re;
+        }
+        acc[0] += (double)re;
+        acc[1] += (double)im;
+        acc[2] += norm2_site(tv);
+    }
+    double tot[3];
+    if (grid_sum(acc, partials, ticket, tot) && threadIdx.x == 0) {
+        if (tot[2] > 0.0) {
+            sc[BI_OMEGA] = tot[0] / tot[2];
+            sc[BI_OMEGA + 1] = tot[1] / tot[2];
+        } else {
+            sc[BI_OMEGA] = sc[BI_OMEGA + 1] = 0.0;
+            sc[BI_BREAK] = 1.0;
+        }
+    }
+}
+
+// x += alpha p + omega s; r = s - omega t; then rho_new = <r0, r>, |r|^2, the
+// restart decision and beta = (rho_new / rho)(alpha / omega) for the next direction
+template <int P>
+__global__ void __launch_bounds__(RED_THREADS) k_bi_xr(void *x, void *r, const void *p, const void *s, const void *t,
+                                                       const void *r0, double *partials, unsigned int *ticket,
+                                                       double *sc, int Vh) {
+    using T = typename Traits<P>::real;
+    if (sc[BI_DONE] != 0.0) return;
+    const cplx<T> al = {(T)sc[BI_ALPHA], (T)sc[BI_ALPHA + 1]};
+    const cplx<T> om = {(T)sc[BI_OMEGA], (T)sc[BI_OMEGA + 1]};
+    const cplx<T> mom = {-om.re, -om.im};
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<T> xv[12], pv[12], sv[12], tv[12], r0v[12];
+        SpinorIO<P>::load(xv, x, h, Vh);
+        SpinorIO<P>::load(pv, p, h, Vh);
+        SpinorIO<P>::load(sv, s, h, Vh);
+#pragma unroll
+        for (int k = 0; k < 12; k++) xv[k] = cfma(om, sv[k], cfma(al, pv[k], xv[k]));
+        SpinorIO<P>::store(x, h, Vh, xv);
+        SpinorIO<P>::load(tv, t, h, Vh);
+#pragma unroll
+        for (int k = 0; k < 12; k++) sv[k] = cfma(mom, tv[k], sv[k]);
+        SpinorIO<P>::store(r, h, Vh, sv);
+        // the reductions take r from registers: r was written by this kernel, and
+        // the read-only load path may not see a kernel's own stores
+        SpinorIO<P>::load(r0v, r0, h, Vh);
+        T re = T(0), im = T(0);
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            re += r0v[k].re * sv[k].re + r0v[k].im * sv[k].im;
+            im += r0v[k].re * sv[k].im - r0v[k].im * sv[k].re;
+        }
+        acc[0] += (double)re;
+        acc[1] += (double)im;
+        acc[2] += norm2_site(sv);
+    }
+    double tot[3];
+    if (grid_sum(acc, partials, ticket, tot) && threadIdx.x == 0) {
+        const double2 rho_new = make_double2(tot[0], tot[1]);
+        const double rr = tot[2];
+        sc[BI_RR] = rr;
+        sc[BI_ITERS] += 1.0;
+        if (rr <= sc[BI_TOL2]) sc[BI_DONE] = 1.0;
+        const double arho = sqrt(rho_new.x * rho_new.x + rho_new.y * rho_new.y);
+        if (arho < 1e-6 * sqrt(sc[BI_R0N] * rr)) {
+            // r nearly orthogonal to the shadow residual: r0 = r, rho = |r|^2
+            sc[BI_RESTART] = 1.0;
+            sc[BI_RHO] = rr;
+            sc[BI_RHO + 1] = 0.0;
+            sc[BI_R0N] = rr;
+            sc[BI_BETA] = sc[BI_BETA + 1] = 0.0;
+        } else {
+            sc[BI_RESTART] = 0.0;
+            const double2 ratio = zdiv(rho_new, make_double2(sc[BI_RHO], sc[BI_RHO + 1]));
+            const double2 ao = zdiv(make_double2(sc[BI_ALPHA], sc[BI_ALPHA + 1]),
+                                    make_double2(sc[BI_OMEGA], sc[BI_OMEGA + 1]));
+            const double2 be = zmul(ratio, ao);
+            sc[BI_BETA] = be.x;
+            sc[BI_BETA + 1] = be.y;
+            sc[BI_RHO] = rho_new.x;
+            sc[BI_RHO + 1] = rho_new.y;
+        }
+    }
+}
+
 int bq_dot_launch(bq_ctx *c, const void *a, const void *b, int prec, double *partials, unsigned int *ticket,
                   double *out_dev);
 
@@ -173,75 +408,64 @@ int add_to_double(bq_ctx *c, void *x, const void *d, int pd) {
 // p, v, s, t and the odd-parity temporary of Mhat. When |<r0, r>| falls below
 // 1e-6 |r0| |r| the shadow residual is replaced by r and the recurrences
 // restart; near the critical kappa this keeps the method from stagnating.
+// All scalars live on the device: every reduction's last block computes the
+// next coefficient, and the host reads the residual only every `check`
+// iterations.
 struct Bicg {
     void *b, *x, *r, *r0, *p, *v, *s, *t, *tmp_o;
 };
 
-int bicgstab(bq_ctx *c, int prec, int dag, const Bicg &w, double tol_abs, int max_iter, int *iters, double *dslash) {
-    const zc one(1, 0), zero(0, 0);
-    BQ_TRY(axpy3(c, prec, w.x, zero, nullptr, zero, nullptr, zero, nullptr));
-    BQ_TRY(axpy3(c, prec, w.r, one, w.b, zero, nullptr, zero, nullptr));
-    BQ_TRY(axpy3(c, prec, w.r0, one, w.b, zero, nullptr, zero, nullptr));
-    BQ_TRY(axpy3(c, prec, w.p, zero, nullptr, zero, nullptr, zero, nullptr));
-    BQ_TRY(axpy3(c, prec, w.v, zero, nullptr, zero, nullptr, zero, nullptr));
-    zc rho(1, 0), alpha(1, 0), omega(1, 0), rr;
-    BQ_TRY(dotc(c, prec, w.r, w.r, &rr));
+int bicgstab(bq_ctx *c, int prec, int dag, const Bicg &w, double tol_abs, int max_iter, int check, int *iters,
+             double *dslash) {
+    double *sc = c->red_partials + 6 * RED_MAX_BLOCKS;  // BI_N scalars after the partials and the dot results
+    const int G = red_grid(c->Vh);
+    cudaStream_t st = c->stream;
+#define BI_LAUNCH(K, ...)                                                                                  \
+    do {                                                                                                   \
+        if (prec == BQ_PREC_DOUBLE) K<BQ_PREC_DOUBLE><<<G, RED_THREADS, 0, st>>>(__VA_ARGS__);             \
+        else if (prec == BQ_PREC_SINGLE) K<BQ_PREC_SINGLE><<<G, RED_THREADS, 0, st>>>(__VA_ARGS__);        \
+        else K<BQ_PREC_HALF><<<G, RED_THREADS, 0, st>>>(__VA_ARGS__);                                      \
+        BQ_LAUNCH_CHECK();                                                                                 \
+        BQ_COUNT(c);                                                                                       \
+    } while (0)
+    BI_LAUNCH(k_bi_init, w.b, w.x, w.r, w.r0, w.p, w.v, c->red_partials, c->red_ticket, sc, c->Vh, tol_abs * tol_abs);
+    double h[BI_N];
+    BQ_CUDA_TRY(cudaMemcpyAsync(h, sc, sizeof h, cudaMemcpyDeviceToHost, st));
+    BQ_CUDA_TRY(cudaStreamSynchronize(st));
+    const double rr_start = h[BI_RR];
     *iters = 0;
-    const double rr_start = rr.real();
-    double r0n = rr.real();  // |r0|^2 of the current shadow residual
-    if (rr.real() <= tol_abs * tol_abs) return BQ_OK;
+    if (!(rr_start > tol_abs * tol_abs)) return BQ_OK;
+    if (check < 1) check = 1;
+    int prev_launched = 0;
     for (int k = 0; k < max_iter; k++) {
-        zc rho_new;
-        BQ_TRY(dotc(c, prec, w.r0, w.r, &rho_new));
-        if (!(std::abs(rho_new) == std::abs(rho_new))) {
-            bq_set_error("BiCGstab breakdown at iteration %d: <r0, r> is not finite", k);
-            return BQ_ERR_NOT_CONVERGED;
-        }
-        // r nearly orthogonal to the shadow residual: restart the recurrences
-        // with r0 = r (x and r carry over), which keeps <r0, r> = |r|^2 > 0
-        if (std::abs(rho_new) < 1e-6 * sqrt(r0n * rr.real())) {
-            BQ_TRY(axpy3(c, prec, w.r0, one, w.r, zero, nullptr, zero, nullptr));
-            BQ_TRY(axpy3(c, prec, w.p, zero, nullptr, zero, nullptr, zero, nullptr));
-            BQ_TRY(axpy3(c, prec, w.v, zero, nullptr, zero, nullptr, zero, nullptr));
-            BQ_TRY(dotc(c, prec, w.r0, w.r, &rho_new));
-            r0n = rho_new.real();
-            rho = alpha = omega = one;
-            if (!(r0n > 0)) {
-                bq_set_error("BiCGstab breakdown at iteration %d: |r|^2 = %.3e", k, r0n);
-                return BQ_ERR_NOT_CONVERGED;
-            }
-        }
-        const zc beta = (rho_new / rho) * (alpha / omega);
-        rho = rho_new;
-        BQ_TRY(axpy3(c, prec, w.p, one, w.r, beta, w.p, -beta * omega, w.v));  // p = r + beta (p - omega v)
-        BQ_TRY(bq_mhat_launch(c, prec, w.v, w.p, dag, w.tmp_o));               // v = Mhat p
-        zc r0v;
-        BQ_TRY(dotc(c, prec, w.r0, w.v, &r0v));
-        alpha = rho / r0v;
-        BQ_TRY(axpy3(c, prec, w.s, one, w.r, -alpha, w.v, zero, nullptr));     // s = r - alpha v
-        BQ_TRY(bq_mhat_launch(c, prec, w.t, w.s, dag, w.tmp_o));               // t = Mhat s
-        zc ts, tt;
-        BQ_TRY(dotc(c, prec, w.t, w.s, &ts));
-        BQ_TRY(dotc(c, prec, w.t, w.t, &tt));
-        omega = (tt.real() > 0) ? ts / tt : zero;
-        BQ_TRY(axpy3(c, prec, w.x, one, w.x, alpha, w.p, omega, w.s));        // x += alpha p + omega s
-        BQ_TRY(axpy3(c, prec, w.r, one, w.s, -omega, w.t, zero, nullptr));    // r = s - omega t
-        BQ_TRY(dotc(c, prec, w.r, w.r, &rr));
-        *dslash += 4;
-        *iters = k + 1;
-        if (!(rr.real() <= 1e12 * rr_start)) {
+        BI_LAUNCH(k_bi_dir, w.p, w.r, w.v, w.r0, sc, c->Vh);
+        BQ_TRY(bq_mhat_launch(c, prec, w.v, w.p, dag, w.tmp_o));  // v = Mhat p
+        BI_LAUNCH(k_bi_alpha, w.r0, w.v, c->red_partials, c->red_ticket, sc, c->Vh);
+        BI_LAUNCH(k_bi_s, w.s, w.r, w.v, sc, c->Vh);                  // s = r - alpha v
+        BQ_TRY(bq_mhat_launch(c, prec, w.t, w.s, dag, w.tmp_o));  // t = Mhat s
+        BI_LAUNCH(k_bi_omega, w.t, w.s, c->red_partials, c->red_ticket, sc, c->Vh);
+        BI_LAUNCH(k_bi_xr, w.x, w.r, w.p, w.s, w.t, w.r0, c->red_partials, c->red_ticket, sc, c->Vh);
+        if ((k + 1) % check != 0 && k + 1 < max_iter) continue;
+        BQ_CUDA_TRY(cudaMemcpyAsync(h, sc, sizeof h, cudaMemcpyDeviceToHost, st));
+        BQ_CUDA_TRY(cudaStreamSynchronize(st));
+        // iterations after convergence (up to check - 1 of them) changed nothing
+        *iters = (int)h[BI_ITERS];
+        *dslash += 4.0 * (k + 1 - prev_launched);
+        prev_launched = k + 1;
+        if (!(h[BI_RR] <= 1e12 * rr_start)) {
             // NaN, or growth by 1e6 in norm: past the critical kappa the spectrum of
             // Mhat surrounds the origin and BiCGstab diverges (CG on Mhat^dag Mhat does not)
-            bq_set_error("BiCGstab diverged at iteration %d: |r|^2 = %.3e from %.3e (use the CG method)", k,
-                         rr.real(), rr_start);
+            bq_set_error("BiCGstab diverged by iteration %d: |r|^2 = %.3e from %.3e (use the CG method)", k + 1,
+                         h[BI_RR], rr_start);
             return BQ_ERR_NOT_CONVERGED;
         }
-        if (rr.real() <= tol_abs * tol_abs) break;
-        if (omega == zero) {
-            bq_set_error("BiCGstab breakdown at iteration %d: omega = 0", k);
+        if (h[BI_BREAK] != 0.0) {
+            bq_set_error("BiCGstab breakdown by iteration %d (<r0, v> or <t, t> vanished)", k + 1);
             return BQ_ERR_NOT_CONVERGED;
         }
+        if (h[BI_DONE] != 0.0) break;
     }
+#undef BI_LAUNCH
     return BQ_OK;
 }
 
@@ -296,7 +520,7 @@ int solve_mhat_bicgstab(bq_ctx *c, FullWork &w, int dag, const bq_solver_params 
         const double tol_in = (pin == BQ_PREC_DOUBLE) ? 0.5 * sqrt(target2)
                                                       : fmax(delta * sqrt(rr.real()), 0.5 * sqrt(target2));
         int its = 0;
-        BQ_TRY(bicgstab(c, pin, dag, bw, tol_in, sp->max_iter - total, &its, &st->dslash_calls));
+        BQ_TRY(bicgstab(c, pin, dag, bw, tol_in, sp->max_iter - total, sp->check_every, &its, &st->dslash_calls));
         total += its;
         if (pin == BQ_PREC_DOUBLE)
             BQ_TRY(axpy3(c, BQ_PREC_DOUBLE, w.xe, one, w.xe, one, w.ix, zero, nullptr));
