@@ -76,6 +76,9 @@ typedef struct {
                          iterated residual fell by this factor since the last update (mixed only) */
     int check_every;  /* iterations between host-side convergence checks (>= 1) */
     double shift;     /* sigma >= 0: solve (Mhat^dag Mhat + sigma) x = b */
+    int initial_guess; /* bq_solve_cg / bq_solve_cg_batch: 1 = start from the x passed in (a
+                          restart, or the previous solution in a molecular-dynamics
+                          trajectory), 0 = start from x = 0; the other solvers start from 0 */
 } bq_solver_params;
 
 typedef struct {

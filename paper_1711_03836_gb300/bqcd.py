@@ -35,7 +35,8 @@ class bq_params(ctypes.Structure):
 
 class bq_solver_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
-                ("delta", ctypes.c_double), ("check_every", ctypes.c_int), ("shift", ctypes.c_double)]
+                ("delta", ctypes.c_double), ("check_every", ctypes.c_int), ("shift", ctypes.c_double),
+                ("initial_guess", ctypes.c_int)]
 
 
 class bq_solver_stats(ctypes.Structure):
@@ -287,13 +288,15 @@ def bq_apply_mdagm(ctx, out, inp, precision):
 
 
 def bq_solve_cg(ctx, x, b, tol=1e-10, max_iter=10000, precision="double", delta=1e-3, check_every=8, shift=0.0,
-                raise_on_nonconvergence=True):
-    """Solve (Mhat^dag Mhat + shift) x = b; x, b canonical [V/2][4][3] complex128 (host or device)."""
+                raise_on_nonconvergence=True, initial_guess=False):
+    """Solve (Mhat^dag Mhat + shift) x = b; x, b canonical [V/2][4][3] complex128 (host or device);
+    initial_guess=True starts from the x passed in."""
     px, wx = _ptr_where(x)
     pb, wb = _ptr_where(b)
     if wx != wb:
         raise ValueError("x and b must both be host or both be device buffers")
-    sp = bq_solver_params(tol, int(max_iter), PREC_NAMES[precision], delta, int(check_every), shift)
+    sp = bq_solver_params(tol, int(max_iter), PREC_NAMES[precision], delta, int(check_every), shift,
+                          int(bool(initial_guess)))
     st = bq_solver_stats()
     s = _lib_handle().bq_solve_cg(ctx, px, pb, wx, ctypes.byref(sp), ctypes.byref(st))
     if s != BQ_OK and (raise_on_nonconvergence or s != BQ_ERR_NOT_CONVERGED):
@@ -302,7 +305,7 @@ def bq_solve_cg(ctx, x, b, tol=1e-10, max_iter=10000, precision="double", delta=
 
 
 def bq_solve_cg_batch(ctxs, xs, bs, tol=1e-10, max_iter=20000, precision="double", delta=1e-3, check_every=8,
-                      shift=0.0, raise_on_nonconvergence=True):
+                      shift=0.0, raise_on_nonconvergence=True, initial_guess=False):
     """Solve (Mhat^dag Mhat + shift) xs[i] = bs[i] on lattice ctxs[i] for every i in one batched solve."""
     n = len(ctxs)
     if len(xs) != n or len(bs) != n:
@@ -320,7 +323,8 @@ def bq_solve_cg_batch(ctxs, xs, bs, tol=1e-10, max_iter=20000, precision="double
     carr = (ctypes.c_void_p * n)(*[c.value for c in ctxs])
     xarr = (ctypes.c_void_p * n)(*px)
     barr = (ctypes.c_void_p * n)(*pb)
-    sp = bq_solver_params(tol, int(max_iter), PREC_NAMES[precision], delta, int(check_every), shift)
+    sp = bq_solver_params(tol, int(max_iter), PREC_NAMES[precision], delta, int(check_every), shift,
+                          int(bool(initial_guess)))
     st = (bq_solver_stats * n)()
     s = _lib_handle().bq_solve_cg_batch(carr, n, xarr, barr, where, ctypes.byref(sp), st)
     if s != BQ_OK and (raise_on_nonconvergence or s != BQ_ERR_NOT_CONVERGED):

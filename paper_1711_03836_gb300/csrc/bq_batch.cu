@@ -966,24 +966,28 @@ extern "C" int bq_solve_cg_batch(bq_ctx *const *ctxs, int nsys, double *const *x
             if (status == BQ_OK) w->stage_bytes = need;
         }
     }
+    // b (and, with an initial guess, x) into the slots
+    const bool x0 = sp->initial_guess != 0;
     for (int i = 0; i < nsys && status == BQ_OK; i++) {
         bq_ctx *c = ctxs[i];
-        const double *src = b[i];
-        if (where == BQ_HOST) {
-            if (cudaMemcpyAsync(w->stage, b[i], (size_t)c->Vh * 192, cudaMemcpyHostToDevice, c0->stream) !=
-                cudaSuccess)
-                status = BQ_ERR_CUDA;
-            src = w->stage;
-        }
-        if (status == BQ_OK) {
-            cudaStream_t keep = c->stream;
-            c->stream = c0->stream;
-            status = bq_pack(c, w->slot[i].b, src, BQ_PREC_DOUBLE);
-            c->stream = keep;
+        for (int which = 0; which < (x0 ? 2 : 1) && status == BQ_OK; which++) {
+            const double *src = which ? x[i] : b[i];
+            if (where == BQ_HOST) {
+                if (cudaMemcpyAsync(w->stage, src, (size_t)c->Vh * 192, cudaMemcpyHostToDevice, c0->stream) !=
+                    cudaSuccess)
+                    status = BQ_ERR_CUDA;
+                src = w->stage;
+            }
+            if (status == BQ_OK) {
+                cudaStream_t keep = c->stream;
+                c->stream = c0->stream;
+                status = bq_pack(c, which ? w->slot[i].x : w->slot[i].b, src, BQ_PREC_DOUBLE);
+                c->stream = keep;
+            }
         }
     }
     if (status == BQ_OK) {
-        status = cg_batch_dispatch(c0, nsys, ctxs, nullptr, sp, false, 0, st);
+        status = cg_batch_dispatch(c0, nsys, ctxs, nullptr, sp, x0, 0, st);
     }
     for (int i = 0; i < nsys && (status == BQ_OK || status == BQ_ERR_NOT_CONVERGED); i++) {
         bq_ctx *c = ctxs[i];
