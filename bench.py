@@ -80,10 +80,13 @@ def parse():
     ap.add_argument("--fp64-arith", default="df64", choices=["native", "df64"],
                     help="arithmetic of the FP64-storage operator kernels")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 CG, sweep, e2e and CPU baseline")
-    ap.add_argument("--mode", default="cg", choices=["cg", "batch12", "multishift10", "ragged4", "qed2x4"],
+    ap.add_argument("--mode", default="cg", choices=["cg", "batch12", "multishift10", "ragged4", "qed2x4",
+                                                     "blockms4x10", "full_cg", "traces8"],
                     help="the timed step: one mixed CG solve (default), 12 point sources in one batched "
-                         "solve, a 10-shift multishift solve, a ragged batch of four lattices, or (48^3x96) "
-                         "4 Gaussian sources for each of the two QED flavours in one batched solve")
+                         "solve, a 10-shift multishift solve, a ragged batch of four lattices, (48^3x96) "
+                         "4 Gaussian sources for each of the two QED flavours in one batched solve, a block "
+                         "multishift solve of 4 sources x 10 shifts, one full-lattice M x = b solve (CG on "
+                         "Mhat^dag Mhat), or the trace samples of 8 Z2 noise vectors")
     return ap.parse_args()
 
 
@@ -528,6 +531,20 @@ def make_step(args, torch, bqcd, synth, lat, b_dev, x_dev, solve_kw, field_input
         xk = [torch.empty_like(b_dev) for _ in shifts]
         kw = {k: v for k, v in solve_kw.items() if k != "max_iter"}
         return (lambda: bqcd.bq_solve_multishift_cg(ctx, xk, b_dev, shifts, **kw)), []
+    if args.mode == "blockms4x10":
+        shifts = [10.0 ** (-4 + 4 * k / 9) for k in range(10)]
+        b4 = [torch.from_numpy(synth.gaussian_spinor(lat.Vh, 780 + r)).cuda() for r in range(4)]
+        x4 = [[torch.empty_like(b_dev) for _ in shifts] for _ in b4]
+        kw = {k: v for k, v in solve_kw.items() if k != "max_iter"}
+        return (lambda: bqcd.bq_solve_multishift_cg_block(ctx, x4, b4, shifts, **kw)), []
+    if args.mode == "full_cg":
+        b_o = torch.from_numpy(synth.gaussian_spinor(lat.Vh, 602)).cuda()
+        x_o = torch.empty_like(b_o)
+        return (lambda: bqcd.bq_solve_full(ctx, x_dev, x_o, b_dev, b_o, method="cg", **solve_kw)), []
+    if args.mode == "traces8":
+        etas = [(torch.from_numpy(synth.z2_noise(lat.Vh, 610 + 2 * n)).cuda(),
+                 torch.from_numpy(synth.z2_noise(lat.Vh, 611 + 2 * n)).cuda()) for n in range(8)]
+        return (lambda: bqcd.bq_trace_samples(ctx, [e for e, _ in etas], [o for _, o in etas], **solve_kw)[1]), []
     # ragged: the workload lattice plus 8^4, 12^4 and 16^3x32, in one batched solve
     lats, bs, xr = [lat], [b_dev], [x_dev]
     for i, dims in enumerate([(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32)]):
