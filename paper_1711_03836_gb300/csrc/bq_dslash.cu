@@ -368,21 +368,41 @@ __device__ __forceinline__ void dslash_site_df64(const DslashArgs &a, const void
 
     if (EPI == EPI_PLAIN) {
         SpinorIO<BQ_PREC_DF64>::store(out, h, Vh, acc);
-    } else if (EPI == EPI_CLOVINV) {
-        cplx<T> o[12];
-        clover_apply_site<BQ_PREC_DF64>(o, acc, a.clov, h, Vh);
-        SpinorIO<BQ_PREC_DF64>::store(out, h, Vh, o);
-    } else {
-        cplx<T> xv[12], o[12];
-        SpinorIO<BQ_PREC_DF64>::load(xv, xin, h, Vh);
-        clover_apply_site<BQ_PREC_DF64>(o, xv, a.clov, h, Vh);
-        const T k = (T)a.k;
+        return;
+    }
+    // clover epilogue one chirality block (spin components 6b .. 6b + 5) at a
+    // time in a rolled loop: one copy of the 6x6 block code instead of two keeps
+    // the kernel inside the instruction cache
+    const T k = (T)a.k;
+#pragma unroll 1
+    for (int b = 0; b < 2; b++) {
+        T d[6];
+        cplx<T> o[15], xb[6], ab[6], yb[6];
+        CloverIO<BQ_PREC_DF64>::load_block(d, o, a.clov, b, h, Vh);
 #pragma unroll
-        for (int c = 0; c < 12; c++) {
-            o[c].re = fma(-k, acc[c].re, o[c].re);
-            o[c].im = fma(-k, acc[c].im, o[c].im);
+        for (int i = 0; i < 6; i++) ab[i] = b ? acc[6 + i] : acc[i];
+        if (EPI == EPI_CLOVINV) {
+#pragma unroll
+            for (int i = 0; i < 6; i++) xb[i] = ab[i];
+        } else {
+            const double2 *px = static_cast<const double2 *>(xin) + (size_t)(6 * b) * Vh + h;
+#pragma unroll
+            for (int i = 0; i < 6; i++) {
+                const double2 v = ldg(px + (size_t)i * Vh);
+                xb[i] = {df_from_double(v.x), df_from_double(v.y)};
+            }
         }
-        SpinorIO<BQ_PREC_DF64>::store(out, h, Vh, o);
+        herm6_apply(d, o, xb, yb);
+        if (EPI == EPI_XPAY) {
+#pragma unroll
+            for (int i = 0; i < 6; i++) {
+                yb[i].re = fma(-k, ab[i].re, yb[i].re);
+                yb[i].im = fma(-k, ab[i].im, yb[i].im);
+            }
+        }
+        double2 *po = static_cast<double2 *>(out) + (size_t)(6 * b) * Vh + h;
+#pragma unroll
+        for (int i = 0; i < 6; i++) po[(size_t)i * Vh] = make_double2(df_to_double(yb[i].re), df_to_double(yb[i].im));
     }
 }
 
