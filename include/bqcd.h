@@ -317,8 +317,11 @@ int bq_solve_multishift_cg_block(bq_ctx *ctx, int nrhs, double *const *x, const 
  * (the solve starts from 0). stats->true_residual = |b - M x| / |b| over both
  * parities, computed in FP64 after the reconstruction; BQ_ERR_NOT_CONVERGED
  * when it stays above params->tol (x then holds the last iterate), also when
- * BiCGstab breaks down (rho or omega 0). b = 0 gives x = 0. Allocates and frees
- * its own 18 half-lattice work vectors per call. */
+ * BiCGstab breaks down (<r0, v> or <t, t> vanishing) or diverges (|r| grows by
+ * 1e6: past the critical kappa, where CG still converges). b = 0 gives x = 0.
+ * Its 18 half-lattice work vectors are allocated on the first call and kept
+ * with the context until bq_destroy. BiCGstab's coefficients stay on the device;
+ * the host reads the residual every params->check_every iterations. */
 int bq_solve_full(bq_ctx *ctx, double *x_e, double *x_o, const double *b_e, const double *b_o, int where,
                   int method, int dagger, const bq_solver_params *params, bq_solver_stats *stats);
 
@@ -335,7 +338,9 @@ int bq_solve_full(bq_ctx *ctx, double *x_e, double *x_o, const double *b_e, cons
  *   samples[5n + 4]    = |y|^2 = eta^dag (M^dag M)^{-1} eta
  * are written; the mean over the noise estimates each trace when the noise has
  * E[eta eta^dag] = 1. stats (may be NULL) has 2 * nnoise entries: the M solve
- * of noise n at n, the M^dag solve at nnoise + n. params->shift must be 0. */
+ * of noise n at n, the M^dag solve at nnoise + n. params->shift must be 0.
+ * FP64 work vectors (8 per noise vector) are kept with the context for later
+ * calls; the batched solver's slots likewise. */
 int bq_trace_samples(bq_ctx *ctx, int nnoise, const double *const *eta_e, const double *const *eta_o, int where,
                      const bq_solver_params *params, double *samples, bq_solver_stats *stats);
 
