@@ -6,7 +6,11 @@
  * chemical potential e^{+-mu} on time links, the clover term of Eq. 2, and the
  * QCD+QED U(1) phases of Eq. 5, in even-odd preconditioned form
  *     Mhat = A_ee - kappa^2 D_eo A_oo^{-1} D_oe,
- * and solves with it by CG and multishift CG (Section 4, "solvers").
+ * and solves with it by CG and multishift CG (Section 4, "solvers"), also
+ * batched over right-hand sides, shifts and lattices. Around the solve: the
+ * full-lattice system M x = b (or M^dag x = b) by CG-normal or BiCGstab,
+ * stout-smeared hopping links (Eq. 5), the clover log det and stochastic trace
+ * samples of the fermion matrix (Section 5).
  *
  * Conventions.
  *   Lattice extents dims = {Lx, Ly, Lz, Lt}, all even and >= 2; V = Lx*Ly*Lz*Lt.
