@@ -112,13 +112,11 @@ extern "C" int bq_create(bq_ctx **out, const int dims[4], void *stream) {
     return BQ_OK;
 }
 
-void bq_solver_free(bq_ctx *c);  // bq_solvers.cu
 void bq_full_free(bq_ctx *c);    // bq_full.cu
 
 extern "C" int bq_destroy(bq_ctx *c) {
     if (!c) return BQ_OK;
     cudaStreamSynchronize(c->stream);
-    bq_solver_free(c);
     bq_batch_free(c);
     bq_full_free(c);
     cudaFree(c->U_canon);

@@ -666,7 +666,6 @@ __device__ __forceinline__ void clover_apply_site(cplx<T> out[12], const cplx<T>
 
 enum { BQ_NPREC = 3, BQ_NFIELD = 4 };  // field storages: the three precisions + df64 pairs
 
-struct SolverWork;  // defined in the solver translation unit
 struct BatchWork;   // defined in the batched solver translation unit
 
 struct bq_ctx {
@@ -704,7 +703,6 @@ struct bq_ctx {
     double *red_partials;          // block partial sums of reductions
     unsigned int *red_ticket;      // last-block ticket
     int *dev_flag;                 // device error flag (singular clover etc.)
-    SolverWork *solver;
     BatchWork *batch;
 
     // counters and optional per-launch event timing of the hopping term

@@ -1,6 +1,6 @@
-// bq_ms.cuh -- multishift CG recurrences shared by the single-system and the
-// block (several right-hand sides) multishift solvers: device bodies of the
-// three BLAS steps of an iteration and the per-system scalar layout.
+// bq_ms.cuh -- multishift CG recurrences of the (block) multishift solver:
+// device bodies of the three BLAS steps of an iteration and the per-system
+// scalar layout.
 #pragma once
 
 #include "bq_reduce.cuh"
