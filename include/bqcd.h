@@ -277,7 +277,7 @@ int bq_solve_cg_batch(bq_ctx *const *ctx, int nsys, double *const *x, const doub
  * RHMC rational approximation): solve (Mhat^dag Mhat + shifts[k]) x[k] = b for
  * k < nshift (1..32, shifts >= 0) in ONE Krylov space of the smallest shift,
  * run in params->precision to what that precision resolves (FP64: tol,
- * FP32: 1e-6, FP16: 1e-3 relative iterated residual), with per-shift
+ * FP32: 1e-7, FP16: 3e-4 relative iterated residual), with per-shift
  * zeta/alpha/beta recurrences and per-shift freezing; then every shift is
  * refined by (mixed-precision) CG from that solution to a TRUE FP64 residual
  * <= tol |b|, all shifts together as one batched solve.  x[k] are canonical even spinors (host or device, as b); stats
