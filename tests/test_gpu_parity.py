@@ -804,3 +804,36 @@ def test_cg_initial_guess(bq, prec):
         assert s_["converged"] and np.linalg.norm(op.mdagm(xd.cpu().numpy()) - bh) / np.linalg.norm(bh) <= 1e-10
     assert sts[0]["iterations"] < sts[1]["iterations"]
     lat.close()
+
+
+def test_parameter_and_field_updates(bq):
+    """The derived fields follow every change: kappa, c_SW, mu, the time boundary,
+    the charge with a U(1) field, and a new gauge field, at FP64, FP32 and FP16,
+    each apply checked against the oracle built from the new state."""
+    dims = (6, 4, 6, 10)
+    U1, U2 = synth.gauge_field(dims, 0.2, 1), synth.gauge_field(dims, 0.25, 2)
+    A = synth.u1_field(dims, 0.1, 3)
+    psi = synth.gaussian_spinor(dims[0] * dims[1] * dims[2] * dims[3] // 2, 5)
+    lat = bq.Lattice(dims, 0.12, 1.0, 0.0, -1.0)
+    bq.bq_set_gauge(lat.ctx, U1)
+    states = [
+        (dict(kappa=0.12, csw=1.0, mu=0.0, t_bc=-1.0, charge=0.0), U1, None),
+        (dict(kappa=0.135, csw=1.9, mu=0.0, t_bc=-1.0, charge=0.0), U1, None),
+        (dict(kappa=0.135, csw=1.9, mu=0.15, t_bc=+1.0, charge=0.0), U1, None),
+        (dict(kappa=0.13, csw=1.7, mu=0.05, t_bc=-1.0, charge=2.0 / 3.0), U1, A),
+        (dict(kappa=0.13, csw=1.7, mu=0.05, t_bc=-1.0, charge=-1.0 / 3.0), U2, A),
+        (dict(kappa=0.13, csw=1.7, mu=0.05, t_bc=-1.0, charge=0.0), U2, None),
+    ]
+    for prm, U, A_ in states:
+        bq.bq_set_params(lat.ctx, **prm)
+        if U is U2:
+            bq.bq_set_gauge(lat.ctx, U2)
+        bq.bq_set_u1(lat.ctx, A_)
+        p = oracle.params(dims, **prm)
+        op = oracle.Operator(p, U, A_)
+        ref = op.mhat(psi)
+        for prec in ("double", "single", "half"):
+            out = lat.spinor(prec)
+            bq.bq_apply_mhat(lat.ctx, out, lat.pack(psi, prec), 0, prec)
+            assert rel(lat.unpack(out, prec), ref) < TOL[prec], (prm, prec)
+    lat.close()
