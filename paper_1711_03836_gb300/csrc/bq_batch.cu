@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "bq_ms.cuh"
+#include "bq_nvtx.cuh"
 
 struct SysVec {
     void *b, *x, *r, *t;  // FP64 native
@@ -930,6 +931,7 @@ int bq_cg_batch_core(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double *sh
 
 extern "C" int bq_solve_cg_batch(bq_ctx *const *ctxs, int nsys, double *const *x, const double *const *b, int where,
                                  const bq_solver_params *sp, bq_solver_stats *stats) {
+    BqRange range("bq_solve_cg_batch");
     if (!ctxs || nsys < 1 || !x || !b || !(where == BQ_HOST || where == BQ_DEVICE)) {
         bq_set_error("bq_solve_cg_batch: bad arguments");
         return BQ_ERR_ARG;
@@ -1173,6 +1175,7 @@ static int ms_block_run(bq_ctx *c0, int nrhs, int n, const double *shifts, int b
 extern "C" int bq_solve_multishift_cg_block(bq_ctx *c, int nrhs, double *const *x, const double *const *b, int where,
                                             int nshift, const double *shifts, const bq_solver_params *sp,
                                             bq_solver_stats *stats, double *residuals) {
+    BqRange range("bq_solve_multishift_cg_block");
     if (!c || nrhs < 1 || !x || !b || !shifts || !sp || !(where == BQ_HOST || where == BQ_DEVICE) || nshift < 1 ||
         nshift > MS_MAX) {
         bq_set_error("bq_solve_multishift_cg_block: bad arguments (nrhs >= 1, 1 <= nshift <= %d)", MS_MAX);

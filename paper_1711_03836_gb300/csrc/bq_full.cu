@@ -22,6 +22,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "bq_nvtx.cuh"
 #include "bq_reduce.cuh"
 
 using zc = std::complex<double>;
@@ -587,6 +588,7 @@ int solve_mhat_cg(bq_ctx *c, FullWork &w, int dag, const bq_solver_params *sp, d
 
 extern "C" int bq_solve_full(bq_ctx *c, double *x_e, double *x_o, const double *b_e, const double *b_o, int where,
                              int method, int dagger, const bq_solver_params *sp, bq_solver_stats *st) {
+    BqRange range("bq_solve_full");
     if (!c || !x_e || !x_o || !b_e || !b_o || !sp || !(where == BQ_HOST || where == BQ_DEVICE) ||
         !(method == BQ_SOLVER_CG || method == BQ_SOLVER_BICGSTAB) || !(dagger == 0 || dagger == 1)) {
         bq_set_error("bq_solve_full: bad arguments");
@@ -724,6 +726,7 @@ struct TraceSys {
 
 extern "C" int bq_trace_samples(bq_ctx *c, int nnoise, const double *const *eta_e, const double *const *eta_o,
                                 int where, const bq_solver_params *sp, double *samples, bq_solver_stats *stats) {
+    BqRange range("bq_trace_samples");
     if (!c || nnoise < 1 || !eta_e || !eta_o || !samples || !sp || !(where == BQ_HOST || where == BQ_DEVICE)) {
         bq_set_error("bq_trace_samples: bad arguments");
         return BQ_ERR_ARG;

@@ -7,6 +7,7 @@
 #include <math.h>
 
 #include "bq_geo.cuh"
+#include "bq_nvtx.cuh"
 #include "bq_reduce.cuh"
 
 // exp(X) of a traceless anti-Hermitian 3x3 matrix: scaling and squaring of a
@@ -77,6 +78,7 @@ __global__ void __launch_bounds__(128) k_stout_step(double2 *out, const double2 
 
 int bq_prepare_hop_links(bq_ctx *c) {
     if (c->U_hop_valid) return BQ_OK;
+    BqRange range("stout smearing");
     const size_t bytes = (size_t)c->V * 4 * 9 * sizeof(double2);
     BQ_TRY(bq_alloc((void **)&c->U_hop, bytes));
     double2 *tmp = nullptr;
