@@ -39,6 +39,58 @@ __device__ M3 expm_su3(const M3 &X) {
     return E;
 }
 
+// exp(X) = exp(iQ), Q = -iX Hermitian traceless, in closed form by the
+// Cayley-Hamilton theorem (Morningstar and Peardon 2004, Section III):
+// exp(iQ) = f0 + f1 Q + f2 Q^2 with the f_j from c0 = det Q = tr Q^3 / 3 and
+// c1 = tr Q^2 / 2. For c0 < 0 the f_j of -c0 are used, f_j(-c0) = (-1)^j
+// conj(f_j(c0)), which keeps the angle theta in [0, pi/2] and the denominator
+// 9u^2 - w^2 >= 2 c1 away from zero; c1 ~ 0 (Q ~ 0) takes the Taylor path.
+__device__ M3 expm_su3_ch(const M3 &X) {
+    M3 Q;
+    for (int k = 0; k < 9; k++) Q.a[k] = {X.a[k].im, -X.a[k].re};  // -i X
+    const M3 Q2 = mmul(Q, Q);
+    const M3 Q3 = mmul(Q, Q2);
+    const double c1 = 0.5 * (Q2.a[0].re + Q2.a[4].re + Q2.a[8].re);
+    if (!(c1 > 1e-12)) return expm_su3(X);
+    double c0 = (Q3.a[0].re + Q3.a[4].re + Q3.a[8].re) / 3.0;
+    const bool neg = c0 < 0.0;
+    c0 = fabs(c0);
+    const double c0max = 2.0 * pow(c1 / 3.0, 1.5);
+    const double theta = acos(fmin(c0 / c0max, 1.0));
+    const double u = sqrt(c1 / 3.0) * cos(theta / 3.0);
+    const double w = sqrt(c1) * sin(theta / 3.0);
+    const double w2 = w * w, u2 = u * u;
+    // xi0(w) = sin(w) / w, by its series near w = 0
+    const double xi0 = (fabs(w) < 0.05) ? 1.0 - w2 / 6.0 * (1.0 - w2 / 20.0 * (1.0 - w2 / 42.0)) : sin(w) / w;
+    const double cw = cos(w);
+    const cplx<double> e2iu = {cos(2.0 * u), sin(2.0 * u)}, emiu = {cos(u), -sin(u)};
+    // h0 = (u^2 - w^2) e^{2iu} + e^{-iu} [8 u^2 cos w + 2 i u (3u^2 + w^2) xi0]
+    cplx<double> h0 = cadd(cscale(u2 - w2, e2iu), cmul(emiu, cplx<double>{8.0 * u2 * cw, 2.0 * u * (3.0 * u2 + w2) * xi0}));
+    // h1 = 2u e^{2iu} - e^{-iu} [2u cos w - i (3u^2 - w^2) xi0]
+    cplx<double> h1 = csub(cscale(2.0 * u, e2iu), cmul(emiu, cplx<double>{2.0 * u * cw, -(3.0 * u2 - w2) * xi0}));
+    // h2 = e^{2iu} - e^{-iu} [cos w + 3 i u xi0]
+    cplx<double> h2 = csub(e2iu, cmul(emiu, cplx<double>{cw, 3.0 * u * xi0}));
+    const double inv = 1.0 / (9.0 * u2 - w2);
+    h0 = cscale(inv, h0);
+    h1 = cscale(inv, h1);
+    h2 = cscale(inv, h2);
+    if (neg) {  // f_j(-c0) = (-1)^j conj(f_j(c0))
+        h0 = cconj(h0);
+        h1 = cscale(-1.0, cconj(h1));
+        h2 = cconj(h2);
+    }
+    M3 E;
+    for (int k = 0; k < 9; k++) E.a[k] = cadd(cmul(h1, Q.a[k]), cmul(h2, Q2.a[k]));
+    E.a[0] = cadd(E.a[0], h0);
+    E.a[4] = cadd(E.a[4], h0);
+    E.a[8] = cadd(E.a[8], h0);
+    return E;
+}
+
+#ifndef STOUT_EXP_CAYLEY_HAMILTON
+#define STOUT_EXP_CAYLEY_HAMILTON 1
+#endif
+
 // one stout step for every link: C = rho sum_{nu != mu} (upper + lower staple),
 // Omega = C U^dag, X = traceless anti-Hermitian part of Omega
 // (= i Q with Q = (i/2)(Omega^dag - Omega) - (i/6) tr(Omega^dag - Omega)),
@@ -71,7 +123,7 @@ __global__ void __launch_bounds__(128) k_stout_step(double2 *out, const double2 
     X.a[0] = csub(X.a[0], tr);
     X.a[4] = csub(X.a[4], tr);
     X.a[8] = csub(X.a[8], tr);
-    const M3 Un = mmul(expm_su3(X), U);
+    const M3 Un = mmul(STOUT_EXP_CAYLEY_HAMILTON ? expm_su3_ch(X) : expm_su3(X), U);
     double2 *p = out + (x * 4 + mu) * 9;
     for (int k = 0; k < 9; k++) p[k] = make_double2(Un.a[k].re, Un.a[k].im);
 }
