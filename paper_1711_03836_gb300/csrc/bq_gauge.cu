@@ -91,27 +91,96 @@ __device__ M3 expm_su3_ch(const M3 &X) {
 #define STOUT_EXP_CAYLEY_HAMILTON 1
 #endif
 
+// the staple products in double-float (links split exactly into float pairs,
+// each matrix entry a lazy sum of six products): GB300 runs FP32 at ~60x its
+// FP64 rate, and the twelve staple products are most of a stout step's work
+struct M3d {
+    cplx<df> a[9];
+};
+__device__ __forceinline__ M3d load_link_df(const double2 *U, long long lex, int mu) {
+    M3d m;
+    const double2 *p = U + (lex * 4 + mu) * 9;
+    for (int k = 0; k < 9; k++) {
+        const double2 v = p[k];
+        m.a[k] = {df_from_double(v.x), df_from_double(v.y)};
+    }
+    return m;
+}
+__device__ __forceinline__ M3d mdag_df(const M3d &x) {
+    M3d m;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) m.a[i * 3 + j] = {x.a[j * 3 + i].re, -x.a[j * 3 + i].im};
+    return m;
+}
+__device__ M3d mmul_df(const M3d &x, const M3d &y) {
+    M3d m;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            dfsum re = dfs_prod(x.a[i * 3].re, y.a[j].re), im = dfs_prod(x.a[i * 3].re, y.a[j].im);
+            dfs_add_prod(re, -x.a[i * 3].im, y.a[j].im);
+            dfs_add_prod(im, x.a[i * 3].im, y.a[j].re);
+            for (int k = 1; k < 3; k++) {
+                const cplx<df> p = x.a[i * 3 + k], q = y.a[k * 3 + j];
+                dfs_add_prod(re, p.re, q.re);
+                dfs_add_prod(re, -p.im, q.im);
+                dfs_add_prod(im, p.re, q.im);
+                dfs_add_prod(im, p.im, q.re);
+            }
+            m.a[i * 3 + j] = {dfs_done(re), dfs_done(im)};
+        }
+    return m;
+}
+
+#ifndef STOUT_STAPLES_DF64
+#define STOUT_STAPLES_DF64 1
+#endif
+
 // one stout step for every link: C = rho sum_{nu != mu} (upper + lower staple),
 // Omega = C U^dag, X = traceless anti-Hermitian part of Omega
 // (= i Q with Q = (i/2)(Omega^dag - Omega) - (i/6) tr(Omega^dag - Omega)),
 // U' = exp(X) U. Links are periodic in every direction.
-__global__ void __launch_bounds__(128) k_stout_step(double2 *out, const double2 *in, Geo g, double rho) {
+// three resident 128-thread blocks per SM (168 registers): 24 ms per step at
+// 32^3x64 against 30 ms at one or two blocks (255 registers)
+#ifndef STOUT_MIN_BLOCKS
+#define STOUT_MIN_BLOCKS 3
+#endif
+__global__ void __launch_bounds__(128, STOUT_MIN_BLOCKS) k_stout_step(double2 *out, const double2 *in, Geo g,
+                                                                      double rho) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= g.V * 4) return;
     const long long x = idx >> 2;
     const int mu = (int)(idx & 3);
     const long long xpm = lex_step(g, x, mu, +1);
     M3 C;
-    for (int k = 0; k < 9; k++) C.a[k] = {0.0, 0.0};
-    for (int nu = 0; nu < 4; nu++) {
-        if (nu == mu) continue;
-        const long long xpn = lex_step(g, x, nu, +1), xmn = lex_step(g, x, nu, -1);
-        const long long xmn_pm = lex_step(g, xmn, mu, +1);
-        // upper staple U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
-        M3 up = mmul(mmul(load_link(in, x, nu), load_link(in, xpn, mu)), mdag(load_link(in, xpm, nu)));
-        // lower staple U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)
-        M3 lo = mmul(mmul(mdag(load_link(in, xmn, nu)), load_link(in, xmn, mu)), load_link(in, xmn_pm, nu));
-        for (int k = 0; k < 9; k++) C.a[k] = cadd(C.a[k], cadd(up.a[k], lo.a[k]));
+    if (STOUT_STAPLES_DF64) {
+        M3d Cd;
+        for (int k = 0; k < 9; k++) Cd.a[k] = {df(0.0f, 0.0f), df(0.0f, 0.0f)};
+        for (int nu = 0; nu < 4; nu++) {
+            if (nu == mu) continue;
+            const long long xpn = lex_step(g, x, nu, +1), xmn = lex_step(g, x, nu, -1);
+            const long long xmn_pm = lex_step(g, xmn, mu, +1);
+            // upper staple U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
+            const M3d up = mmul_df(mmul_df(load_link_df(in, x, nu), load_link_df(in, xpn, mu)),
+                                   mdag_df(load_link_df(in, xpm, nu)));
+            // lower staple U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)
+            const M3d lo = mmul_df(mmul_df(mdag_df(load_link_df(in, xmn, nu)), load_link_df(in, xmn, mu)),
+                                   load_link_df(in, xmn_pm, nu));
+            for (int k = 0; k < 9; k++) {
+                Cd.a[k].re = add_lazy(Cd.a[k].re, add_lazy(up.a[k].re, lo.a[k].re));
+                Cd.a[k].im = add_lazy(Cd.a[k].im, add_lazy(up.a[k].im, lo.a[k].im));
+            }
+        }
+        for (int k = 0; k < 9; k++) C.a[k] = {df_to_double(normalise(Cd.a[k].re)), df_to_double(normalise(Cd.a[k].im))};
+    } else {
+        for (int k = 0; k < 9; k++) C.a[k] = {0.0, 0.0};
+        for (int nu = 0; nu < 4; nu++) {
+            if (nu == mu) continue;
+            const long long xpn = lex_step(g, x, nu, +1), xmn = lex_step(g, x, nu, -1);
+            const long long xmn_pm = lex_step(g, xmn, mu, +1);
+            M3 up = mmul(mmul(load_link(in, x, nu), load_link(in, xpn, mu)), mdag(load_link(in, xpm, nu)));
+            M3 lo = mmul(mmul(mdag(load_link(in, xmn, nu)), load_link(in, xmn, mu)), load_link(in, xmn_pm, nu));
+            for (int k = 0; k < 9; k++) C.a[k] = cadd(C.a[k], cadd(up.a[k], lo.a[k]));
+        }
     }
     const M3 U = load_link(in, x, mu);
     M3 Om = mmul(C, mdag(U));
