@@ -87,10 +87,6 @@ __device__ M3 expm_su3_ch(const M3 &X) {
     return E;
 }
 
-#ifndef STOUT_EXP_CAYLEY_HAMILTON
-#define STOUT_EXP_CAYLEY_HAMILTON 1
-#endif
-
 // the staple products in double-float (links split exactly into float pairs,
 // each matrix entry a lazy sum of six products): GB300 runs FP32 at ~60x its
 // FP64 rate, and the twelve staple products are most of a stout step's work
@@ -131,11 +127,8 @@ __device__ M3d mmul_df(const M3d &x, const M3d &y) {
     return m;
 }
 
-#ifndef STOUT_STAPLES_DF64
-#define STOUT_STAPLES_DF64 1
-#endif
-
-// one stout step for every link: C = rho sum_{nu != mu} (upper + lower staple),
+// one stout step for every link: C = rho sum_{nu != mu} (upper + lower staple)
+// (staple products in double-float, the rest in FP64),
 // Omega = C U^dag, X = traceless anti-Hermitian part of Omega
 // (= i Q with Q = (i/2)(Omega^dag - Omega) - (i/6) tr(Omega^dag - Omega)),
 // U' = exp(X) U. Links are periodic in every direction.
@@ -151,37 +144,25 @@ __global__ void __launch_bounds__(128, STOUT_MIN_BLOCKS) k_stout_step(double2 *o
     const long long x = idx >> 2;
     const int mu = (int)(idx & 3);
     const long long xpm = lex_step(g, x, mu, +1);
-    M3 C;
-    if (STOUT_STAPLES_DF64) {
-        M3d Cd;
-        for (int k = 0; k < 9; k++) Cd.a[k] = {df(0.0f, 0.0f), df(0.0f, 0.0f)};
-        for (int nu = 0; nu < 4; nu++) {
-            if (nu == mu) continue;
-            const long long xpn = lex_step(g, x, nu, +1), xmn = lex_step(g, x, nu, -1);
-            const long long xmn_pm = lex_step(g, xmn, mu, +1);
-            // upper staple U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
-            const M3d up = mmul_df(mmul_df(load_link_df(in, x, nu), load_link_df(in, xpn, mu)),
-                                   mdag_df(load_link_df(in, xpm, nu)));
-            // lower staple U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)
-            const M3d lo = mmul_df(mmul_df(mdag_df(load_link_df(in, xmn, nu)), load_link_df(in, xmn, mu)),
-                                   load_link_df(in, xmn_pm, nu));
-            for (int k = 0; k < 9; k++) {
-                Cd.a[k].re = add_lazy(Cd.a[k].re, add_lazy(up.a[k].re, lo.a[k].re));
-                Cd.a[k].im = add_lazy(Cd.a[k].im, add_lazy(up.a[k].im, lo.a[k].im));
-            }
-        }
-        for (int k = 0; k < 9; k++) C.a[k] = {df_to_double(normalise(Cd.a[k].re)), df_to_double(normalise(Cd.a[k].im))};
-    } else {
-        for (int k = 0; k < 9; k++) C.a[k] = {0.0, 0.0};
-        for (int nu = 0; nu < 4; nu++) {
-            if (nu == mu) continue;
-            const long long xpn = lex_step(g, x, nu, +1), xmn = lex_step(g, x, nu, -1);
-            const long long xmn_pm = lex_step(g, xmn, mu, +1);
-            M3 up = mmul(mmul(load_link(in, x, nu), load_link(in, xpn, mu)), mdag(load_link(in, xpm, nu)));
-            M3 lo = mmul(mmul(mdag(load_link(in, xmn, nu)), load_link(in, xmn, mu)), load_link(in, xmn_pm, nu));
-            for (int k = 0; k < 9; k++) C.a[k] = cadd(C.a[k], cadd(up.a[k], lo.a[k]));
+    M3d Cd;
+    for (int k = 0; k < 9; k++) Cd.a[k] = {df(0.0f, 0.0f), df(0.0f, 0.0f)};
+    for (int nu = 0; nu < 4; nu++) {
+        if (nu == mu) continue;
+        const long long xpn = lex_step(g, x, nu, +1), xmn = lex_step(g, x, nu, -1);
+        const long long xmn_pm = lex_step(g, xmn, mu, +1);
+        // upper staple U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
+        const M3d up = mmul_df(mmul_df(load_link_df(in, x, nu), load_link_df(in, xpn, mu)),
+                               mdag_df(load_link_df(in, xpm, nu)));
+        // lower staple U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)
+        const M3d lo = mmul_df(mmul_df(mdag_df(load_link_df(in, xmn, nu)), load_link_df(in, xmn, mu)),
+                               load_link_df(in, xmn_pm, nu));
+        for (int k = 0; k < 9; k++) {
+            Cd.a[k].re = add_lazy(Cd.a[k].re, add_lazy(up.a[k].re, lo.a[k].re));
+            Cd.a[k].im = add_lazy(Cd.a[k].im, add_lazy(up.a[k].im, lo.a[k].im));
         }
     }
+    M3 C;
+    for (int k = 0; k < 9; k++) C.a[k] = {df_to_double(normalise(Cd.a[k].re)), df_to_double(normalise(Cd.a[k].im))};
     const M3 U = load_link(in, x, mu);
     M3 Om = mmul(C, mdag(U));
     M3 X;
@@ -192,7 +173,7 @@ __global__ void __launch_bounds__(128, STOUT_MIN_BLOCKS) k_stout_step(double2 *o
     X.a[0] = csub(X.a[0], tr);
     X.a[4] = csub(X.a[4], tr);
     X.a[8] = csub(X.a[8], tr);
-    const M3 Un = mmul(STOUT_EXP_CAYLEY_HAMILTON ? expm_su3_ch(X) : expm_su3(X), U);
+    const M3 Un = mmul(expm_su3_ch(X), U);
     double2 *p = out + (x * 4 + mu) * 9;
     for (int k = 0; k < 9; k++) p[k] = make_double2(Un.a[k].re, Un.a[k].im);
 }
