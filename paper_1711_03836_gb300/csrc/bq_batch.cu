@@ -447,7 +447,6 @@ int bq_batch_reserve(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int pr) 
     return BQ_OK;
 }
 
-BatchSlot *bq_batch_slot(bq_ctx *c0, int s) { return &c0->batch->slot[s]; }
 void *bq_batch_slot_b(bq_ctx *c0, int s) { return c0->batch->slot[s].b; }
 void *bq_batch_slot_x(bq_ctx *c0, int s) { return c0->batch->slot[s].x; }
 
