@@ -13,9 +13,13 @@ value = algorithmic hopping-term bytes of all launches in the timed solves
 (8 links + in + out spinor per site, plus the clover blocks / x spinor the
 fused epilogues read) / the timed wall time on the device, in GB/s. The line
 also carries the plain FP64 CG time on the same system (the mixed/FP64
-speed-up), a Dslash bandwidth sweep per precision, the roofline of the
-dominant kernel, the CPU oracle baseline and the end-to-end figure through
-the C ABI with host buffers.
+speed-up), the same solve with an FP16 inner iteration, a Dslash bandwidth
+sweep per precision, the roofline of the dominant kernel, the CPU oracle
+baseline, the end-to-end figure through the C ABI with host buffers, and the
+batched and next-row measurements (12 point sources, 10-shift and block
+multishift, ragged lattices, full-lattice BiCGstab / CG, trace samples, stout
+step, clover log det), each against the same work done one system at a time
+where that comparison exists. --mode selects another timed step.
 
 --impl reference times the FP64 CPU oracle (the only reference there is: the
 paper ships no code) on the same lattice, one Mhat^dag Mhat apply per step.
