@@ -653,11 +653,12 @@ def extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, mixed_ms, torch, bqcd):
     bqcd.bq_set_stout(ctx, 0.0, 0)
     _, ms_copy = _timed(torch, lambda: bqcd.bq_get_hop_links(ctx, U_dev))
     del U_dev
+    _, ms_clov = _timed(torch, lambda: bqcd.bq_build_clover(ctx))
     bqcd.bq_clover_logdet(ctx, 1)
     (ld, neg), ms_ld = _timed(torch, lambda: bqcd.bq_clover_logdet(ctx, 1))
     out["gauge_setup"] = {"stout_step_ms": ms_stout - ms_copy, "stout_plus_link_copy_ms": ms_stout,
                           "stout_GB/s_links_in_out": 2 * Vfull * 4 * 144 / ((ms_stout - ms_copy) * 1e-3) / 1e9,
-                          "clover_logdet_odd_ms": ms_ld, "clover_logdet_odd": ld, "negative_blocks": neg}
+                          "clover_build_and_invert_ms": ms_clov, "clover_logdet_odd_ms": ms_ld, "clover_logdet_odd": ld, "negative_blocks": neg}
 
     # ---- batching (row a9) and multishift (row a8), each against the same work done one system at a time
     out["batched"] = batched_extras(torch, bqcd, args.fp64_arith)

@@ -152,9 +152,12 @@ int bq_set_u1(bq_ctx *ctx, const double *A, int where);
 /* Build the clover term A(x) = 1 + i kappa c_SW sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x)
  * (Eq. 2; sigma = (i/2)[gamma_mu,gamma_nu], F = traceless part of (Q - Q^dag)/8,
  * Q = sum of the four plaquette leaves) on the GPU from the SU(3) links, and
- * its inverse on odd sites (FP64, two 6x6 Hermitian blocks per site).
+ * its inverse (FP64, two 6x6 Hermitian blocks per site: A = L D L^dag
+ * without pivoting when every |d_j| is at least 0.1 of the block's largest
+ * entry, else Gauss-Jordan with partial pivoting).
  * Called implicitly by the first operator application after a change.
- * BQ_ERR_CLOVER_SINGULAR if a block has no inverse. */
+ * BQ_ERR_CLOVER_SINGULAR if a block has no inverse (a pivot below 1e-13 of
+ * the block's largest entry). */
 int bq_build_clover(bq_ctx *ctx);
 
 /* How batched solves whose first context is ctx lay right-hand sides of one
@@ -184,8 +187,10 @@ int bq_set_stout(bq_ctx *ctx, double rho, int n_iter);
 int bq_get_hop_links(bq_ctx *ctx, double *U, int where);
 
 /* log det of the clover term (Eq. 2) summed over the sites of one parity:
- * *logdet = sum_x log|det A(x)| in FP64 (LU with partial pivoting of each
- * 6x6 chirality block), *negative (may be NULL) = number of blocks whose
+ * *logdet = sum_x log|det A(x)| in FP64 (per 6x6 chirality block the
+ * product of the pivots of L D L^dag, or of LU with partial pivoting where a
+ * pivot of L D L^dag is below 0.1 of the block's largest entry),
+ * *negative (may be NULL) = number of 6x6 blocks (not sites) whose
  * determinant is negative. For the even-odd preconditioned action the
  * fermion determinant carries det A_oo, i.e. parity 1.
  * BQ_ERR_CLOVER_SINGULAR if a block is singular. */

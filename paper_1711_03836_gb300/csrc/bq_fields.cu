@@ -301,21 +301,29 @@ __device__ void field_strength(const double2 *U, const Geo &g, long long x, int 
     long long xmm = lex_step(g, x, mu, -1), xmn = lex_step(g, x, nu, -1);
     long long xmm_pn = lex_step(g, xmm, nu, +1), xmm_mn = lex_step(g, xmm, nu, -1);
     long long xmn_pm = lex_step(g, xmn, mu, +1);
+    // the four leaves as paths of four links each (site, direction, daggered):
+    //   x -> x+mu -> x+mu+nu -> x+nu -> x,   x -> x+nu -> x+nu-mu -> x-mu -> x,
+    //   x -> x-mu -> x-mu-nu -> x-nu -> x,   x -> x-nu -> x-nu+mu -> x+mu -> x
+    const long long site[16] = {x, xpm, xpn, x, x, xmm_pn, xmm, xmm, xmm, xmm_mn, xmm_mn, xmn, xmn, xmn, xmn_pm, x};
+    const unsigned dir_nu = 0x5a5au;  // bit j: link j points along nu (else mu)
+    const unsigned dag = 0x936cu;     // bit j: link j enters daggered
+    // each leaf multiplied out left to right in double-float (one partial
+    // product and one link live), rounded to FP64 and summed there; the loops
+    // stay rolled so that the sixteen link loads are not all hoisted at once
     M3 Q;
-    // leaf 1: x -> x+mu -> x+mu+nu -> x+nu -> x
-    Q = mmul(mmul(load_link(U, x, mu), load_link(U, xpm, nu)), mmul(mdag(load_link(U, xpn, mu)), mdag(load_link(U, x, nu))));
-    // leaf 2: x -> x+nu -> x+nu-mu -> x-mu -> x
-    M3 t = mmul(mmul(load_link(U, x, nu), mdag(load_link(U, xmm_pn, mu))),
-                mmul(mdag(load_link(U, xmm, nu)), load_link(U, xmm, mu)));
-    for (int k = 0; k < 9; k++) Q.a[k] = cadd(Q.a[k], t.a[k]);
-    // leaf 3: x -> x-mu -> x-mu-nu -> x-nu -> x
-    t = mmul(mmul(mdag(load_link(U, xmm, mu)), mdag(load_link(U, xmm_mn, nu))),
-             mmul(load_link(U, xmm_mn, mu), load_link(U, xmn, nu)));
-    for (int k = 0; k < 9; k++) Q.a[k] = cadd(Q.a[k], t.a[k]);
-    // leaf 4: x -> x-nu -> x-nu+mu -> x+mu -> x
-    t = mmul(mmul(mdag(load_link(U, xmn, nu)), load_link(U, xmn, mu)),
-             mmul(load_link(U, xmn_pm, nu), mdag(load_link(U, x, mu))));
-    for (int k = 0; k < 9; k++) Q.a[k] = cadd(Q.a[k], t.a[k]);
+    for (int k = 0; k < 9; k++) Q.a[k] = {0.0, 0.0};
+#pragma unroll 1
+    for (int l = 0; l < 4; l++) {
+        M3d P = load_link_df(U, site[4 * l], (dir_nu >> (4 * l)) & 1 ? nu : mu);
+        if ((dag >> (4 * l)) & 1) P = mdag_df(P);
+#pragma unroll 1
+        for (int j = 4 * l + 1; j < 4 * l + 4; j++) {
+            const M3d L = load_link_df(U, site[j], (dir_nu >> j) & 1 ? nu : mu);
+            P = (dag >> j) & 1 ? mmul_df(P, mdag_df(L)) : mmul_df(P, L);
+        }
+        for (int k = 0; k < 9; k++)
+            Q.a[k] = cadd(Q.a[k], cplx<double>{df_to_double(P.a[k].re), df_to_double(P.a[k].im)});
+    }
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++) {
             cplx<double> q = Q.a[i * 3 + j], qt = cconj(Q.a[j * 3 + i]);
@@ -331,58 +339,61 @@ __device__ void field_strength(const double2 *U, const Geo &g, long long x, int 
 // E1 = F14 -+ F23 ... the chirality block is 1 + i kc [[E3, E1 - iE2], [E1 + iE2, -E3]]
 // (upper block: E1 = F14 - F23, E2 = F24 + F13, E3 = F34 - F12;
 //  lower block: E1 = -F14 - F23, E2 = -F24 + F13, E3 = -F34 - F12).
-__global__ void k_build_clover(double2 *master, size_t pblk, const double2 *U, Geo g, double kc) {
-    long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// A block of 192 threads covers 32 sites: one warp per plane computes F_{mu nu}
+// of its 32 sites into shared memory, then two threads per site (one per
+// chirality block) assemble and store the blocks.
+#define CLOVER_SITES 32
+__global__ void __launch_bounds__(6 * CLOVER_SITES) k_build_clover(double2 *master, size_t pblk, const double2 *U,
+                                                                   Geo g, double kc) {
+    // planes: 0:(0,1) 1:(0,2) 2:(0,3) 3:(1,2) 4:(1,3) 5:(2,3)
+    __shared__ double2 sF[6][9][CLOVER_SITES];
+    const int lane = threadIdx.x % CLOVER_SITES, pl = threadIdx.x / CLOVER_SITES;
+    const long long x0 = (long long)blockIdx.x * CLOVER_SITES;
+    if (x0 + lane < g.V) {
+        const int mu = pl < 3 ? 0 : (pl < 5 ? 1 : 2);
+        const int nu = pl < 3 ? pl + 1 : (pl < 5 ? pl - 1 : 3);
+        M3 F;
+        field_strength(U, g, x0 + lane, mu, nu, F);
+        for (int k = 0; k < 9; k++) sF[pl][k][lane] = make_double2(F.a[k].re, F.a[k].im);
+    }
+    __syncthreads();
+    if (threadIdx.x >= 2 * CLOVER_SITES) return;
+    const long long x = x0 + lane;
     if (x >= g.V) return;
+    const int b = threadIdx.x / CLOVER_SITES;
     int c[4];
     lex_coords(g, x, c);
-    int par = (c[0] + c[1] + c[2] + c[3]) & 1;
-    int h = (int)(x >> 1);
-    // planes: 0:(0,1) 1:(0,2) 2:(0,3) 3:(1,2) 4:(1,3) 5:(2,3)
-    M3 F[6];
-    int pl = 0;
-    for (int mu = 0; mu < 4; mu++)
-        for (int nu = mu + 1; nu < 4; nu++) field_strength(U, g, x, mu, nu, F[pl++]);
-    double2 *dst = master + (size_t)(par * 2 + 0) * pblk;
-    for (int b = 0; b < 2; b++) {
-        double sg = b == 0 ? 1.0 : -1.0;
-        M3 E1, E2, E3;
-        for (int k = 0; k < 9; k++) {
-            E1.a[k] = csub(cscale(sg, F[2].a[k]), F[3].a[k]);  // +-F14 - F23
-            E2.a[k] = cadd(cscale(sg, F[4].a[k]), F[1].a[k]);  // +-F24 + F13
-            E3.a[k] = csub(cscale(sg, F[5].a[k]), F[0].a[k]);  // +-F34 - F12
+    const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+    const int h = (int)(x >> 1);
+    const double sg = b == 0 ? 1.0 : -1.0;
+    cplx<double> B[36];
+    for (int a = 0; a < 3; a++)
+        for (int bb = 0; bb < 3; bb++) {
+            const int k = a * 3 + bb;
+            const double2 f12 = sF[0][k][lane], f13 = sF[1][k][lane], f14 = sF[2][k][lane];
+            const double2 f23 = sF[3][k][lane], f24 = sF[4][k][lane], f34 = sF[5][k][lane];
+            const cplx<double> e1 = {sg * f14.x - f23.x, sg * f14.y - f23.y};  // +-F14 - F23
+            const cplx<double> e2 = {sg * f24.x + f13.x, sg * f24.y + f13.y};  // +-F24 + F13
+            const cplx<double> e3 = {sg * f34.x - f12.x, sg * f34.y - f12.y};  // +-F34 - F12
+            const double d = (a == bb) ? 1.0 : 0.0;
+            // i kc E3, i kc (E1 - i E2) = i kc E1 + kc E2, i kc (E1 + i E2) = i kc E1 - kc E2, -i kc E3
+            B[(0 + a) * 6 + (0 + bb)] = {d - kc * e3.im, kc * e3.re};
+            B[(0 + a) * 6 + (3 + bb)] = {-kc * e1.im + kc * e2.re, kc * e1.re + kc * e2.im};
+            B[(3 + a) * 6 + (0 + bb)] = {-kc * e1.im - kc * e2.re, kc * e1.re - kc * e2.im};
+            B[(3 + a) * 6 + (3 + bb)] = {d + kc * e3.im, -kc * e3.re};
         }
-        cplx<double> B[36];
-        for (int a = 0; a < 3; a++)
-            for (int bb = 0; bb < 3; bb++) {
-                cplx<double> e1 = E1.a[a * 3 + bb], e2 = E2.a[a * 3 + bb], e3 = E3.a[a * 3 + bb];
-                double d = (a == bb) ? 1.0 : 0.0;
-                // i kc E3, i kc (E1 - i E2) = i kc E1 + kc E2, i kc (E1 + i E2) = i kc E1 - kc E2, -i kc E3
-                B[(0 + a) * 6 + (0 + bb)] = {d - kc * e3.im, kc * e3.re};
-                B[(0 + a) * 6 + (3 + bb)] = {-kc * e1.im + kc * e2.re, kc * e1.re + kc * e2.im};
-                B[(3 + a) * 6 + (0 + bb)] = {-kc * e1.im - kc * e2.re, kc * e1.re - kc * e2.im};
-                B[(3 + a) * 6 + (3 + bb)] = {d + kc * e3.im, -kc * e3.re};
-            }
-        store_herm6(dst, b, h, g.Vh, B);
-    }
+    store_herm6(master + (size_t)(par * 2 + 0) * pblk, b, h, g.Vh, B);
 }
 
-// inverse of each 6x6 block (Gauss-Jordan with partial pivoting, FP64); a block
-// whose pivot falls below 1e-13 of its largest entry is reported as singular
-__global__ void k_invert_clover(double2 *master, size_t pblk, int Vh, int *flag) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= 4 * Vh) return;
-    int h = idx % Vh;
-    int b = (idx / Vh) & 1;
-    int par = idx / (2 * Vh);
-    const double2 *src = master + (size_t)(par * 2 + 0) * pblk;
-    double2 *dst = master + (size_t)(par * 2 + 1) * pblk;
-    cplx<double> a[6][12];
+// Gauss-Jordan inverse with partial pivoting (FP64) of chirality block b of
+// half-site h, read from src and written to dst; false (nothing written) when
+// a pivot falls below 1e-13 of the block's largest entry
+__device__ __noinline__ bool invert6_pivoted(const double2 *src, double2 *dst, int b, int h, int Vh) {
     cplx<double> B[36];
     load_herm6(src, b, h, Vh, B);
-    // numerically singular: a pivot below 1e-13 of the block's largest entry
     double scale = 0.0;
     for (int k = 0; k < 36; k++) scale = fmax(scale, hypot(B[k].re, B[k].im));
+    cplx<double> a[6][12];
     for (int i = 0; i < 6; i++)
         for (int j = 0; j < 6; j++) {
             a[i][j] = B[i * 6 + j];
@@ -398,10 +409,7 @@ __global__ void k_invert_clover(double2 *master, size_t pblk, int Vh, int *flag)
                 piv = r;
             }
         }
-        if (!(best > 1e-13 * scale)) {
-            atomicExch(flag, 1);
-            return;
-        }
+        if (!(best > 1e-13 * scale)) return false;
         if (piv != col)
             for (int j = 0; j < 12; j++) {
                 cplx<double> t = a[col][j];
@@ -418,10 +426,86 @@ __global__ void k_invert_clover(double2 *master, size_t pblk, int Vh, int *flag)
             for (int j = 0; j < 12; j++) a[r][j] = csub(a[r][j], cmul(f, a[col][j]));
         }
     }
-    // the inverse of a Hermitian matrix is Hermitian: keep the diagonal's real part and the upper triangle
     for (int i = 0; i < 6; i++)
         for (int j = 0; j < 6; j++) B[i * 6 + j] = a[i][6 + j];
     store_herm6(dst, b, h, Vh, B);
+    return true;
+}
+
+// inverse of each Hermitian 6x6 block, FP64. Fast path: A = L D L^dag without
+// pivoting (L unit lower triangular, D real), A^-1 = X^dag D^-1 X with X = L^-1,
+// taken when every |d_j| is at least 0.1 of the block's largest entry (all
+// blocks of smooth and moderately rough fields). Otherwise Gauss-Jordan with
+// partial pivoting; a block whose pivot falls below 1e-13 of its largest entry
+// is reported as singular.
+__global__ void k_invert_clover(double2 *master, size_t pblk, int Vh, int *flag) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 4 * Vh) return;
+    int h = idx % Vh;
+    int b = (idx / Vh) & 1;
+    int par = idx / (2 * Vh);
+    const double2 *src = master + (size_t)(par * 2 + 0) * pblk;
+    double2 *dst = master + (size_t)(par * 2 + 1) * pblk;
+    cplx<double> B[36];
+    load_herm6(src, b, h, Vh, B);
+    double scale = 0.0;
+    for (int k = 0; k < 36; k++) scale = fmax(scale, hypot(B[k].re, B[k].im));
+    // L D L^dag; W_ik = L_ik d_k. The loops run over fixed trip counts with
+    // guards, so that they unroll completely and every array stays in registers.
+    cplx<double> L[36], W[36];
+    double dinv[6];
+    bool fast = true;
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+        double dj = B[j * 7].re;
+#pragma unroll
+        for (int k = 0; k < 6; k++)
+            if (k < j) dj -= W[j * 6 + k].re * L[j * 6 + k].re + W[j * 6 + k].im * L[j * 6 + k].im;
+        fast = fast && fabs(dj) >= 0.1 * scale;
+        dinv[j] = 1.0 / dj;
+#pragma unroll
+        for (int i = 0; i < 6; i++)
+            if (i > j) {
+                cplx<double> t = B[i * 6 + j];
+#pragma unroll
+                for (int k = 0; k < 6; k++)
+                    if (k < j) t = csub(t, cmul(W[i * 6 + k], cconj(L[j * 6 + k])));
+                W[i * 6 + j] = t;
+                L[i * 6 + j] = cscale(dinv[j], t);
+            }
+    }
+    if (!fast) {
+        if (!invert6_pivoted(src, dst, b, h, Vh)) atomicExch(flag, 1);
+        return;
+    }
+    // X = L^-1, unit lower triangular: X_ij = -L_ij - sum_{j<k<i} L_ik X_kj
+    cplx<double> X[36];
+#pragma unroll
+    for (int j = 0; j < 6; j++)
+#pragma unroll
+        for (int i = 0; i < 6; i++)
+            if (i > j) {
+                cplx<double> t = cscale(-1.0, L[i * 6 + j]);
+#pragma unroll
+                for (int k = 0; k < 6; k++)
+                    if (k > j && k < i) t = csub(t, cmul(L[i * 6 + k], X[k * 6 + j]));
+                X[i * 6 + j] = t;
+            }
+    // (A^-1)_ij = sum_{k >= max(i,j)} conj(X_ki) X_kj / d_k (X_kk = 1), upper triangle and diagonal
+    cplx<double> Binv[36];
+#pragma unroll
+    for (int i = 0; i < 6; i++)
+#pragma unroll
+        for (int j = 0; j < 6; j++)
+            if (j >= i) {
+                cplx<double> t = i == j ? cplx<double>{dinv[j], 0.0} : cscale(dinv[j], cconj(X[j * 6 + i]));
+#pragma unroll
+                for (int k = 0; k < 6; k++)
+                    if (k > j) t = cadd(t, cscale(dinv[k], cmul(cconj(X[k * 6 + i]), X[k * 6 + j])));
+                Binv[i * 6 + j] = t;
+            }
+    // the inverse of a Hermitian matrix is Hermitian: keep the diagonal's real part and the upper triangle
+    store_herm6(dst, b, h, Vh, Binv);
 }
 
 template <int PREC>
@@ -469,8 +553,9 @@ extern "C" int bq_build_clover(bq_ctx *c) {
     BQ_TRY(bq_alloc((void **)&c->clov_master, sizeof(double2) * pblk * 4));
     Geo g = geo_of(c);
     BQ_CUDA_TRY(cudaMemsetAsync(c->dev_flag, 0, sizeof(int), c->stream));
-    k_build_clover<<<grid_for(c->V, 64), 64, 0, c->stream>>>((double2 *)c->clov_master, pblk, c->U_canon, g,
-                                                               c->params.kappa * c->params.csw);
+    const unsigned nblk = (unsigned)((c->V + CLOVER_SITES - 1) / CLOVER_SITES);
+    k_build_clover<<<nblk, 6 * CLOVER_SITES, 0, c->stream>>>((double2 *)c->clov_master, pblk, c->U_canon, g,
+                                                             c->params.kappa * c->params.csw);
     BQ_LAUNCH_CHECK();
     BQ_COUNT(c);
     k_invert_clover<<<grid_for(4LL * c->Vh, 64), 64, 0, c->stream>>>((double2 *)c->clov_master, pblk, c->Vh,

@@ -87,46 +87,6 @@ __device__ M3 expm_su3_ch(const M3 &X) {
     return E;
 }
 
-// the staple products in double-float (links split exactly into float pairs,
-// each matrix entry a lazy sum of six products): GB300 runs FP32 at ~60x its
-// FP64 rate, and the twelve staple products are most of a stout step's work
-struct M3d {
-    cplx<df> a[9];
-};
-__device__ __forceinline__ M3d load_link_df(const double2 *U, long long lex, int mu) {
-    M3d m;
-    const double2 *p = U + (lex * 4 + mu) * 9;
-    for (int k = 0; k < 9; k++) {
-        const double2 v = p[k];
-        m.a[k] = {df_from_double(v.x), df_from_double(v.y)};
-    }
-    return m;
-}
-__device__ __forceinline__ M3d mdag_df(const M3d &x) {
-    M3d m;
-    for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 3; j++) m.a[i * 3 + j] = {x.a[j * 3 + i].re, -x.a[j * 3 + i].im};
-    return m;
-}
-__device__ M3d mmul_df(const M3d &x, const M3d &y) {
-    M3d m;
-    for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 3; j++) {
-            dfsum re = dfs_prod(x.a[i * 3].re, y.a[j].re), im = dfs_prod(x.a[i * 3].re, y.a[j].im);
-            dfs_add_prod(re, -x.a[i * 3].im, y.a[j].im);
-            dfs_add_prod(im, x.a[i * 3].im, y.a[j].re);
-            for (int k = 1; k < 3; k++) {
-                const cplx<df> p = x.a[i * 3 + k], q = y.a[k * 3 + j];
-                dfs_add_prod(re, p.re, q.re);
-                dfs_add_prod(re, -p.im, q.im);
-                dfs_add_prod(im, p.re, q.im);
-                dfs_add_prod(im, p.im, q.re);
-            }
-            m.a[i * 3 + j] = {dfs_done(re), dfs_done(im)};
-        }
-    return m;
-}
-
 // one stout step for every link: C = rho sum_{nu != mu} (upper + lower staple)
 // (staple products in double-float, the rest in FP64),
 // Omega = C U^dag, X = traceless anti-Hermitian part of Omega
@@ -245,11 +205,58 @@ extern "C" int bq_get_hop_links(bq_ctx *c, double *U, int where) {
 }
 
 // --------------------------------------------------------------------------
-// log det of the clover term on one parity: per site and chirality block, LU
-// with partial pivoting of the 6x6 block in FP64; log|det| = sum log|pivot|,
-// and the block's determinant sign (real for a Hermitian block) from the
-// pivots' phases and the row swaps. Sums: [0] log|det|, [1] blocks with det < 0.
+// log det of the clover term on one parity, per site and chirality block, in
+// FP64. Sums: [0] log|det|, [1] blocks with det < 0.
 
+// LU with partial pivoting of chirality block b of half-site h: log|det| =
+// sum log|pivot|, the sign (real for a Hermitian block) from the pivots'
+// phases and the row swaps; -inf for a zero pivot
+__device__ __noinline__ double logdet6_pivoted(const double2 *blk, int b, int h, int Vh, bool *negative) {
+    cplx<double> B[36];
+    load_herm6(blk, b, h, Vh, B);
+    double la = 0.0;
+    cplx<double> ph = {1.0, 0.0};
+    int swaps = 0;
+    for (int col = 0; col < 6; col++) {
+        int piv = col;
+        double best = hypot(B[col * 6 + col].re, B[col * 6 + col].im);
+        for (int r = col + 1; r < 6; r++) {
+            const double m = hypot(B[r * 6 + col].re, B[r * 6 + col].im);
+            if (m > best) {
+                best = m;
+                piv = r;
+            }
+        }
+        if (!(best > 0.0)) {
+            *negative = false;
+            return -INFINITY;
+        }
+        if (piv != col) {
+            swaps++;
+            for (int j = 0; j < 6; j++) {
+                const cplx<double> t = B[col * 6 + j];
+                B[col * 6 + j] = B[piv * 6 + j];
+                B[piv * 6 + j] = t;
+            }
+        }
+        const cplx<double> p = B[col * 6 + col];
+        la += log(best);
+        ph = cmul(ph, cplx<double>{p.re / best, p.im / best});
+        const double n2 = p.re * p.re + p.im * p.im;
+        const cplx<double> inv = {p.re / n2, -p.im / n2};
+        for (int r = col + 1; r < 6; r++) {
+            const cplx<double> f = cmul(B[r * 6 + col], inv);
+            for (int j = col; j < 6; j++) B[r * 6 + j] = csub(B[r * 6 + j], cmul(f, B[col * 6 + j]));
+        }
+    }
+    *negative = ((swaps & 1) ? -ph.re : ph.re) < 0.0;
+    return la;
+}
+
+// Fast path: A = L D L^dag without pivoting (D real), det A = prod d_j, taken
+// when every |d_j| is at least 0.1 of the block's largest entry; otherwise the
+// pivoted LU above. Loops of fixed trip count with guards unroll completely,
+// so that the block stays in registers.
 __global__ void __launch_bounds__(RED_THREADS) k_clover_logdet(const double2 *blk, int Vh, double *partials,
                                                                unsigned int *ticket, double *out) {
     double v[2] = {0.0, 0.0};
@@ -257,44 +264,41 @@ __global__ void __launch_bounds__(RED_THREADS) k_clover_logdet(const double2 *bl
         const int h = idx % Vh, b = idx / Vh;
         cplx<double> B[36];
         load_herm6(blk, b, h, Vh, B);
-        double la = 0.0;
-        cplx<double> ph = {1.0, 0.0};
-        int swaps = 0;
-        for (int col = 0; col < 6; col++) {
-            int piv = col;
-            double best = hypot(B[col * 6 + col].re, B[col * 6 + col].im);
-            for (int r = col + 1; r < 6; r++) {
-                const double m = hypot(B[r * 6 + col].re, B[r * 6 + col].im);
-                if (m > best) {
-                    best = m;
-                    piv = r;
+        double scale = 0.0;
+        for (int k = 0; k < 36; k++) scale = fmax(scale, hypot(B[k].re, B[k].im));
+        cplx<double> L[36], W[36];  // W_ik = L_ik d_k
+        double det = 1.0;
+        bool fast = true;
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+            double dj = B[j * 7].re;
+#pragma unroll
+            for (int k = 0; k < 6; k++)
+                if (k < j) dj -= W[j * 6 + k].re * L[j * 6 + k].re + W[j * 6 + k].im * L[j * 6 + k].im;
+            fast = fast && fabs(dj) >= 0.1 * scale;
+            det *= dj;
+            const double dinv = 1.0 / dj;
+#pragma unroll
+            for (int i = 0; i < 6; i++)
+                if (i > j) {
+                    cplx<double> t = B[i * 6 + j];
+#pragma unroll
+                    for (int k = 0; k < 6; k++)
+                        if (k < j) t = csub(t, cmul(W[i * 6 + k], cconj(L[j * 6 + k])));
+                    W[i * 6 + j] = t;
+                    L[i * 6 + j] = cscale(dinv, t);
                 }
-            }
-            if (!(best > 0.0)) {
-                la = -INFINITY;
-                break;
-            }
-            if (piv != col) {
-                swaps++;
-                for (int j = 0; j < 6; j++) {
-                    const cplx<double> t = B[col * 6 + j];
-                    B[col * 6 + j] = B[piv * 6 + j];
-                    B[piv * 6 + j] = t;
-                }
-            }
-            const cplx<double> p = B[col * 6 + col];
-            la += log(best);
-            ph = cmul(ph, cplx<double>{p.re / best, p.im / best});
-            const double n2 = p.re * p.re + p.im * p.im;
-            const cplx<double> inv = {p.re / n2, -p.im / n2};
-            for (int r = col + 1; r < 6; r++) {
-                const cplx<double> f = cmul(B[r * 6 + col], inv);
-                for (int j = col; j < 6; j++) B[r * 6 + j] = csub(B[r * 6 + j], cmul(f, B[col * 6 + j]));
-            }
         }
-        const double sg = (swaps & 1) ? -ph.re : ph.re;
+        bool neg;
+        double la;
+        if (fast) {
+            la = log(fabs(det));
+            neg = det < 0.0;
+        } else {
+            la = logdet6_pivoted(blk, b, h, Vh, &neg);
+        }
         v[0] += la;
-        v[1] += (sg < 0.0) ? 1.0 : 0.0;
+        v[1] += neg ? 1.0 : 0.0;
     }
     double tot[2];
     if (grid_sum(v, partials, ticket, tot) && threadIdx.x == 0) {

@@ -91,3 +91,45 @@ __device__ __forceinline__ void load_herm6(const double2 *blk, int b, int h, int
         }
 }
 
+
+// 3x3 complex matrices in double-float (links split exactly into float pairs,
+// each product entry a lazy sum of six products): GB300 runs FP32 at ~60x its
+// FP64 rate, and the staple and clover-leaf products are most of the work of
+// a stout step and of the clover build
+struct M3d {
+    cplx<df> a[9];
+};
+__device__ __forceinline__ M3d load_link_df(const double2 *U, long long lex, int mu) {
+    M3d m;
+    const double2 *p = U + (lex * 4 + mu) * 9;
+    for (int k = 0; k < 9; k++) {
+        const double2 v = p[k];
+        m.a[k] = {df_from_double(v.x), df_from_double(v.y)};
+    }
+    return m;
+}
+__device__ __forceinline__ M3d mdag_df(const M3d &x) {
+    M3d m;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) m.a[i * 3 + j] = {x.a[j * 3 + i].re, -x.a[j * 3 + i].im};
+    return m;
+}
+__device__ inline M3d mmul_df(const M3d &x, const M3d &y) {
+    M3d m;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            dfsum re = dfs_prod(x.a[i * 3].re, y.a[j].re), im = dfs_prod(x.a[i * 3].re, y.a[j].im);
+            dfs_add_prod(re, -x.a[i * 3].im, y.a[j].im);
+            dfs_add_prod(im, x.a[i * 3].im, y.a[j].re);
+            for (int k = 1; k < 3; k++) {
+                const cplx<df> p = x.a[i * 3 + k], q = y.a[k * 3 + j];
+                dfs_add_prod(re, p.re, q.re);
+                dfs_add_prod(re, -p.im, q.im);
+                dfs_add_prod(im, p.re, q.im);
+                dfs_add_prod(im, p.im, q.re);
+            }
+            m.a[i * 3 + j] = {dfs_done(re), dfs_done(im)};
+        }
+    return m;
+}
+

@@ -86,6 +86,24 @@ def test_clover_parity(bq, prec):
     lat.close()
 
 
+@pytest.mark.parametrize("dims", [(6, 6, 6, 6), (6, 6, 6, 10)])
+def test_clover_build_ragged_tail(bq, dims):
+    """The clover build covers 32 sites per block (one warp per mu-nu plane);
+    V = 1296 and 2160 leave a partly filled last block."""
+    lat, U, A, p = make(bq, dims)
+    assert lat.Vh * 2 % 32 != 0
+    psi = synth.gaussian_spinor(lat.Vh, 6)
+    src = lat.pack(psi, "double")
+    out = lat.spinor("double")
+    for par in (0, 1):
+        Am = oracle.clover_field(p, U, par)
+        for inv in (False, True):
+            bq.bq_apply_clover(lat.ctx, out, src, par, inv, "double")
+            ref = oracle.clover_apply(oracle.clover_invert(Am) if inv else Am, psi)
+            assert rel(lat.unpack(out, "double"), ref) < TOL["double"], (par, inv)
+    lat.close()
+
+
 @pytest.mark.parametrize("prec,recon,mu,charge", CASES)
 def test_mhat_parity(bq, prec, recon, mu, charge):
     dims = (6, 4, 6, 10)
@@ -578,6 +596,35 @@ def test_clover_logdet_parity(bq, dims, eps):
         ld_o, neg_o = oracle.clover_logdet(p, U, par)
         assert abs(ld - ld_o) <= 1e-12 * max(1.0, abs(ld_o)) + 1e-10, (ld, ld_o)
         assert neg == neg_o == 0
+    lat.close()
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_clover_rough_field_both_paths(bq, seed):
+    """A rough field (eps 2) with kappa c_SW = 1: about a quarter of the 6x6
+    blocks have an LDL^dag pivot below 0.1 of their largest entry and take the
+    pivoted fallback of the inverse and of the log det, the rest the unpivoted
+    fast path; most blocks have det < 0. The blocks' condition
+    numbers reach 1e5, so the inverse is held to 1e-10 (1e5 x FP64 unit
+    roundoff, with a factor 10 for the elimination's growth)."""
+    dims = (6, 4, 6, 10)
+    lat, U, A, p = make(bq, dims, kappa=0.25, csw=4.0, eps=2.0, seed=seed)
+    psi = synth.gaussian_spinor(lat.Vh, 7)
+    src = lat.pack(psi, "double")
+    out = lat.spinor("double")
+    for par in (0, 1):
+        Am = oracle.clover_field(p, U, par)
+        bq.bq_apply_clover(lat.ctx, out, src, par, True, "double")
+        assert rel(lat.unpack(out, "double"), oracle.clover_apply(oracle.clover_invert(Am), psi)) < 1e-10, par
+        ld, neg = bq.bq_clover_logdet(lat.ctx, par)
+        ld_o, neg_sites = oracle.clover_logdet(p, U, par)
+        assert abs(ld - ld_o) <= 1e-12 * abs(ld_o), (ld, ld_o)
+        # the library counts 6x6 chirality blocks with det < 0, the oracle 12x12 sites;
+        # count the blocks of the oracle's clover matrices, and the sign of det A agrees
+        neg_blocks = sum(int(np.sum(np.linalg.slogdet(Am[:, 6 * b:6 * b + 6, 6 * b:6 * b + 6])[0].real < 0))
+                         for b in (0, 1))
+        assert neg == neg_blocks and neg_blocks > 1000, (neg, neg_blocks)
+        assert neg % 2 == neg_sites % 2
     lat.close()
 
 
