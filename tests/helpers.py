@@ -109,3 +109,13 @@ def abelian_background(dims, mu, nu, m, c, dep_on):
         U[:, mu] = 0
         U[:, mu, [0, 1, 2], [0, 1, 2]] = ph
     return U, phi
+
+
+def two_plane_background(dims, c12, c34, m):
+    """Constant abelian field strength in the planes (0,1) and (2,3) at once:
+    U_1(x) = diag(exp(i phi c12_a x_0)), U_3(x) = diag(exp(i phi' c34_a x_2)),
+    every other link 1. Every plaquette of the other four planes is 1."""
+    U, phi = abelian_background(dims, 0, 1, m, c12, "mu")
+    U34, phi34 = abelian_background(dims, 2, 3, m, c34, "mu")
+    U[:, 3] = U34[:, 3]
+    return U, phi, phi34

@@ -599,6 +599,32 @@ def test_clover_logdet_parity(bq, dims, eps):
     lat.close()
 
 
+def test_clover_logdet_two_planes_closed_form(bq):
+    """Constant abelian fields in the planes 12 and 34 with g = g' =
+    (2/3, -1/3, -1/3) and kappa c_SW = 1: per site one chirality block has
+    det 1 and the other prod_a (1 - (2 kc g_a)^2) < 0 (the two blocks hold the
+    sigma sign pairs (s, s') and (s, -s')), so every site contributes one
+    negative block and log|det A(x)| = log|prod_a (1 - 4 kc^2 g_a^2)|."""
+    from helpers import two_plane_background
+
+    dims = (4, 4, 4, 6)
+    c = (1.0, 0.0, 0.0)
+    U, phi, _ = two_plane_background(dims, c, c, 1)
+    kc = 1.0
+    g = np.sin(phi * np.array(c))
+    g -= g.mean()
+    det_site = np.prod(1 - 4 * kc ** 2 * g ** 2)
+    assert det_site < 0
+    lat = bq.Lattice(dims, 0.25, 4.0, 0.0, -1.0, 0.0)
+    bq.bq_set_gauge(lat.ctx, U)
+    n = lat.Vh
+    for par in (0, 1):
+        ld, neg = bq.bq_clover_logdet(lat.ctx, par)
+        assert abs(ld - n * np.log(abs(det_site))) < 1e-12 * n, (ld, n * np.log(abs(det_site)))
+        assert neg == n
+    lat.close()
+
+
 @pytest.mark.parametrize("seed", [1, 2])
 def test_clover_rough_field_both_paths(bq, seed):
     """A rough field (eps 2) with kappa c_SW = 1: about a quarter of the 6x6

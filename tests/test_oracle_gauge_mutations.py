@@ -3,7 +3,8 @@ adjoint solve, trace samples, clover log det) have teeth: each plausible
 mistake planted in a copy of the oracle's Python source (a mis-oriented
 staple, Omega without U^dag, a lost trace term, the exponential's sign, the
 sign of the hopping term in M, a non-adjoint hop in the adjoint solve, a wrong
-gamma_5, |x|^2 instead of |y|^2, a halved log det) is caught by at least one
+gamma_5, |x|^2 instead of |y|^2, a halved log det, positive determinants
+counted as negative) is caught by at least one
 pin of tests/test_oracle_gauge_pins.py or tests/test_oracle_pins.py. Mistakes
 are planted in the oracle on the CPU only."""
 import types
@@ -32,12 +33,14 @@ MUTATIONS = {
                         "s3 = np.vdot(x_e, x_e).real + np.vdot(x_o, x_o).real"),
     "half the log det": ("return float(np.sum(ld)), int(np.sum(sign.real < 0))",
                          "return float(np.sum(ld)) / 2, int(np.sum(sign.real < 0))"),
+    "positive determinants counted": ("int(np.sum(sign.real < 0))", "int(np.sum(sign.real > 0))"),
 }
 
 PIN_CALLS = [
     lambda: gpins.test_stout_abelian_closed_form(0.1),
     lambda: gpins.test_stout_gauge_covariance_and_group(),
     lambda: gpins.test_clover_logdet_closed_form(),
+    lambda: gpins.test_clover_logdet_two_planes_negative(),
     lambda: gpins.test_trace_samples_sum_to_dense_traces(0.2, 2.0 / 3.0),
     lambda: pins.test_free_field_full_operator(0.15, 0.11),
 ]

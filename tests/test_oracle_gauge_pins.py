@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 from paper_1711_03836_gb300 import synth
-from helpers import abelian_background, gauge_transform
+from helpers import abelian_background, gauge_transform, two_plane_background
 
 
 def _neighbour(dims, mu, d):
@@ -94,6 +94,37 @@ def test_clover_logdet_closed_form():
         assert neg == 0
     ld0, _ = oracle.clover_logdet(oracle.params(dims, kappa=kappa, csw=0.0), synth.gauge_field(dims, 0.3, 1), 0)
     assert ld0 == 0.0
+
+
+def test_clover_logdet_two_planes_negative():
+    """F_12 = i diag(g_a), F_34 = i diag(g'_a) commute, and so do sigma_12 and
+    sigma_34 (eigenvalues +-1 each, every sign pair once per colour), so the 12x12
+    clover matrix has eigenvalues 1 - kc (s g_a + s' g'_a) and
+    det A(x) = prod_a (1 - kc^2 (g_a + g'_a)^2) (1 - kc^2 (g_a - g'_a)^2),
+    independent of the gamma basis. With g = g' = (2/3, -1/3, -1/3) and kc = 1
+    exactly one factor is negative: every site has det A(x) < 0."""
+    dims = (4, 4, 4, 6)
+    c = (1.0, 0.0, 0.0)
+    U, phi, phi34 = two_plane_background(dims, c, c, 1)
+    assert abs(phi - np.pi / 2) < 1e-15 and abs(phi34 - np.pi / 2) < 1e-15
+    kappa, csw = 0.25, 4.0
+    kc = kappa * csw
+    g = np.sin(phi * np.array(c))
+    g -= g.mean()
+    gp = np.sin(phi34 * np.array(c))
+    gp -= gp.mean()
+    det_site = np.prod((1 - kc ** 2 * (g + gp) ** 2) * (1 - kc ** 2 * (g - gp) ** 2))
+    assert det_site < 0
+    p_ = oracle.params(dims, kappa=kappa, csw=csw)
+    for par in (0, 1):
+        ld, neg = oracle.clover_logdet(p_, U, par)
+        n = synth.volume(dims) // 2
+        assert abs(ld - n * np.log(abs(det_site))) < 1e-12 * n
+        assert neg == n
+    # a positive case of the same form: kc = 0.5 leaves every factor positive
+    ld, neg = oracle.clover_logdet(oracle.params(dims, kappa=0.125, csw=4.0), U, 0)
+    det_pos = np.prod((1 - 0.25 * (g + gp) ** 2) * (1 - 0.25 * (g - gp) ** 2))
+    assert neg == 0 and abs(ld - synth.volume(dims) // 2 * np.log(det_pos)) < 1e-12 * synth.volume(dims)
 
 
 # ---------------------------------------------------------------- stochastic traces
