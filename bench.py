@@ -60,7 +60,7 @@ EPI_NAMES = ["dhop", "dhop_clovinv", "dhop_xpay"]
 
 
 def link_b(prec, recon):
-    return (12 if recon == 12 else 18) * {0: 8, 1: 4, 2: 2}[prec]
+    return recon * {0: 8, 1: 4, 2: 2}[prec]
 
 
 def mdagm_bytes(prec, recon, Vh):
@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--fp64-arith", default="df64", choices=["native", "df64"],
                     help="arithmetic of the FP64-storage operator kernels")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 CG, sweep, e2e and CPU baseline")
+    ap.add_argument("--batch-mapping", type=int, default=0,
+                    help="right-hand-side mapping of the batched modes (0 = autotuned; see bq_set_batch_mapping)")
     ap.add_argument("--mode", default="cg", choices=["cg", "batch12", "multishift10", "ragged4", "qed2x4",
                                                      "blockms4x10", "full_cg", "traces8"],
                     help="the timed step: one mixed CG solve (default), 12 point sources in one batched "
@@ -151,7 +153,7 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ traffic from the committed ncu summary
 
-KERNEL_SOURCES = ("bq_dslash.cu", "bq_internal.cuh")  # the files that define k_dslash
+KERNEL_SOURCES = ("bq_device.cuh", "bq_stencil.cuh")  # the files that define k_dslash
 
 
 def kernel_source_hash():
@@ -192,7 +194,8 @@ def oracle_setup(wl):
     return op, b, Vh
 
 
-def oracle_gbs(op, b, Vh, steps, warmup):
+def oracle_gbs(op, b, Vh, steps, warmup, median=False):
+    """(GB/s, seconds) of the oracle's Mhat^dag Mhat: the mean over `steps` applies, or their median."""
     for _ in range(warmup):
         op.mdagm(b)
     ts = []
@@ -200,8 +203,8 @@ def oracle_gbs(op, b, Vh, steps, warmup):
         t0 = time.perf_counter()
         op.mdagm(b)
         ts.append(time.perf_counter() - t0)
-    total = sum(ts)
-    return mdagm_bytes(0, 18, Vh) * steps / total / 1e9, total / steps
+    t = statistics.median(ts) if median else sum(ts) / steps
+    return mdagm_bytes(0, 18, Vh) / t / 1e9, t
 
 
 def run_reference(args):
@@ -285,6 +288,7 @@ def main():
     delta = args.delta if args.delta is not None else {"single": 1e-3, "half": 1e-1, "double": 0.0}[args.inner]
     solve_kw = dict(tol=1e-10, precision=args.inner, delta=delta, check_every=args.check_every, max_iter=20000)
 
+    bqcd.bq_set_batch_mapping(ctx, args.batch_mapping)
     step, extra_ctxs = make_step(args, torch, bqcd, synth, lat, b_dev, x_dev, solve_kw, field_inputs)
     del field_inputs, U, A
     for _ in range(max(args.warmup, 0)):
@@ -349,6 +353,8 @@ def main():
         "solve": summarize(stats[-1]),
     }
     if args.mode != "cg":
+        line["config"]["batch_mapping"] = bqcd.bq_get_batch_mapping(ctx)
+    if args.mode != "cg":
         line["config"]["workload"] = f"{args.mode} on " + line["config"]["workload"]
 
     for l in extra_ctxs:
@@ -363,7 +369,39 @@ def main():
     return 0
 
 
-FP64_PEAK_GFLOPS = 1250.0
+FP64_NOMINAL_GFLOPS = 1250.0
+
+
+def measured_fp64_peak():
+    """Sustained FP64 FMA rate of this GPU (GFLOP/s) from the DFMA-chain probe
+    (paper_1711_03836_gb300/probe/bq_probe.cu), or the nominal 1.25 TFLOP/s."""
+    import ctypes
+
+    from paper_1711_03836_gb300 import build as cuda_build
+
+    try:
+        lib = ctypes.CDLL(cuda_build.build_probe())
+        v = ctypes.c_double()
+        if lib.bq_probe_dfma_gflops(5, ctypes.byref(v)) == 0 and v.value > 0:
+            return v.value, "measured (DFMA-chain probe, best of 5 launches)"
+    except Exception as e:  # the probe is a measurement aid; the bench still runs without it
+        return FP64_NOMINAL_GFLOPS, f"nominal (probe failed: {e})"
+    return FP64_NOMINAL_GFLOPS, "nominal (probe failed)"
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
 
 
 def _timed(torch, fn):
@@ -391,11 +429,13 @@ def batched_extras(torch, bqcd, fp64_arith):
     xs = [torch.empty_like(b) for b in srcs]
     bqcd.bq_solve_cg_batch([lat.ctx] * 12, xs, srcs, **kw)  # warm
     st_b, ms_b = _timed(torch, lambda: bqcd.bq_solve_cg_batch([lat.ctx] * 12, xs, srcs, **kw))
+    mapping_b = bqcd.bq_get_batch_mapping(lat.ctx)
     st_s, ms_s = _timed(torch, lambda: [bqcd.bq_solve_cg(lat.ctx, x, b, **kw) for x, b in zip(xs, srcs)])
     out["point_sources_12_24^3x48"] = {
         "batched_ms": ms_b, "sequential_ms": ms_s, "speedup": ms_s / ms_b,
         "max_true_residual": max(s_["true_residual"] for s_ in st_b),
-        "iterations_max": max(s_["iterations"] for s_ in st_b)}
+        "iterations_max": max(s_["iterations"] for s_ in st_b), "mapping": mapping_b}
+    out["batched_apply_12_24^3x48"] = batched_apply_roofline(torch, bqcd, lat)
     # RHMC multishift: 10 shifts geometric over [1e-4, 1] vs 10 separate CG solves
     b = torch.from_numpy(synth.gaussian_spinor(lat.Vh, 77)).cuda()
     shifts = [10.0 ** (-4 + 4 * k / 9) for k in range(10)]
@@ -440,6 +480,40 @@ def batched_extras(torch, bqcd, fp64_arith):
     for l in lats:
         l.close()
     return out
+
+
+def batched_apply_roofline(torch, bqcd, lat, nrhs=12, reps=10):
+    """The batched hopping-term kernels alone: Mhat^dag Mhat of nrhs Gaussian
+    sources in one bq_apply_mdagm_batch call (FP32, 12-real links), CUDA events
+    around every launch, for each right-hand-side mapping. Algorithmic bytes per
+    launch: links and clover once per site of a unit, spinors per right-hand side."""
+    from paper_1711_03836_gb300 import synth
+
+    peak, _ = measured_peaks()
+    ins = [lat.pack(synth.gaussian_spinor(lat.Vh, 1200 + i), "single") for i in range(nrhs)]
+    outs = [lat.spinor("single") for _ in range(nrhs)]
+    res = {"peak_GB/s": peak}
+    names = {-3: "tile_4_blocks", -4: "tile_5_blocks", -5: "tile_6_blocks", -1: "block_interleaved",
+             -2: "warp_per_rhs", 4: "warp_interleaved_4"}
+    for mapping in (-3, -4, -5, -1, -2, 4):
+        bqcd.bq_set_batch_mapping(lat.ctx, mapping)
+        for _ in range(3):
+            bqcd.bq_apply_mdagm_batch([lat.ctx] * nrhs, outs, ins, "single")
+        bqcd.bq_reset_counters(lat.ctx, timing=True)
+        for _ in range(reps):
+            bqcd.bq_apply_mdagm_batch([lat.ctx] * nrhs, outs, ins, "single")
+        c = bqcd.bq_get_counters(lat.ctx)
+        r = {}
+        for epi, en in ((1, "dhop_clovinv"), (2, "dhop_xpay")):
+            n = c["dslash_launches"][1][epi]
+            ms = c["dslash_ms"][1][epi] / max(n, 1)
+            gbs = c["dslash_bytes"][1][epi] / max(n, 1) / (ms * 1e-3) / 1e9
+            r[en] = {"us_per_launch": ms * 1e3, "GB/s": gbs, "frac": gbs / peak,
+                     "bytes_per_launch": c["dslash_bytes"][1][epi] / max(n, 1)}
+        r["mdagm_us"] = 2 * (r["dhop_clovinv"]["us_per_launch"] + r["dhop_xpay"]["us_per_launch"])
+        res[names[mapping]] = r
+    bqcd.bq_set_batch_mapping(lat.ctx, 0)
+    return res
 
 
 def full_system_extras(torch, bqcd, fp64_arith):
@@ -612,7 +686,8 @@ def extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, mixed_ms, torch, bqcd):
     # ---- hopping-term bandwidth sweep (plain D_hop, inputs larger than L2)
     sweep = {}
     for prec, recon, arith in (("double", 18, "native"), ("double", 12, "native"), ("double", 18, "df64"),
-                               ("single", 18, None), ("single", 12, None), ("half", 18, None), ("half", 12, None)):
+                               ("single", 18, None), ("single", 12, None), ("single", 8, None),
+                               ("half", 18, None), ("half", 12, None), ("half", 8, None)):
         bqcd.bq_set_recon(ctx, prec, recon)
         if arith:
             bqcd.bq_set_fp64_arith(ctx, arith)
@@ -637,10 +712,16 @@ def extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, mixed_ms, torch, bqcd):
     bqcd.bq_set_recon(ctx, "half", 12)
     out["dslash_sweep"] = sweep
 
+    fp64_peak, fp64_src = measured_fp64_peak()
+    hbm_peak, _ = measured_peaks()
+    out["fp64_peak"] = {"GFLOP/s": fp64_peak, "source": fp64_src}
     for k, v in sweep.items():
-        if k.startswith("double") and k.endswith("native"):
-            # native FP64 is bound by the FP64 units: 1.25 TFLOP/s nominal on GB300
-            v["frac_of_fp64_alu_1250"] = v["GFLOP/s"] / FP64_PEAK_GFLOPS
+        if k.startswith("double"):
+            # 1320 flops per 1536 (r18) / 1152 (r12) bytes: at the HBM peak that would need
+            # 5.8 / 7.8 TFLOP/s, so min(HBM, FP64) binds at the FP64 rate for the FP64 units
+            bound = min(hbm_peak, fp64_peak * v["GB/s"] / max(v["GFLOP/s"], 1e-9))
+            v["frac_of_min_hbm_fp64"] = v["GB/s"] / bound
+            v["frac_of_fp64_peak"] = v["GFLOP/s"] / fp64_peak
 
     # ---- gauge-side setup: one stout step of every link, clover log det of each parity
     Vfull = 2 * Vh
@@ -664,16 +745,123 @@ def extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, mixed_ms, torch, bqcd):
     out["batched"] = batched_extras(torch, bqcd, args.fp64_arith)
     out.update(full_system_extras(torch, bqcd, args.fp64_arith))
 
-    # ---- CPU oracle on the host cores (bounded sample: 2 Mhat^dag Mhat applies)
+    # ---- the configuration-2 lattice (16^3x32, mu = 0 and 0.1): fields fit in L2
+    out["config2_16^3x32"] = config2_extras(torch, bqcd, args.fp64_arith)
+
+    # ---- CPU oracle on the host cores: median of 5 Mhat^dag Mhat applies on the workload
+    # lattice, and the oracle's D_hop and CG on configurations 1 and 2
     import oracle
 
     wl = WORKLOADS[args.workload]
     op, bb, Vh_o = oracle_setup(wl)
-    gbs, t_step = oracle_gbs(op, bb, Vh_o, 2, 1)
+    gbs, t_step = oracle_gbs(op, bb, Vh_o, 5, 1, median=True)
     out["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": oracle.num_threads(), "kind": "oracle",
-                           "sample": f"2 FP64 Mhat^dag Mhat applies on the full {args.workload} lattice, "
-                                     f"{t_step:.2f} s each"}
+                           "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+                           "sample": f"median of 5 FP64 Mhat^dag Mhat applies on the full {args.workload} "
+                                     f"lattice, {t_step:.2f} s each"}
+    out["cpu_oracle_configs"] = oracle_config_timings(out["config2_16^3x32"])
     return out
+
+
+def oracle_config_timings(gpu_cfg2):
+    """The oracle's D_hop (median of 5) and CG solves on configurations 1 (8^4) and 2
+    (16^3x32, mu = 0 and 0.1) on the host cores: CG timed in full on 8^4 (median
+    of 5); on 16^3x32 one Mhat^dag Mhat apply (median of 5) times the GPU solve's
+    iteration count, labelled extrapolated."""
+    import oracle
+    from paper_1711_03836_gb300 import synth
+
+    res = {"cores": oracle.num_threads(), "nproc": os.cpu_count(), "cpu_model": cpu_model()}
+    for name, wl_name, mu in (("8^4", "8^4", 0.0), ("16^3x32_mu0", "16^3x32", 0.0), ("16^3x32_mu0.1", "16^3x32", 0.1)):
+        wl = dict(WORKLOADS[wl_name], mu=mu)
+        op, b, Vh = oracle_setup(wl)
+        U = op.U
+        psi = synth.gaussian_spinor(Vh, 5)
+        ts = []
+        for _ in range(6):
+            t0 = time.perf_counter()
+            oracle.dhop(op.p, U, None, psi, 0)
+            ts.append(time.perf_counter() - t0)
+        t_d = statistics.median(ts[1:])
+        r = {"dhop_ms": t_d * 1e3, "dhop_GB/s": 1536.0 * Vh / t_d / 1e9, "dhop_GFLOP/s": 1320.0 * Vh / t_d / 1e9}
+        if wl_name == "8^4":
+            ts = []
+            its = 0
+            for _ in range(6):
+                t0 = time.perf_counter()
+                _, its = op.cg(b, tol=1e-10)
+                ts.append(time.perf_counter() - t0)
+            r.update({"cg_ms": statistics.median(ts[1:]) * 1e3, "cg_iterations": int(its)})
+        else:
+            _, t_m = oracle_gbs(op, b, Vh, 5, 1, median=True)
+            key = "mu0" if mu == 0.0 else "mu0.1"
+            its = gpu_cfg2.get(key, {}).get("fp64_iterations")
+            if its:
+                r.update({"cg_ms_extrapolated": t_m * its * 1e3, "cg_iterations_of_gpu_fp64_solve": its,
+                          "mdagm_apply_ms": t_m * 1e3, "note": "extrapolated: one apply x iteration count"})
+        res[name] = r
+    return res
+
+
+def config2_extras(torch, bqcd, fp64_arith):
+    """16^3x32, kappa 0.1350, c_SW 1.7, links exp(i 0.2 A): FP64 vs FP32 D_hop
+    (plain, FP64 units, double-float, FP32 r18 / r12) and the mixed CG (FP32
+    inner, FP64 reliable update at every 1e-3 drop) against plain FP64 CG, at
+    mu = 0 and mu = 0.1. The FP64 links (75 MB), clover and spinors fit in the
+    129 MB L2 with room to spare, so these figures are L2-resident: GB/s above
+    the HBM peak are possible here and are not HBM figures."""
+    from paper_1711_03836_gb300 import synth
+
+    wl = WORKLOADS["16^3x32"]
+    res = {"l2": "L2-resident (FP64 links 75 MB, FP32 links 25 MB, one FP32 spinor 6 MB)"}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    U = synth.gauge_field(wl["dims"], wl["eps"], wl["seed"])
+    for mu in (0.0, 0.1):
+        lat = bqcd.Lattice(wl["dims"], wl["kappa"], wl["csw"], mu, -1.0)
+        ctx = lat.ctx
+        bqcd.bq_set_gauge(ctx, U)
+        bqcd.bq_set_fp64_arith(ctx, fp64_arith)
+        b = synth.gaussian_spinor(lat.Vh, wl["seed"] + 1000)
+        b_dev = torch.from_numpy(b).cuda()
+        x_dev = torch.empty_like(b_dev)
+        r = {}
+        sweep = {}
+        for prec, recon, arith in (("double", 18, "native"), ("double", 18, "df64"), ("single", 18, None),
+                                   ("single", 12, None)):
+            bqcd.bq_set_recon(ctx, prec, recon)
+            if arith:
+                bqcd.bq_set_fp64_arith(ctx, arith)
+            src, dst = lat.pack(b, prec), lat.spinor(prec)
+            for _ in range(3):
+                bqcd.bq_apply_dhop(ctx, dst, src, 1, 0, prec)
+            n = 50
+            e0.record()
+            for i in range(n):
+                bqcd.bq_apply_dhop(ctx, dst, src, i & 1, 0, prec)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / n * 1e-3
+            pid = PREC_ID[prec]
+            sweep[f"{prec}_r{recon}" + (f"_{arith}" if arith else "")] = {
+                "GB/s": (8 * link_b(pid, recon) + 2 * SPINOR_B[pid]) * lat.Vh / t / 1e9,
+                "GFLOP/s": 1320.0 * lat.Vh / t / 1e9, "us": t * 1e6}
+        bqcd.bq_set_fp64_arith(ctx, fp64_arith)
+        bqcd.bq_set_recon(ctx, "single", 12)
+        r["dslash_sweep"] = sweep
+        kw = dict(tol=1e-10, check_every=8, max_iter=20000)
+        for name, prec in (("mixed", "single"), ("fp64", "double")):
+            bqcd.bq_solve_cg(ctx, x_dev, b_dev, precision=prec, delta=1e-3, **kw)
+            e0.record()
+            st = bqcd.bq_solve_cg(ctx, x_dev, b_dev, precision=prec, delta=1e-3, **kw)
+            e1.record()
+            torch.cuda.synchronize()
+            r[f"{name}_ms"] = e0.elapsed_time(e1)
+            r[f"{name}_iterations"] = st["iterations"]
+            r[f"{name}_true_residual"] = st["true_residual"]
+        r["speedup_mixed_vs_fp64"] = r["fp64_ms"] / r["mixed_ms"]
+        res["mu0" if mu == 0.0 else "mu0.1"] = r
+        lat.close()
+    return res
 
 
 if __name__ == "__main__":

@@ -47,14 +47,15 @@ enum {
     BQ_ERR_ARG = 1,             /* invalid argument (null pointer, bad size, bad enum) */
     BQ_ERR_CUDA = 2,            /* a CUDA runtime call failed */
     BQ_ERR_NOT_CONVERGED = 3,   /* solver hit max_iter; stats are still filled */
-    BQ_ERR_TIMEOUT = 4,         /* a bounded device-side wait gave up */
+    BQ_ERR_TIMEOUT = 4,         /* reserved for a bounded device-side wait that gives up; no kernel of
+                                   this library waits on another, so no call returns it at present */
     BQ_ERR_CLOVER_SINGULAR = 5, /* a 6x6 clover block could not be inverted */
     BQ_ERR_STATE = 6,           /* call made before the fields it needs were set */
     BQ_ERR_NOMEM = 7            /* device allocation failed */
 };
 
 enum { BQ_PREC_DOUBLE = 0, BQ_PREC_SINGLE = 1, BQ_PREC_HALF = 2 };
-enum { BQ_RECON_18 = 18, BQ_RECON_12 = 12 };
+enum { BQ_RECON_18 = 18, BQ_RECON_12 = 12, BQ_RECON_8 = 8 };
 enum { BQ_HOST = 0, BQ_DEVICE = 1 };
 enum { BQ_FP64_NATIVE = 0, BQ_FP64_DF64 = 1 };
 enum { BQ_SOLVER_CG = 0, BQ_SOLVER_BICGSTAB = 1 };
@@ -123,9 +124,15 @@ const char *bq_last_error(void);
  * c_SW or the charge invalidates derived fields (rebuilt lazily). */
 int bq_set_params(bq_ctx *ctx, const bq_params *p);
 
-/* Link storage for one precision: BQ_RECON_18 (all 18 reals) or BQ_RECON_12
- * (first two rows; the third is rebuilt as conj(row1 x row2), valid for SU(3)
- * links only, so it is refused while a U(1) field is set). */
+/* Link storage for one precision: BQ_RECON_18 (all 18 reals), BQ_RECON_12
+ * (first two rows; the third is rebuilt as conj(row1 x row2)) or, for
+ * BQ_PREC_SINGLE and BQ_PREC_HALF, BQ_RECON_8 (U01, U02, U10 and the phases of
+ * U00 and U20; the rest rebuilt from unitarity and det U = 1, with two sine /
+ * cosine evaluations, two square roots and one reciprocal per link). 12 and 8
+ * are valid for SU(3) links only, so they are refused while a U(1) field is
+ * set; 8 is singular where |U00| = 1, so the link packing (on the first
+ * operator call) fails with BQ_ERR_ARG if a link has |U01|^2 + |U02|^2 < 1e-6
+ * (e.g. a unit gauge field). BQ_RECON_8 for BQ_PREC_DOUBLE: BQ_ERR_ARG. */
 int bq_set_recon(bq_ctx *ctx, int precision, int recon);
 
 /* Arithmetic of the FP64-storage operator kernels (D_hop, clover, fused
@@ -160,14 +167,45 @@ int bq_set_u1(bq_ctx *ctx, const double *A, int where);
  * the block's largest entry). */
 int bq_build_clover(bq_ctx *ctx);
 
+/* Set the clover term A(x) from the caller instead of building it from the
+ * links (Eq. 2: the clover-improved action, also with the CPT-breaking term
+ * kappa lambda H added by the caller; Section 4 keeps the clover field in a
+ * packed format). A = canonical field A[V][2][36] FP64, host or device memory
+ * (where = BQ_HOST / BQ_DEVICE), sites in lex order over the whole lattice;
+ * per site the two Hermitian 6x6 chirality blocks of A(x) (block 0: spin
+ * components 0, 1; block 1: spin components 2, 3; row/column index
+ * 3 * (spin mod 2) + colour), each as its 6 real diagonal entries followed by
+ * the 15 complex entries above the diagonal in row-major order, re before im.
+ * A(x) is the whole matrix, unit term included; it must commute with
+ * gamma_5 (block diagonal in the chiral basis), which the packed form assumes.
+ * The field is copied, then the inverses of the blocks of both parities are
+ * computed in FP64 as bq_build_clover does. BQ_ERR_CLOVER_SINGULAR if a block
+ * has no inverse; the caller's field is then dropped and the context goes back
+ * to the clover term built from the links. A caller-supplied field stays in use
+ * when the links, kappa or c_SW change, until the next bq_set_clover; A = NULL,
+ * or a call of bq_build_clover, returns to the clover term built from the links.
+ * Host data are staged through a temporary device buffer of at most 2^20 sites. */
+int bq_set_clover(bq_ctx *ctx, const double *A, int where);
+
 /* How batched solves whose first context is ctx lay right-hand sides of one
  * lattice onto threads in the hopping-term launches (Section 3, block solvers):
  * 0 = autotuned on the first solve of each batch shape (default), -1 =
  * consecutive blocks take the right-hand sides of the same sites in turn,
- * -2 = 32 sites per block with one right-hand side per warp, R = 1..8 = the
- * R right-hand sides of a site in adjacent threads of one warp. Results agree
- * to rounding whatever the mapping. Other values: BQ_ERR_ARG. */
+ * -2 = 32 sites per block with one right-hand side per warp, -3 = 32-site
+ * tiles whose links (reconstructed once) and clover blocks are staged in
+ * shared memory once for up to 16 right-hand sides (FP32 and FP16 storage;
+ * FP64 launches of the same solve use -1), -4 and -5 = the same tiles with the
+ * kernel compiled for 5 and 6 resident blocks per SM instead of 4 (96 and 80
+ * registers per thread instead of 128), R = 1..8 = the R right-hand sides
+ * of a site in adjacent threads of one warp. Results agree to rounding
+ * whatever the mapping. Other values: BQ_ERR_ARG. */
 int bq_set_batch_mapping(bq_ctx *ctx, int mapping);
+
+/* The right-hand-side mapping (values as for bq_set_batch_mapping, never 0)
+ * that the last batched solve or batched apply with ctx as first context used
+ * for its FP32 / FP16 launches, forced or chosen by the autotuner; 0 before any
+ * batched call of more than one system. */
+int bq_get_batch_mapping(const bq_ctx *ctx, int *mapping);
 
 /* Stout smearing of the hopping term's links (Section 2, QCD+QED: the
  * fermion action of Eq. 5 hops with singly iterated stout links; Morningstar
@@ -220,7 +258,7 @@ int bq_spinor_unpack(bq_ctx *ctx, double *canonical, const void *native, int pre
  * synchronises the library stream. Uses the context's reduction scratch. */
 int bq_spinor_dot(bq_ctx *ctx, const void *a, const void *b, int precision, double *result);
 
-/* The same <a, b> as bq_spinor_dot, for callers that cannot allocate device
+/* <a, b> as bq_spinor_dot computes it, for callers that cannot allocate device
  * memory: programs that give all of the GPU's memory to their own arena at
  * start-up, or that must not risk the device-wide synchronisation a
  * cudaMalloc/cudaFree can imply inside a time-critical loop. The paper has no
@@ -230,11 +268,15 @@ int bq_spinor_dot(bq_ctx *ctx, const void *a, const void *b, int precision, doub
  * every GPU loading the library holds until exit. a and b are native device
  * buffers of n_sites = V/2 sites at `precision`; n_sites is limited to
  * 4 194 304 (16 384 blocks of 256 sites), larger values return BQ_ERR_ARG.
+ * The result is the same on every call for the same inputs; it is summed over
+ * another partition of the sites than bq_spinor_dot's, so the two agree to
+ * rounding, not necessarily in the last bits.
  * result is host memory; the call synchronises `cuda_stream`. All calls share
  * the array (its ticket is cleared per call): calls that overlap on the GPU
- * race and must be serialised by the caller. The first call on a device looks
- * up the array's address with that device current; make it before any stream
- * capture. */
+ * race and must be serialised by the caller. The array's address is looked up
+ * on every call with the caller's device current (so a context re-created by
+ * cudaDeviceReset is handled); the first call on a device also loads the
+ * library's module there, so make it before any stream capture. */
 int bq_spinor_dot_noalloc(const void *a, const void *b, long long n_sites, int precision, void *cuda_stream,
                           double *result);
 
@@ -253,6 +295,19 @@ int bq_apply_mhat(bq_ctx *ctx, void *out, const void *in, int dagger, int precis
 
 /* out = Mhat^dagger Mhat in. out must not alias in. */
 int bq_apply_mdagm(bq_ctx *ctx, void *out, const void *in, int precision);
+
+/* out[i] = Mhat^dagger Mhat in[i] for nsys systems at once (the operator of
+ * the block solvers of Section 3 applied to many right-hand sides): system i
+ * lives on lattice ctx[i] (native even-parity buffers of that context at
+ * `precision`); systems that share a context share the link and clover loads
+ * of each of the four batched hopping-term launches, with the right-hand-side
+ * mapping of bq_set_batch_mapping on ctx[0] (0 = shared-memory tiles for FP32
+ * and FP16 storage, block-interleaved for FP64). The contexts obey the rules
+ * of bq_solve_cg_batch (one device, same link storage and FP64 arithmetic);
+ * queued on ctx[0]'s stream. No out[j] may alias an in[i]. The two
+ * intermediate vectors per system are the batched solver's work vectors,
+ * kept with ctx[0]. */
+int bq_apply_mdagm_batch(bq_ctx *const *ctx, int nsys, void *const *out, const void *const *in, int precision);
 
 /* ---- solvers (canonical FP64 spinors, host or device) --------------------- */
 

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libbqcd_gb300.so")
 BQ_OK, BQ_ERR_ARG, BQ_ERR_CUDA, BQ_ERR_NOT_CONVERGED, BQ_ERR_TIMEOUT, BQ_ERR_CLOVER_SINGULAR, BQ_ERR_STATE, \
     BQ_ERR_NOMEM = range(8)
 BQ_PREC_DOUBLE, BQ_PREC_SINGLE, BQ_PREC_HALF = 0, 1, 2
-BQ_RECON_18, BQ_RECON_12 = 18, 12
+BQ_RECON_18, BQ_RECON_12, BQ_RECON_8 = 18, 12, 8
 BQ_HOST, BQ_DEVICE = 0, 1
 BQ_FP64_NATIVE, BQ_FP64_DF64 = 0, 1
 BQ_SOLVER_CG, BQ_SOLVER_BICGSTAB = 0, 1
@@ -88,6 +88,7 @@ _SIGS = {
     "bq_set_gauge": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "bq_set_u1": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "bq_build_clover": (ctypes.c_int, [ctypes.c_void_p]),
+    "bq_set_clover": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "bq_spinor_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int]),
     "bq_spinor_pack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "bq_spinor_unpack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
@@ -101,6 +102,9 @@ _SIGS = {
                                        ctypes.c_int]),
     "bq_apply_mhat": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "bq_apply_mdagm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "bq_apply_mdagm_batch": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                            ctypes.c_int]),
     "bq_solve_cg": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                    ctypes.POINTER(bq_solver_params), ctypes.POINTER(bq_solver_stats)]),
     "bq_solve_cg_batch": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
@@ -116,6 +120,7 @@ _SIGS = {
                                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(bq_solver_params),
                                                     ctypes.POINTER(bq_solver_stats), ctypes.POINTER(ctypes.c_double)]),
     "bq_set_batch_mapping": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "bq_get_batch_mapping": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "bq_set_stout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]),
     "bq_get_hop_links": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "bq_clover_logdet": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -235,6 +240,15 @@ def bq_build_clover(ctx):
     _check(_lib_handle().bq_build_clover(ctx), "bq_build_clover")
 
 
+def bq_set_clover(ctx, A):
+    """Caller-supplied clover field A[V][2][36] float64 (host or device), or None to build it from the links."""
+    if A is None:
+        _check(_lib_handle().bq_set_clover(ctx, None, BQ_HOST), "bq_set_clover")
+        return
+    p, w = _ptr_where(A)
+    _check(_lib_handle().bq_set_clover(ctx, p, w), "bq_set_clover")
+
+
 def bq_spinor_bytes(ctx, precision):
     return int(_lib_handle().bq_spinor_bytes(ctx, PREC_NAMES[precision]))
 
@@ -285,6 +299,17 @@ def bq_apply_mhat(ctx, out, inp, dagger, precision):
 
 def bq_apply_mdagm(ctx, out, inp, precision):
     _check(_lib_handle().bq_apply_mdagm(ctx, _dev_ptr(out), _dev_ptr(inp), PREC_NAMES[precision]), "bq_apply_mdagm")
+
+
+def bq_apply_mdagm_batch(ctxs, outs, ins, precision):
+    """outs[i] = Mhat^dag Mhat ins[i] on lattice ctxs[i] for every i (native CUDA buffers)."""
+    n = len(ctxs)
+    if len(outs) != n or len(ins) != n:
+        raise ValueError("one output and one input per system")
+    carr = (ctypes.c_void_p * n)(*[c.value for c in ctxs])
+    oarr = (ctypes.c_void_p * n)(*[_dev_ptr(o) for o in outs])
+    iarr = (ctypes.c_void_p * n)(*[_dev_ptr(i) for i in ins])
+    _check(_lib_handle().bq_apply_mdagm_batch(carr, n, oarr, iarr, PREC_NAMES[precision]), "bq_apply_mdagm_batch")
 
 
 def bq_solve_cg(ctx, x, b, tol=1e-10, max_iter=10000, precision="double", delta=1e-3, check_every=8, shift=0.0,
@@ -384,8 +409,16 @@ def bq_solve_multishift_cg_block(ctx, xs, bs, shifts, tol=1e-10, max_iter=20000,
 
 
 def bq_set_batch_mapping(ctx, mapping):
-    """0 autotuned, -1 block-interleaved, -2 one rhs per warp, 1..8 rhs interleaved in a warp."""
+    """0 autotuned, -1 block-interleaved, -2 one rhs per warp, -3 shared-memory tiles, 1..8 rhs
+    interleaved in a warp."""
     _check(_lib_handle().bq_set_batch_mapping(ctx, int(mapping)), "bq_set_batch_mapping")
+
+
+def bq_get_batch_mapping(ctx):
+    """Mapping used by the last batched call with ctx first (0: none yet)."""
+    m = ctypes.c_int()
+    _check(_lib_handle().bq_get_batch_mapping(ctx, ctypes.byref(m)), "bq_get_batch_mapping")
+    return m.value
 
 
 def bq_set_stout(ctx, rho, n_iter=1):

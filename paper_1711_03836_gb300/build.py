@@ -66,5 +66,22 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     return LIB
 
 
+PROBE_SRC = os.path.join(HERE, "probe", "bq_probe.cu")
+PROBE_LIB = os.path.join(HERE, "libbq_probe.so")
+
+
+def build_probe(force: bool = False) -> str:
+    """The FP64 FMA-rate probe the bench uses as its FP64 roofline (a separate library)."""
+    if not force and not _stale(PROBE_LIB, [PROBE_SRC]):
+        return PROBE_LIB
+    tmp = PROBE_LIB + f".tmp{os.getpid()}"
+    cmd = [NVCC, *ARCH, *FLAGS, "-shared", PROBE_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PROBE_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True, ptxas_v="-v" in sys.argv))

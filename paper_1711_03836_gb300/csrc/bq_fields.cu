@@ -54,8 +54,12 @@ int bq_alloc(void **p, size_t bytes) {
 
 static int valid_prec(int p) { return p == BQ_PREC_DOUBLE || p == BQ_PREC_SINGLE || p == BQ_PREC_HALF; }
 
+// clover = 1: the clover term built from the links is out of date; a clover
+// field set by the caller (bq_set_clover) does not follow the links or kappa,
+// c_SW and stays until the caller replaces or removes it
 static void invalidate_derived(bq_ctx *c, int links, int clover) {
     if (links && clover) c->U_hop_valid = 0;  // a new gauge field
+    if (c->clov_user) clover = 0;
     for (int p = 0; p < BQ_NFIELD; p++) {
         if (links) c->links_valid[p] = 0;
         if (clover) c->clov_valid[p] = 0;
@@ -167,12 +171,16 @@ extern "C" int bq_set_cuda_graphs(bq_ctx *c, int enable) {
 }
 
 extern "C" int bq_set_recon(bq_ctx *c, int prec, int recon) {
-    if (!c || !valid_prec(prec) || !(recon == BQ_RECON_18 || recon == BQ_RECON_12)) {
+    if (!c || !valid_prec(prec) || !(recon == BQ_RECON_18 || recon == BQ_RECON_12 || recon == BQ_RECON_8)) {
         bq_set_error("bq_set_recon: bad arguments");
         return BQ_ERR_ARG;
     }
-    if (recon == BQ_RECON_12 && c->A_u1) {
-        bq_set_error("bq_set_recon: 12-real links need SU(3) links; a U(1) field is set");
+    if (recon == BQ_RECON_8 && prec == BQ_PREC_DOUBLE) {
+        bq_set_error("bq_set_recon: 8-real links are offered for FP32 and FP16 storage only");
+        return BQ_ERR_ARG;
+    }
+    if (recon != BQ_RECON_18 && c->A_u1) {
+        bq_set_error("bq_set_recon: %d-real links need SU(3) links; a U(1) field is set", recon);
         return BQ_ERR_ARG;
     }
     if (c->recon[prec] != recon) {
@@ -209,8 +217,8 @@ extern "C" int bq_set_u1(bq_ctx *c, const double *A, int where) {
         return BQ_OK;
     }
     for (int p = 0; p < BQ_NPREC; p++)
-        if (c->recon[p] == BQ_RECON_12) {
-            bq_set_error("bq_set_u1: precision %d uses 12-real links, which need SU(3) links", p);
+        if (c->recon[p] != BQ_RECON_18) {
+            bq_set_error("bq_set_u1: precision %d uses %d-real links, which need SU(3) links", p, c->recon[p]);
             return BQ_ERR_ARG;
         }
     size_t bytes = (size_t)c->V * 4 * sizeof(double);
@@ -231,7 +239,8 @@ extern "C" int bq_set_u1(bq_ctx *c, const double *A, int where) {
 // links
 
 template <int PREC, int RECON>
-__global__ void k_pack_links(char *dst, size_t blk, const double2 *U, const double *A, double charge, Geo g) {
+__global__ void k_pack_links(char *dst, size_t blk, const double2 *U, const double *A, double charge, Geo g,
+                             int *flag) {
     long long lex = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (lex >= g.V) return;
     int c[4];
@@ -247,6 +256,9 @@ __global__ void k_pack_links(char *dst, size_t blk, const double2 *U, const doub
             sincos(-charge * A[lex * 4 + mu], &s, &co);
             for (int k = 0; k < 9; k++) u[k] = make_double2(co * u[k].x - s * u[k].y, co * u[k].y + s * u[k].x);
         }
+        // 8-real links are singular where |U00| = 1 (see reconstruct8)
+        if (RECON == BQ_RECON_8 && u[1].x * u[1].x + u[1].y * u[1].y + u[2].x * u[2].x + u[2].y * u[2].y < BQ_RECON8_MIN_N)
+            atomicExch(flag, 1);
         LinkIO<PREC, RECON>::store(dst + (size_t)(par * 4 + mu) * blk, h, g.Vh, u);
     }
 }
@@ -275,19 +287,30 @@ int bq_prepare_links(bq_ctx *c, int prec) {
         BQ_TRY(bq_prepare_hop_links(c));
         Usrc = c->U_hop;
     }
-#define PACK(P, R) k_pack_links<P, R><<<grid, 128, 0, c->stream>>>(c->links[prec], blk, Usrc, c->A_u1, q, g)
+    if (recon == BQ_RECON_8) BQ_CUDA_TRY(cudaMemsetAsync(c->dev_flag, 0, sizeof(int), c->stream));
+#define PACK(P, R) k_pack_links<P, R><<<grid, 128, 0, c->stream>>>(c->links[prec], blk, Usrc, c->A_u1, q, g, c->dev_flag)
     if (prec == BQ_PREC_DOUBLE) {
         if (recon == 12) PACK(BQ_PREC_DOUBLE, 12); else PACK(BQ_PREC_DOUBLE, 18);
     } else if (prec == BQ_PREC_SINGLE) {
-        if (recon == 12) PACK(BQ_PREC_SINGLE, 12); else PACK(BQ_PREC_SINGLE, 18);
+        if (recon == 12) PACK(BQ_PREC_SINGLE, 12); else if (recon == 8) PACK(BQ_PREC_SINGLE, 8); else PACK(BQ_PREC_SINGLE, 18);
     } else if (prec == BQ_PREC_HALF) {
-        if (recon == 12) PACK(BQ_PREC_HALF, 12); else PACK(BQ_PREC_HALF, 18);
+        if (recon == 12) PACK(BQ_PREC_HALF, 12); else if (recon == 8) PACK(BQ_PREC_HALF, 8); else PACK(BQ_PREC_HALF, 18);
     } else {
         if (recon == 12) PACK(BQ_PREC_DF64, 12); else PACK(BQ_PREC_DF64, 18);
     }
 #undef PACK
     BQ_LAUNCH_CHECK();
     BQ_COUNT(c);
+    if (recon == BQ_RECON_8) {
+        int flag = 0;
+        BQ_CUDA_TRY(cudaMemcpyAsync(&flag, c->dev_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        BQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        if (flag) {
+            bq_set_error("8-real links: a link has |U01|^2 + |U02|^2 < %g (|U00| = 1 is singular for this storage); "
+                         "use 12- or 18-real links for this field", BQ_RECON8_MIN_N);
+            return BQ_ERR_ARG;
+        }
+    }
     c->links_valid[prec] = 1;
     return BQ_OK;
 }
@@ -549,6 +572,7 @@ extern "C" int bq_build_clover(bq_ctx *c) {
         bq_set_error("gauge field not set");
         return BQ_ERR_STATE;
     }
+    c->clov_user = 0;  // building from the links replaces a caller-supplied field
     size_t pblk = (size_t)36 * c->Vh;  // double2 per (parity, inverse) block
     BQ_TRY(bq_alloc((void **)&c->clov_master, sizeof(double2) * pblk * 4));
     Geo g = geo_of(c);
@@ -569,6 +593,89 @@ extern "C" int bq_build_clover(bq_ctx *c) {
         bq_set_error("clover block without inverse");
         return BQ_ERR_CLOVER_SINGULAR;
     }
+    c->clov_master_valid = 1;
+    c->clov[BQ_PREC_DOUBLE] = (char *)c->clov_master;
+    c->clov_valid[BQ_PREC_DOUBLE] = 1;
+    c->clov_valid[BQ_PREC_SINGLE] = c->clov_valid[BQ_PREC_HALF] = c->clov_valid[BQ_PREC_DF64] = 0;
+    return BQ_OK;
+}
+
+// Caller-supplied clover field: canonical [V][2][36] FP64 in lex order (per
+// site and chirality block: 6 real diagonal entries, then the 15 complex
+// entries above the diagonal row by row), i.e. 36 double2 per site, written
+// into the packed A blocks of its parity: the k-th double2 of a site is chunk k
+// of the site's half-lattice column. One thread per (site, double2).
+__global__ void k_set_clover(double2 *master, size_t pblk, const double2 *src, long long x0, long long n, Geo g) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= 36 * n) return;
+    const long long x = x0 + idx / 36;
+    const int k = (int)(idx % 36);
+    int co[4];
+    lex_coords(g, x, co);
+    const int par = (co[0] + co[1] + co[2] + co[3]) & 1;
+    master[(size_t)(par * 2) * pblk + (size_t)k * g.Vh + (size_t)(x >> 1)] = src[idx];
+}
+
+extern "C" int bq_set_clover(bq_ctx *c, const double *A, int where) {
+    if (!c || !(where == BQ_HOST || where == BQ_DEVICE)) {
+        bq_set_error("bq_set_clover: bad arguments");
+        return BQ_ERR_ARG;
+    }
+    if (!A) {  // back to the clover term built from the links
+        if (c->clov_user) {
+            c->clov_user = 0;
+            invalidate_derived(c, 0, 1);
+        }
+        return BQ_OK;
+    }
+    c->clov_user = 0;
+    invalidate_derived(c, 0, 1);
+    const size_t pblk = (size_t)36 * c->Vh;
+    BQ_TRY(bq_alloc((void **)&c->clov_master, sizeof(double2) * pblk * 4));
+    Geo g = geo_of(c);
+    // host data goes through a bounded device staging buffer, 2^20 sites (604 MB) at a time
+    const long long chunk = where == BQ_HOST ? (c->V < (1LL << 20) ? c->V : (1LL << 20)) : c->V;
+    double2 *stage = nullptr;
+    if (where == BQ_HOST) BQ_TRY(bq_alloc((void **)&stage, sizeof(double2) * 36 * (size_t)chunk));
+    int st = BQ_OK;
+    for (long long x0 = 0; x0 < c->V && st == BQ_OK; x0 += chunk) {
+        const long long n = (c->V - x0 < chunk) ? c->V - x0 : chunk;
+        const double2 *src = reinterpret_cast<const double2 *>(A) + 36 * x0;
+        if (where == BQ_HOST) {
+            cudaError_t e = cudaMemcpyAsync(stage, src, sizeof(double2) * 36 * (size_t)n, cudaMemcpyHostToDevice,
+                                            c->stream);
+            if (e != cudaSuccess) {
+                bq_set_error("bq_set_clover: copy failed: %s", cudaGetErrorString(e));
+                st = BQ_ERR_CUDA;
+                break;
+            }
+            src = stage;
+        }
+        k_set_clover<<<grid_for(36 * n, 256), 256, 0, c->stream>>>((double2 *)c->clov_master, pblk, src, x0, n, g);
+        if (cudaGetLastError() != cudaSuccess) st = BQ_ERR_CUDA;
+        BQ_COUNT(c);
+    }
+    int flag = 0;
+    if (st == BQ_OK && (cudaMemsetAsync(c->dev_flag, 0, sizeof(int), c->stream) != cudaSuccess)) st = BQ_ERR_CUDA;
+    if (st == BQ_OK) {
+        k_invert_clover<<<grid_for(4LL * c->Vh, 64), 64, 0, c->stream>>>((double2 *)c->clov_master, pblk, c->Vh,
+                                                                         c->dev_flag);
+        BQ_COUNT(c);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&flag, c->dev_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+            st = BQ_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess && st == BQ_OK) st = BQ_ERR_CUDA;
+    cudaFree(stage);
+    if (st != BQ_OK) {
+        bq_set_error("bq_set_clover: CUDA error while setting the clover field");
+        return st;
+    }
+    if (flag) {  // the caller's field is dropped; the context goes back to building from the links
+        bq_set_error("bq_set_clover: a clover block of the field has no inverse");
+        return BQ_ERR_CLOVER_SINGULAR;
+    }
+    c->clov_user = 1;
     c->clov_master_valid = 1;
     c->clov[BQ_PREC_DOUBLE] = (char *)c->clov_master;
     c->clov_valid[BQ_PREC_DOUBLE] = 1;

@@ -16,11 +16,17 @@
 // lattice is 1 048 576); larger inputs are rejected with BQ_ERR_ARG.  All calls
 // share the array: the ticket is cleared before each launch, and calls whose
 // kernels overlap on the GPU (several host threads or streams at once) race on
-// it, so callers must serialise them.  The first call on each device looks up
-// the array's device address (cudaGetSymbolAddress) with that device current;
-// make that first call before any stream capture.
-#include <mutex>
-
+// it, so callers must serialise them.  The array's device address is looked
+// up (cudaGetSymbolAddress, a host-side lookup that allocates nothing) on every
+// call with the caller's device current, so a primary context re-created after
+// cudaDeviceReset, which may load the module at another address, is handled.
+// The first call on a device also loads the library's module there; make that
+// first call before any stream capture.
+//
+// The sum runs over one partial per 256-site block, then the last block adds
+// the partials in block order: the same inputs give the same bits on every
+// call, but the partition differs from bq_spinor_dot's grid-stride loop, so
+// the two agree to rounding, not bit for bit.
 #include "bq_internal.cuh"
 
 namespace {
@@ -35,10 +41,6 @@ constexpr int NA_TICKET = NA_RESULT + 2;
 constexpr int NA_DOUBLES = NA_TICKET + 2;
 
 static __device__ __align__(256) double g_noalloc_scratch[NA_DOUBLES];
-
-constexpr int NA_MAX_DEVICES = 64;
-std::mutex g_setup_mutex;
-double *g_scratch_ptr[NA_MAX_DEVICES] = {nullptr};
 
 __device__ __forceinline__ double na_warp_sum(double v) {
 #pragma unroll
@@ -108,26 +110,19 @@ __global__ void __launch_bounds__(NA_THREADS) k_dot_noalloc(const void *a, const
     }
 }
 
-// device address of the scratch array on the current device (looked up once per device)
+// device address of the scratch array in the current device's context,
+// looked up on every call (no allocation; handles a re-created context)
 int scratch_for_current_device(double **out) {
     int dev = -1;
     BQ_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= NA_MAX_DEVICES) {
-        bq_set_error("bq_spinor_dot_noalloc: device %d out of range", dev);
-        return BQ_ERR_ARG;
+    double *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        bq_set_error("bq_spinor_dot_noalloc: cudaGetSymbolAddress failed on device %d: %s", dev,
+                     cudaGetErrorString(e));
+        return BQ_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-        double *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            bq_set_error("bq_spinor_dot_noalloc: cudaGetSymbolAddress failed on device %d: %s", dev,
-                         cudaGetErrorString(e));
-            return BQ_ERR_CUDA;
-        }
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return BQ_OK;
 }
 

@@ -1,0 +1,290 @@
+// bq_tile.cu -- the batched hopping term (Eq. 1 / Eq. 5) with the links and
+// the clover term of a tile of sites staged in shared memory once for all
+// right-hand sides of a unit (the block solvers of Section 3 apply one operator
+// to many right-hand sides), FP32 and FP16 storage.
+#include "bq_internal.cuh"
+#include "bq_stencil.cuh"
+
+// --------------------------------------------------------------------------
+// Tiled batched hopping term (FP32 and FP16 storage). A block owns a tile of
+// TILE_SITES = 32 output sites of one unit and serves every right-hand side of
+// the unit: first the block loads the tile's eight links per site once (12-real
+// links reconstructed once, FP16 converted once) and its clover blocks into
+// shared memory, then each warp takes right-hand sides w, w + 4, ... with one
+// site per lane, reading the links and the clover from shared memory. Link and
+// clover bytes and their load/convert instructions are paid once per site of
+// the unit instead of once per site and right-hand side.
+
+#define TILE_SITES 32
+
+// full-lattice coordinates and the eight neighbour half-site indices of h
+struct SiteNb {
+    int t;
+    int hn[8];  // d = 2 mu + back: x+, x-, y+, y-, z+, z-, t+, t-
+};
+__device__ __forceinline__ SiteNb site_neighbours(const DslashArgs &a, int h) {
+    SiteNb s;
+    const int Lxh = a.Lxh;
+    const int xh = h % Lxh;
+    int r = h / Lxh;
+    const int y = r % a.L1;
+    r /= a.L1;
+    const int z = r % a.L2;
+    const int t = r / a.L2;
+    const int x = 2 * xh + ((a.parity + y + z + t) & 1);
+    const int sy = Lxh, sz = Lxh * a.L1, st = sz * a.L2;
+    s.t = t;
+    s.hn[0] = h - xh + (((x + 1 == a.L0) ? 0 : x + 1) >> 1);
+    s.hn[1] = h - xh + (((x == 0) ? a.L0 - 1 : x - 1) >> 1);
+    s.hn[2] = (y + 1 == a.L1) ? h - (a.L1 - 1) * sy : h + sy;
+    s.hn[3] = (y == 0) ? h + (a.L1 - 1) * sy : h - sy;
+    s.hn[4] = (z + 1 == a.L2) ? h - (a.L2 - 1) * sz : h + sz;
+    s.hn[5] = (z == 0) ? h + (a.L2 - 1) * sz : h - sz;
+    s.hn[6] = (t + 1 == a.L3) ? h - (a.L3 - 1) * st : h + st;
+    s.hn[7] = (t == 0) ? h + (a.L3 - 1) * st : h - st;
+    return s;
+}
+
+// one hop with the link already in registers (FP32 arithmetic; FP16 spinors
+// are projected and multiplied unscaled, the site's scale folded into the
+// accumulation as in hop())
+template <int PREC, int MU, int S, bool BACK, bool SCALE>
+__device__ __forceinline__ void hop_link(cplx<float> acc[12], const void *in, int hn, const cplx<float> U[9], int Vh,
+                                         float coef) {
+    constexpr bool FOLD = SCALE || PREC == BQ_PREC_HALF;
+    cplx<float> psi[12];
+    float f = SCALE ? coef : 1.0f;
+    if constexpr (PREC == BQ_PREC_HALF) {
+        float n;
+        SpinorIO<PREC>::load_unscaled(psi, in, hn, Vh, n);
+        f *= n;
+    } else {
+        SpinorIO<PREC>::load(psi, in, hn, Vh);
+    }
+    cplx<float> h0[3], h1[3];
+    project<MU, S>(psi, h0, h1);
+    cplx<float> u0[3], u1[3];
+#pragma unroll
+    for (int aa = 0; aa < 3; aa++) {
+        u0[aa] = {0.f, 0.f};
+        u1[aa] = {0.f, 0.f};
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            if (BACK) {
+                u0[aa] = cfmac(U[b * 3 + aa], h0[b], u0[aa]);
+                u1[aa] = cfmac(U[b * 3 + aa], h1[b], u1[aa]);
+            } else {
+                u0[aa] = cfma(U[aa * 3 + b], h0[b], u0[aa]);
+                u1[aa] = cfma(U[aa * 3 + b], h1[b], u1[aa]);
+            }
+        }
+    }
+    if constexpr (FOLD)
+        accumulate_scaled<MU, S>(acc, u0, u1, f);
+    else
+        accumulate<MU, S>(acc, u0, u1);
+}
+
+// link d of the tile's site `lane`: 9 complex as 5 float4 (the last half unused), [8][5][TILE_SITES]
+__device__ __forceinline__ void tile_link(cplx<float> U[9], const float4 *sL, int d, int lane) {
+    const float4 *p = sL + d * 5 * TILE_SITES + lane;
+    const float4 v0 = p[0], v1 = p[TILE_SITES], v2 = p[2 * TILE_SITES], v3 = p[3 * TILE_SITES],
+                 v4 = p[4 * TILE_SITES];
+    U[0] = {v0.x, v0.y};
+    U[1] = {v0.z, v0.w};
+    U[2] = {v1.x, v1.y};
+    U[3] = {v1.z, v1.w};
+    U[4] = {v2.x, v2.y};
+    U[5] = {v2.z, v2.w};
+    U[6] = {v3.x, v3.y};
+    U[7] = {v3.z, v3.w};
+    U[8] = {v4.x, v4.y};
+}
+
+// clover block b of the tile's site `lane`: 9 float4 = 6 diagonal reals + 15 complex, [18][TILE_SITES]
+__device__ __forceinline__ void tile_clover_block(float d[6], cplx<float> o[15], const float4 *sC, int b, int lane) {
+    float r[36];
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        const float4 v = sC[(9 * b + k) * TILE_SITES + lane];
+        r[4 * k] = v.x;
+        r[4 * k + 1] = v.y;
+        r[4 * k + 2] = v.z;
+        r[4 * k + 3] = v.w;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; k++) d[k] = r[k];
+#pragma unroll
+    for (int k = 0; k < 15; k++) o[k] = {r[6 + 2 * k], r[7 + 2 * k]};
+}
+
+// the eight links of the tile's sites (forward: U_mu(x) of the output parity;
+// backward: U_mu(x - mu) of the other parity), reconstructed / converted to FP32
+template <int PREC, int RECON>
+__device__ __forceinline__ void stage_links(float4 *sL, const DslashArgs &a, int h0) {
+    const char *Lo = a.links + (size_t)a.parity * 4 * a.lblk;
+    const char *Li = a.links + (size_t)(1 - a.parity) * 4 * a.lblk;
+    for (int i = threadIdx.x; i < 8 * TILE_SITES; i += blockDim.x) {
+        const int d = i / TILE_SITES, lane = i % TILE_SITES, mu = d >> 1;
+        const int h = h0 + lane;
+        cplx<float> U[9];
+        if (h < a.Vh) {
+            int hl = h;
+            if (d & 1) hl = site_neighbours(a, h).hn[d];
+            LinkIO<PREC, RECON>::load(U, ((d & 1) ? Li : Lo) + (size_t)mu * a.lblk, hl, a.Vh);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 9; k++) U[k] = {0.f, 0.f};
+        }
+        float4 *p = sL + d * 5 * TILE_SITES + lane;
+        p[0] = make_float4(U[0].re, U[0].im, U[1].re, U[1].im);
+        p[TILE_SITES] = make_float4(U[2].re, U[2].im, U[3].re, U[3].im);
+        p[2 * TILE_SITES] = make_float4(U[4].re, U[4].im, U[5].re, U[5].im);
+        p[3 * TILE_SITES] = make_float4(U[6].re, U[6].im, U[7].re, U[7].im);
+        p[4 * TILE_SITES] = make_float4(U[8].re, U[8].im, 0.f, 0.f);
+    }
+}
+
+template <int PREC>
+__device__ __forceinline__ void stage_clover(float4 *sC, const void *clov, int h0, int Vh) {
+    for (int i = threadIdx.x; i < 18 * TILE_SITES; i += blockDim.x) {
+        const int k = i / TILE_SITES, lane = i % TILE_SITES;
+        const int h = h0 + lane;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (h < Vh) {
+            if constexpr (PREC == BQ_PREC_SINGLE) {
+                v = ldg(static_cast<const float4 *>(clov) + (size_t)k * Vh + h);
+            } else {
+                const uint2 u = ldg(static_cast<const uint2 *>(clov) + (size_t)k * Vh + h);
+                const float2 lo = h2f(u.x), hi = h2f(u.y);
+                v = make_float4(lo.x, lo.y, hi.x, hi.y);
+            }
+        }
+        sC[k * TILE_SITES + lane] = v;
+    }
+}
+
+template <int PREC, bool DAG, int EPI>
+__device__ __forceinline__ void dslash_site_tile(const DslashArgs &a, const SiteNb &nb, const void *in, void *out,
+                                                 const void *xin, int h, const float4 *sL, const float4 *sC,
+                                                 int lane) {
+    const int Vh = a.Vh;
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    cplx<float> acc[12];
+#pragma unroll
+    for (int c = 0; c < 12; c++) acc[c] = {0.f, 0.f};
+    cplx<float> U[9];
+    tile_link(U, sL, 0, lane);
+    hop_link<PREC, 0, SF, false, false>(acc, in, nb.hn[0], U, Vh, 1.f);
+    tile_link(U, sL, 1, lane);
+    hop_link<PREC, 0, SB, true, false>(acc, in, nb.hn[1], U, Vh, 1.f);
+    tile_link(U, sL, 2, lane);
+    hop_link<PREC, 1, SF, false, false>(acc, in, nb.hn[2], U, Vh, 1.f);
+    tile_link(U, sL, 3, lane);
+    hop_link<PREC, 1, SB, true, false>(acc, in, nb.hn[3], U, Vh, 1.f);
+    tile_link(U, sL, 4, lane);
+    hop_link<PREC, 2, SF, false, false>(acc, in, nb.hn[4], U, Vh, 1.f);
+    tile_link(U, sL, 5, lane);
+    hop_link<PREC, 2, SB, true, false>(acc, in, nb.hn[5], U, Vh, 1.f);
+    const float cf = (float)(nb.t + 1 == a.L3 ? a.cf * a.bc : a.cf);
+    const float cb = (float)(nb.t == 0 ? a.cb * a.bc : a.cb);
+    tile_link(U, sL, 6, lane);
+    hop_link<PREC, 3, SF, false, true>(acc, in, nb.hn[6], U, Vh, cf);
+    tile_link(U, sL, 7, lane);
+    hop_link<PREC, 3, SB, true, true>(acc, in, nb.hn[7], U, Vh, cb);
+
+    if (EPI == EPI_PLAIN) {
+        SpinorIO<PREC>::store(out, h, Vh, acc);
+        return;
+    }
+    cplx<float> src[12], o[12];
+    if (EPI == EPI_CLOVINV) {
+#pragma unroll
+        for (int c = 0; c < 12; c++) src[c] = acc[c];
+    } else {
+        SpinorIO<PREC>::load(src, xin, h, Vh);
+    }
+#pragma unroll
+    for (int b = 0; b < 2; b++) {
+        float d[6];
+        cplx<float> ob[15];
+        tile_clover_block(d, ob, sC, b, lane);
+        herm6_apply(d, ob, src + 6 * b, o + 6 * b);
+    }
+    if (EPI == EPI_XPAY) {
+        const float k = (float)a.k;
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            o[c].re = fmaf(-k, acc[c].re, o[c].re);
+            o[c].im = fmaf(-k, acc[c].im, o[c].im);
+        }
+    }
+    SpinorIO<PREC>::store(out, h, Vh, o);
+}
+
+// MB: resident 128-thread blocks per SM the kernel is compiled for (registers
+// per thread 128, 96 or 80); the autotuner picks among the variants
+template <int PREC, int RECON, bool DAG, int EPI, int MB>
+__global__ void __launch_bounds__(128, MB) k_dslash_tile(const __grid_constant__ DslashBatchTable tab,
+                                                         const double *mask) {
+    __shared__ float4 sL[8 * 5 * TILE_SITES];
+    __shared__ float4 sC[EPI != EPI_PLAIN ? 18 * TILE_SITES : 1];
+    int u = 0;
+    while (u + 1 < tab.nunits && tab.block0[u + 1] <= (int)blockIdx.x) u++;
+    const DslashUnit &U = tab.units[u];
+    const int h0 = ((int)blockIdx.x - tab.block0[u]) * TILE_SITES;
+    // a unit whose systems are all masked off (converged, or not due for an update) is skipped
+    // by the whole block at once, before the barrier
+    if (mask) {
+        bool any = false;
+        for (int r = 0; r < U.nr; r++) any = any || mask[U.sys[r]] != 0.0;
+        if (!any) return;
+    }
+    stage_links<PREC, RECON>(sL, U.a, h0);
+    if (EPI != EPI_PLAIN) stage_clover<PREC>(sC, U.a.clov, h0, U.a.Vh);
+    __syncthreads();
+    const int lane = (int)(threadIdx.x & 31), warp = (int)(threadIdx.x >> 5), nw = (int)(blockDim.x >> 5);
+    const int h = h0 + lane;
+    if (h >= U.a.Vh) return;
+    const SiteNb nb = site_neighbours(U.a, h);
+    for (int r = warp; r < U.nr; r += nw) {
+        if (mask && mask[U.sys[r]] == 0.0) continue;
+        dslash_site_tile<PREC, DAG, EPI>(U.a, nb, U.in[r], U.out[r], U.xin[r], h, sL, sC, lane);
+    }
+}
+
+template <int PREC, int RECON, int MB>
+static void launch_tile_mb(const DslashBatchTable &tab, const double *mask, int nblocks, bool dag, int epi,
+                           cudaStream_t s) {
+    if (dag) {
+        if (epi == EPI_CLOVINV) k_dslash_tile<PREC, RECON, true, EPI_CLOVINV, MB><<<nblocks, 128, 0, s>>>(tab, mask);
+        else k_dslash_tile<PREC, RECON, true, EPI_XPAY, MB><<<nblocks, 128, 0, s>>>(tab, mask);
+    } else {
+        if (epi == EPI_CLOVINV) k_dslash_tile<PREC, RECON, false, EPI_CLOVINV, MB><<<nblocks, 128, 0, s>>>(tab, mask);
+        else k_dslash_tile<PREC, RECON, false, EPI_XPAY, MB><<<nblocks, 128, 0, s>>>(tab, mask);
+    }
+}
+
+// batched units carry the clover epilogues only (the solvers and the batched
+// apply run D_oe A_oo^-1 and A x - k D_eo steps); tab.variant = resident blocks
+template <int PREC, int RECON>
+static void launch_tile_pr(const DslashBatchTable &tab, const double *mask, int nblocks, bool dag, int epi,
+                           cudaStream_t s) {
+    if (tab.variant == 6) launch_tile_mb<PREC, RECON, 6>(tab, mask, nblocks, dag, epi, s);
+    else if (tab.variant == 5) launch_tile_mb<PREC, RECON, 5>(tab, mask, nblocks, dag, epi, s);
+    else launch_tile_mb<PREC, RECON, 4>(tab, mask, nblocks, dag, epi, s);
+}
+
+void bq_tile_launch(int prec, int recon, const DslashBatchTable &tab, const double *mask, int nblocks, bool dag,
+                    int epi, cudaStream_t s) {
+    if (prec == BQ_PREC_SINGLE) {
+        if (recon == 12) launch_tile_pr<BQ_PREC_SINGLE, 12>(tab, mask, nblocks, dag, epi, s);
+        else if (recon == 8) launch_tile_pr<BQ_PREC_SINGLE, 8>(tab, mask, nblocks, dag, epi, s);
+        else launch_tile_pr<BQ_PREC_SINGLE, 18>(tab, mask, nblocks, dag, epi, s);
+    } else if (prec == BQ_PREC_HALF) {
+        if (recon == 12) launch_tile_pr<BQ_PREC_HALF, 12>(tab, mask, nblocks, dag, epi, s);
+        else if (recon == 8) launch_tile_pr<BQ_PREC_HALF, 8>(tab, mask, nblocks, dag, epi, s);
+        else launch_tile_pr<BQ_PREC_HALF, 18>(tab, mask, nblocks, dag, epi, s);
+    }
+}

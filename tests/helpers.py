@@ -119,3 +119,24 @@ def two_plane_background(dims, c12, c34, m):
     U34, phi34 = abelian_background(dims, 2, 3, m, c34, "mu")
     U[:, 3] = U34[:, 3]
     return U, phi, phi34
+
+
+def pack_clover(dims, A_even, A_odd):
+    """The canonical clover field [V][2][36] (lex site order) of per-parity
+    [V/2][12][12] matrices: per site and chirality block (spin components 0, 1
+    and 2, 3) the 6 real diagonal entries, then the 15 complex entries above the
+    diagonal row by row (re, im). A re-layout of the matrices, no arithmetic."""
+    c = synth.lex_coords(dims)
+    V = synth.volume(dims)
+    par = c.sum(axis=1) % 2
+    h = np.arange(V) // 2
+    A = np.where((par == 0)[:, None, None], A_even[h], A_odd[h])
+    out = np.empty((V, 2, 36))
+    iu = np.triu_indices(6, 1)
+    for b in range(2):
+        B = A[:, 6 * b:6 * b + 6, 6 * b:6 * b + 6]
+        out[:, b, :6] = np.real(np.diagonal(B, axis1=1, axis2=2))
+        up = B[:, iu[0], iu[1]]
+        out[:, b, 6::2] = up.real
+        out[:, b, 7::2] = up.imag
+    return out

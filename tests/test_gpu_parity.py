@@ -51,6 +51,8 @@ CASES = [
     ("single", 12, 0.1, 0.0),
     ("half", 12, 0.0, 0.0),
     ("half", 18, 0.1, 2.0 / 3.0),
+    ("single", 8, 0.1, 0.0),
+    ("half", 8, 0.0, 0.0),
 ]
 
 
@@ -193,9 +195,10 @@ def test_error_codes(bq):
     assert e.value.status == bq.BQ_ERR_STATE
     bq.bq_set_gauge(lat.ctx, synth.gauge_field((4, 4, 4, 4), 0.2, 3))
     bq.bq_set_u1(lat.ctx, synth.u1_field((4, 4, 4, 4), 0.1, 4))
-    with pytest.raises(bq.BqError) as e:
-        bq.bq_set_recon(lat.ctx, "single", 12)
-    assert e.value.status == bq.BQ_ERR_ARG
+    for recon in (12, 8):
+        with pytest.raises(bq.BqError) as e:
+            bq.bq_set_recon(lat.ctx, "single", recon)
+        assert e.value.status == bq.BQ_ERR_ARG
     with pytest.raises(bq.BqError) as e:
         bq.bq_apply_mhat(lat.ctx, out, out, 0, "double")
     assert e.value.status == bq.BQ_ERR_ARG
@@ -204,6 +207,31 @@ def test_error_codes(bq):
     with pytest.raises(bq.BqError) as e:
         bq.bq_solve_cg(lat.ctx, x, b, tol=1e-10, max_iter=2)
     assert e.value.status == bq.BQ_ERR_NOT_CONVERGED
+    lat.close()
+
+
+def test_recon8_refusals(bq):
+    """8-real links: no FP64 storage, and a field with |U00| = 1 (the unit gauge,
+    where the storage is singular) is refused at link packing, not applied."""
+    lat = bq.Lattice((4, 4, 4, 4), 0.12, 1.0)
+    with pytest.raises(bq.BqError) as e:
+        bq.bq_set_recon(lat.ctx, "double", 8)
+    assert e.value.status == bq.BQ_ERR_ARG
+    bq.bq_set_gauge(lat.ctx, synth.unit_gauge((4, 4, 4, 4)))
+    bq.bq_set_recon(lat.ctx, "single", 8)
+    src = lat.pack(synth.gaussian_spinor(lat.Vh, 2), "single")
+    out = lat.spinor("single")
+    with pytest.raises(bq.BqError) as e:
+        bq.bq_apply_mhat(lat.ctx, out, src, 0, "single")
+    assert e.value.status == bq.BQ_ERR_ARG and "8-real" in str(e.value)
+    # the same context with a generic SU(3) field then works
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.3, 5)
+    bq.bq_set_gauge(lat.ctx, U)
+    bq.bq_apply_mhat(lat.ctx, out, src, 0, "single")
+    op = oracle.Operator(oracle.params(dims, kappa=0.12, csw=1.0, t_bc=-1.0), U)
+    psi = lat.unpack(src, "single")
+    assert rel(lat.unpack(out, "single"), op.mhat(psi)) < TOL["single"]
     lat.close()
 
 
@@ -480,7 +508,8 @@ def test_apply_error_report(bq, cfg, capsys):
     ref = oracle.mhat_sites(p, U, None, psi, sites)
     lines = []
     for prec, recon, arith in (("double", 18, "native"), ("double", 18, "df64"), ("double", 12, "df64"),
-                               ("single", 18, None), ("single", 12, None), ("half", 18, None), ("half", 12, None)):
+                               ("single", 18, None), ("single", 12, None), ("single", 8, None),
+                               ("half", 18, None), ("half", 12, None), ("half", 8, None)):
         bq.bq_set_recon(lat.ctx, prec, recon)
         if arith:
             bq.bq_set_fp64_arith(lat.ctx, arith)
@@ -735,7 +764,7 @@ def test_trace_samples(bq, prec, mu, charge):
     lat.close()
 
 
-@pytest.mark.parametrize("mapping", [-1, -2, 1, 2, 4, 8])
+@pytest.mark.parametrize("mapping", [-1, -2, -3, -4, -5, 1, 2, 4, 8])
 @pytest.mark.parametrize("prec", ["single", "half"])
 def test_batched_rhs_mappings(bq, mapping, prec):
     """Every mapping of right-hand sides onto threads (forced, not autotuned):

@@ -35,10 +35,35 @@ def test_noalloc_dot_matches_context_dot(bq, prec, dims):
         ref = bq.bq_spinor_dot(lat.ctx, na, nb, prec)
         got = bq.bq_spinor_dot_noalloc(na, nb, lat.Vh, prec)
         assert abs(got - ref) <= tol * abs(ref), (call, got, ref)
+        # against the plain definition: np.vdot of the stored values (unpacked to FP64)
+        exact = np.vdot(lat.unpack(na, prec), lat.unpack(nb, prec))
+        assert abs(got - exact) <= tol * np.linalg.norm(a) * np.linalg.norm(b), (call, got, exact)
+        # the same inputs give the same bits on every call
+        assert bq.bq_spinor_dot_noalloc(na, nb, lat.Vh, prec) == got
         got_self = bq.bq_spinor_dot_noalloc(na, na, lat.Vh, prec)
         ref_self = bq.bq_spinor_dot(lat.ctx, na, na, prec)
         assert abs(got_self - ref_self) <= tol * abs(ref_self)
         assert abs(got_self.imag) <= tol * abs(got_self)
+    lat.close()
+
+
+def test_noalloc_dot_at_the_size_limit(bq):
+    """4 194 304 sites: all 16 384 block partials of the static array in use and
+    the ticket counting up to its last value (FP16 storage keeps the buffers at
+    about 0.2 GB each)."""
+    dims = (32, 32, 32, 256)
+    lat = bq.Lattice(dims, 0.13)
+    assert lat.Vh == 4194304
+    for call in range(2):
+        a = synth.gaussian_spinor(lat.Vh, 30 + call)
+        b = synth.gaussian_spinor(lat.Vh, 40 + call)
+        na, nb = lat.pack(a, "half"), lat.pack(b, "half")
+        got = bq.bq_spinor_dot_noalloc(na, nb, lat.Vh, "half")
+        ref = bq.bq_spinor_dot(lat.ctx, na, nb, "half")
+        assert abs(got - ref) <= 1e-6 * abs(ref), (call, got, ref)
+        exact = np.vdot(lat.unpack(na, "half"), lat.unpack(nb, "half"))
+        assert abs(got - exact) <= 1e-6 * np.linalg.norm(a) * np.linalg.norm(b), (call, got, exact)
+        del na, nb
     lat.close()
 
 
