@@ -505,8 +505,14 @@ static int build_units(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int ma
             u->nr = e - s;
             u->log2R = log2_ceil(u->nr);
             u->interleave = m == -1 ? 1 : m == -2 ? 2 : m <= -3 ? 3 : 0;
-            // double-float FP64 launches of block-interleaved units run a lane pair per site
-            if (u->interleave == 1 && prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) u->interleave = 5;
+            if (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) {
+                // double-float FP64 launches: block-interleaved units with a lane pair per site; the
+                // intermediate vectors of the Mhat^dag Mhat (odd, and Mhat in) are float pairs
+                const int fmt[4] = {DF_OUT_PAIR, DF_IN_PAIR | DF_OUT_PAIR, DF_IN_PAIR | DF_OUT_PAIR,
+                                    DF_IN_PAIR | DF_X_PAIR};
+                u->interleave = 5;
+                u->a.fmt = fmt[k];
+            }
             for (int q = 0; q < u->nr; q++) {
                 BatchSlot *sl = &w->slot[s + q];
                 void *pv[8][3] = {{sl->p, sl->to_s, nullptr},  {sl->to_s, sl->te_s, sl->p},
@@ -559,7 +565,7 @@ static int mdagm_batch(bq_ctx *c0, int prec, int recon, int first_step, const Un
             // a single system: the plain kernel, no unit indirection (it is
             // active whenever this runs: the loop stops at convergence)
             const DslashUnit &u = tabs[0].units[0];
-            BQ_TRY(bq_dslash_launch(c0, prec, u.out[0], u.in[0], parity, dagger, epi, u.xin[0], u.a.k));
+            BQ_TRY(bq_dslash_launch(c0, prec, u.out[0], u.in[0], parity, dagger, epi, u.xin[0], u.a.k, u.a.fmt));
             continue;
         }
         for (size_t q = 0; q < tabs.size(); q++)

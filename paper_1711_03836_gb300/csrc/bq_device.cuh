@@ -726,4 +726,10 @@ struct DslashArgs {
     double cf, cb;  // time-hop factors forward / backward (e^{+mu}, e^{-mu}, swapped for the adjoint)
     double bc;      // time boundary sign
     double k;       // xpay coefficient
+    int fmt;        // double-float kernels: spinors stored as float pairs (DF_IN_PAIR | DF_X_PAIR | DF_OUT_PAIR)
 };
+
+// Storage of FP64 spinors that only the double-float kernels read and write (the
+// intermediate vectors of one Mhat or Mhat^dag Mhat): float4 [12][Vh] per
+// component (re.hi, re.lo, im.hi, im.lo), the bytes of FP64 without the split.
+enum { DF_IN_PAIR = 1, DF_X_PAIR = 2, DF_OUT_PAIR = 4 };

@@ -7,12 +7,11 @@
 #include "bq_device.cuh"
 
 // --------------------------------------------------------------------------
-// Double-float variant with the eight hops in a rolled loop. Unrolled, the
-// df64 hop code no longer fits the instruction cache (ncu: most issue slots
-// lost to instruction fetch); rolled, one copy serves all directions and the
-// direction-dependent projector becomes data: (1 + S gamma_mu) psi has upper
+// The direction-dependent projector as data: (1 + S gamma_mu) psi has upper
 // components h0 = psi0 + i^k0 psi_j0, h1 = psi1 + i^k1 psi_j1 and lower
-// components i^k2 u_m2, i^k3 u_m3 of the colour-multiplied pair (u0, u1).
+// components i^k2 u_m2, i^k3 u_m3 of the colour-multiplied pair (u0, u1), so
+// one rolled loop body serves all eight hops (unrolled, the double-float hop
+// code does not fit the instruction cache).
 
 __device__ __forceinline__ df dneg(df x, bool n) { return n ? df(-x.hi, -x.lo) : x; }
 
@@ -23,171 +22,6 @@ __device__ __forceinline__ cplx<df> mul_ipow(cplx<df> z, int k) {
     w.re = dneg(sw ? z.im : z.re, nre);
     w.im = dneg(sw ? z.re : z.im, nim);
     return w;
-}
-
-template <int RECON, bool DAG, int EPI>
-__device__ __forceinline__ void dslash_site_df64(const DslashArgs &a, const void *in, void *out, const void *xin,
-                                                 const int h) {
-    using T = df;
-    const int Lxh = a.Lxh, Vh = a.Vh;
-    const int xh = h % Lxh;
-    int r = h / Lxh;
-    const int y = r % a.L1;
-    r /= a.L1;
-    const int z = r % a.L2;
-    const int t = r / a.L2;
-    const int x = 2 * xh + ((a.parity + y + z + t) & 1);
-    const char *Lo = a.links + (size_t)a.parity * 4 * a.lblk;
-    const char *Li = a.links + (size_t)(1 - a.parity) * 4 * a.lblk;
-    constexpr int SF = DAG ? +1 : -1;
-    const int sy = Lxh, sz = Lxh * a.L1, st = sz * a.L2;
-    const T cf = T(t + 1 == a.L3 ? a.cf * a.bc : a.cf), cb = T(t == 0 ? a.cb * a.bc : a.cb);
-
-    cplx<T> acc[12];
-#pragma unroll
-    for (int c = 0; c < 12; c++) acc[c] = {T(0), T(0)};
-
-#pragma unroll 1
-    for (int d = 0; d < 8; d++) {
-        const int mu = d >> 1;
-        const bool back = d & 1;
-        const int S = back ? -SF : SF;
-        int hn;
-        switch (d) {
-            case 0: hn = h - xh + (((x + 1 == a.L0) ? 0 : x + 1) >> 1); break;
-            case 1: hn = h - xh + (((x == 0) ? a.L0 - 1 : x - 1) >> 1); break;
-            case 2: hn = (y + 1 == a.L1) ? h - (a.L1 - 1) * sy : h + sy; break;
-            case 3: hn = (y == 0) ? h + (a.L1 - 1) * sy : h - sy; break;
-            case 4: hn = (z + 1 == a.L2) ? h - (a.L2 - 1) * sz : h + sz; break;
-            case 5: hn = (z == 0) ? h + (a.L2 - 1) * sz : h - sz; break;
-            case 6: hn = (t + 1 == a.L3) ? h - (a.L3 - 1) * st : h + st; break;
-            default: hn = (t == 0) ? h + (a.L3 - 1) * st : h - st; break;
-        }
-        const char *lb = (back ? Li : Lo) + (size_t)mu * a.lblk;
-        const int hl = back ? hn : h;
-        // projector data
-        int j0, j1, k0, k1, m2, m3, k2, k3;
-        if (mu == 0) {
-            j0 = 3; j1 = 2; k0 = k1 = (S > 0) ? 3 : 1;
-            m2 = 1; m3 = 0; k2 = k3 = (S > 0) ? 1 : 3;
-        } else if (mu == 1) {
-            j0 = 3; j1 = 2; k0 = (S > 0) ? 2 : 0; k1 = (S > 0) ? 0 : 2;
-            m2 = 1; m3 = 0; k2 = (S > 0) ? 0 : 2; k3 = (S > 0) ? 2 : 0;
-        } else if (mu == 2) {
-            j0 = 2; j1 = 3; k0 = (S > 0) ? 3 : 1; k1 = (S > 0) ? 1 : 3;
-            m2 = 0; m3 = 1; k2 = (S > 0) ? 1 : 3; k3 = (S > 0) ? 3 : 1;
-        } else {
-            j0 = 2; j1 = 3; k0 = k1 = (S > 0) ? 0 : 2;
-            m2 = 0; m3 = 1; k2 = k3 = (S > 0) ? 0 : 2;
-        }
-        cplx<T> psi[12];
-        SpinorIO<BQ_PREC_DF64>::load(psi, in, hn, Vh);
-        cplx<T> h0[3], h1[3];
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const cplx<T> pa = mul_ipow((j0 == 3) ? psi[9 + c] : psi[6 + c], k0);
-            const cplx<T> pb = mul_ipow((j1 == 3) ? psi[9 + c] : psi[6 + c], k1);
-            h0[c] = {add_lazy(psi[c].re, pa.re), add_lazy(psi[c].im, pa.im)};
-            h1[c] = {add_lazy(psi[3 + c].re, pb.re), add_lazy(psi[3 + c].im, pb.im)};
-        }
-        cplx<T> U[9];
-        LinkIO<BQ_PREC_DF64, RECON>::load(U, lb, hl, Vh);
-        if (back) {  // U^dagger in registers, so that one mat-vec serves both directions
-#pragma unroll
-            for (int aa = 0; aa < 3; aa++) {
-                U[aa * 4] = cconj(U[aa * 4]);
-#pragma unroll
-                for (int b = aa + 1; b < 3; b++) {
-                    const cplx<T> tmp = U[aa * 3 + b];
-                    U[aa * 3 + b] = cconj(U[b * 3 + aa]);
-                    U[b * 3 + aa] = cconj(tmp);
-                }
-            }
-        }
-        // each colour component: a lazy sum of six products per real part (twelve
-        // independent sums per hop keep the FP32 pipe busy at three warps per scheduler)
-        cplx<T> u0[3], u1[3];
-#pragma unroll
-        for (int aa = 0; aa < 3; aa++) {
-            dfsum r0 = dfs_prod(U[aa * 3].re, h0[0].re), i0 = dfs_prod(U[aa * 3].re, h0[0].im);
-            dfsum r1 = dfs_prod(U[aa * 3].re, h1[0].re), i1 = dfs_prod(U[aa * 3].re, h1[0].im);
-            dfs_add_prod(r0, -U[aa * 3].im, h0[0].im);
-            dfs_add_prod(i0, U[aa * 3].im, h0[0].re);
-            dfs_add_prod(r1, -U[aa * 3].im, h1[0].im);
-            dfs_add_prod(i1, U[aa * 3].im, h1[0].re);
-#pragma unroll
-            for (int b = 1; b < 3; b++) {
-                const cplx<T> w = U[aa * 3 + b];
-                dfs_add_prod(r0, w.re, h0[b].re);
-                dfs_add_prod(r0, -w.im, h0[b].im);
-                dfs_add_prod(i0, w.re, h0[b].im);
-                dfs_add_prod(i0, w.im, h0[b].re);
-                dfs_add_prod(r1, w.re, h1[b].re);
-                dfs_add_prod(r1, -w.im, h1[b].im);
-                dfs_add_prod(i1, w.re, h1[b].im);
-                dfs_add_prod(i1, w.im, h1[b].re);
-            }
-            u0[aa] = {dfs_done(r0), dfs_done(i0)};
-            u1[aa] = {dfs_done(r1), dfs_done(i1)};
-        }
-        if (mu == 3) {
-            const T coef = back ? cb : cf;
-#pragma unroll
-            for (int aa = 0; aa < 3; aa++) {
-                u0[aa] = cscale(coef, u0[aa]);
-                u1[aa] = cscale(coef, u1[aa]);
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const cplx<T> l2 = mul_ipow(m2 ? u1[c] : u0[c], k2), l3 = mul_ipow(m3 ? u1[c] : u0[c], k3);
-            acc[c] = {add_lazy(acc[c].re, u0[c].re), add_lazy(acc[c].im, u0[c].im)};
-            acc[3 + c] = {add_lazy(acc[3 + c].re, u1[c].re), add_lazy(acc[3 + c].im, u1[c].im)};
-            acc[6 + c] = {add_lazy(acc[6 + c].re, l2.re), add_lazy(acc[6 + c].im, l2.im)};
-            acc[9 + c] = {add_lazy(acc[9 + c].re, l3.re), add_lazy(acc[9 + c].im, l3.im)};
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 12; c++) acc[c] = {normalise(acc[c].re), normalise(acc[c].im)};
-
-    if (EPI == EPI_PLAIN) {
-        SpinorIO<BQ_PREC_DF64>::store(out, h, Vh, acc);
-        return;
-    }
-    // clover epilogue one chirality block (spin components 6b .. 6b + 5) at a
-    // time in a rolled loop: one copy of the 6x6 block code instead of two keeps
-    // the kernel inside the instruction cache
-    const T k = (T)a.k;
-#pragma unroll 1
-    for (int b = 0; b < 2; b++) {
-        T d[6];
-        cplx<T> o[15], xb[6], ab[6], yb[6];
-        CloverIO<BQ_PREC_DF64>::load_block(d, o, a.clov, b, h, Vh);
-#pragma unroll
-        for (int i = 0; i < 6; i++) ab[i] = b ? acc[6 + i] : acc[i];
-        if (EPI == EPI_CLOVINV) {
-#pragma unroll
-            for (int i = 0; i < 6; i++) xb[i] = ab[i];
-        } else {
-            const double2 *px = static_cast<const double2 *>(xin) + (size_t)(6 * b) * Vh + h;
-#pragma unroll
-            for (int i = 0; i < 6; i++) {
-                const double2 v = ldg(px + (size_t)i * Vh);
-                xb[i] = {df_from_double(v.x), df_from_double(v.y)};
-            }
-        }
-        herm6_apply(d, o, xb, yb);
-        if (EPI == EPI_XPAY) {
-#pragma unroll
-            for (int i = 0; i < 6; i++) {
-                yb[i].re = fma(-k, ab[i].re, yb[i].re);
-                yb[i].im = fma(-k, ab[i].im, yb[i].im);
-            }
-        }
-        double2 *po = static_cast<double2 *>(out) + (size_t)(6 * b) * Vh + h;
-#pragma unroll
-        for (int i = 0; i < 6; i++) po[(size_t)i * Vh] = make_double2(df_to_double(yb[i].re), df_to_double(yb[i].im));
-    }
 }
 
 // --------------------------------------------------------------------------
@@ -210,7 +44,9 @@ __device__ __forceinline__ df dshfl(df v) {
     return df(__shfl_xor_sync(0xffffffffu, v.hi, 1), __shfl_xor_sync(0xffffffffu, v.lo, 1));
 }
 
-template <int RECON, bool DAG, int EPI>
+// FMT: DF_IN_PAIR / DF_X_PAIR / DF_OUT_PAIR select float-pair storage for the
+// hopped spinor, the xpay spinor and the output (FP64 otherwise)
+template <int RECON, bool DAG, int EPI, int FMT>
 __device__ __forceinline__ void dslash_site_df64_pair(const DslashArgs &a, const void *in, void *out, const void *xin,
                                                       const int h, const int q, const bool valid) {
     using T = df;
@@ -279,10 +115,19 @@ __device__ __forceinline__ void dslash_site_df64_pair(const DslashArgs &a, const
         cplx<T> hq[3];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            const double2 vq = ldg(pin + (size_t)(3 * q + c) * Vh + hn);
-            const double2 vj = ldg(pin + (size_t)(3 * jq + c) * Vh + hn);
-            const cplx<T> pj = mul_ipow(cplx<T>{df_from_double(vj.x), df_from_double(vj.y)}, kq);
-            hq[c] = {add_lazy(df_from_double(vq.x), pj.re), add_lazy(df_from_double(vq.y), pj.im)};
+            cplx<T> pq, pj;
+            if constexpr (FMT & DF_IN_PAIR) {
+                const float4 *pp = static_cast<const float4 *>(in);
+                const float4 vq = ldg(pp + (size_t)(3 * q + c) * Vh + hn), vj = ldg(pp + (size_t)(3 * jq + c) * Vh + hn);
+                pq = {T(vq.x, vq.y), T(vq.z, vq.w)};
+                pj = {T(vj.x, vj.y), T(vj.z, vj.w)};
+            } else {
+                const double2 vq = ldg(pin + (size_t)(3 * q + c) * Vh + hn), vj = ldg(pin + (size_t)(3 * jq + c) * Vh + hn);
+                pq = {df_from_double(vq.x), df_from_double(vq.y)};
+                pj = {df_from_double(vj.x), df_from_double(vj.y)};
+            }
+            pj = mul_ipow(pj, kq);
+            hq[c] = {add_lazy(pq.re, pj.re), add_lazy(pq.im, pj.im)};
         }
         // U h_q (or U^dag h_q): 18-real links one row (or column) at a time; 12-real
         // links whole, the third row rebuilt
@@ -344,9 +189,13 @@ __device__ __forceinline__ void dslash_site_df64_pair(const DslashArgs &a, const
     }
     if (!valid) return;
     double2 *po = static_cast<double2 *>(out) + (size_t)(6 * q) * Vh + h;
+    float4 *po4 = static_cast<float4 *>(out) + (size_t)(6 * q) * Vh + h;
     if (EPI == EPI_PLAIN) {
 #pragma unroll
-        for (int i = 0; i < 6; i++) po[(size_t)i * Vh] = make_double2(df_to_double(ab[i].re), df_to_double(ab[i].im));
+        for (int i = 0; i < 6; i++) {
+            if constexpr (FMT & DF_OUT_PAIR) po4[(size_t)i * Vh] = make_float4(ab[i].re.hi, ab[i].re.lo, ab[i].im.hi, ab[i].im.lo);
+            else po[(size_t)i * Vh] = make_double2(df_to_double(ab[i].re), df_to_double(ab[i].im));
+        }
         return;
     }
     // the clover block of this lane, row by row (an off-diagonal entry is read for
@@ -355,6 +204,13 @@ __device__ __forceinline__ void dslash_site_df64_pair(const DslashArgs &a, const
     if (EPI == EPI_CLOVINV) {
 #pragma unroll
         for (int i = 0; i < 6; i++) xb[i] = ab[i];
+    } else if constexpr (FMT & DF_X_PAIR) {
+        const float4 *px = static_cast<const float4 *>(xin) + (size_t)(6 * q) * Vh + h;
+#pragma unroll
+        for (int i = 0; i < 6; i++) {
+            const float4 v = ldg(px + (size_t)i * Vh);
+            xb[i] = {T(v.x, v.y), T(v.z, v.w)};
+        }
     } else {
         const double2 *px = static_cast<const double2 *>(xin) + (size_t)(6 * q) * Vh + h;
 #pragma unroll
@@ -387,14 +243,32 @@ __device__ __forceinline__ void dslash_site_df64_pair(const DslashArgs &a, const
             yi.re = fma(-k, ab[i].re, yi.re);
             yi.im = fma(-k, ab[i].im, yi.im);
         }
-        po[(size_t)i * Vh] = make_double2(df_to_double(yi.re), df_to_double(yi.im));
+        if constexpr (FMT & DF_OUT_PAIR) po4[(size_t)i * Vh] = make_float4(yi.re.hi, yi.re.lo, yi.im.hi, yi.im.lo);
+        else po[(size_t)i * Vh] = make_double2(df_to_double(yi.re), df_to_double(yi.im));
     }
 }
 
-template <int RECON, bool DAG, int EPI>
+template <int RECON, bool DAG, int EPI, int FMT>
 __global__ void __launch_bounds__(128, DF64P_MIN_BLOCKS) k_dslash_df64p(const DslashArgs a) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int h = t >> 1;
     const bool valid = h < a.Vh;
-    dslash_site_df64_pair<RECON, DAG, EPI>(a, a.in, a.out, a.xin, valid ? h : a.Vh - 1, t & 1, valid);
+    dslash_site_df64_pair<RECON, DAG, EPI, FMT>(a, a.in, a.out, a.xin, valid ? h : a.Vh - 1, t & 1, valid);
+}
+
+// batched launch with a lane pair per site (interleave 5): block bl takes
+// right-hand side bl % nr and the 64 sites of site block bl / nr
+template <int RECON, bool DAG, int EPI, int FMT>
+__global__ void __launch_bounds__(128, DF64P_MIN_BLOCKS) k_dslash_batch_df64p(const __grid_constant__ DslashBatchTable tab,
+                                                                              const double *mask) {
+    int u = 0;
+    while (u + 1 < tab.nunits && tab.block0[u + 1] <= (int)blockIdx.x) u++;
+    const DslashUnit &U = tab.units[u];
+    const int bl = (int)blockIdx.x - tab.block0[u];
+    const int r = bl % U.nr;
+    if (mask && mask[U.sys[r]] == 0.0) return;  // the whole block: one right-hand side
+    const int h = (bl / U.nr) * 64 + (int)(threadIdx.x >> 1);
+    const bool valid = h < U.a.Vh;
+    dslash_site_df64_pair<RECON, DAG, EPI, FMT>(U.a, U.in[r], U.out[r], U.xin[r], valid ? h : U.a.Vh - 1,
+                                                (int)(threadIdx.x & 1), valid);
 }

@@ -24,10 +24,6 @@ template <int PREC>
 struct BatchMinBlocks {
     static constexpr int value = BATCH_MIN_BLOCKS;
 };
-template <>
-struct BatchMinBlocks<BQ_PREC_DF64> {
-    static constexpr int value = DF64_MIN_BLOCKS;
-};
 
 template <int PREC, int RECON, bool DAG, int EPI>
 __global__ void __launch_bounds__(128, BatchMinBlocks<PREC>::value) k_dslash_batch(const __grid_constant__ DslashBatchTable tab, const double *mask) {
@@ -52,23 +48,6 @@ __global__ void __launch_bounds__(128, BatchMinBlocks<PREC>::value) k_dslash_bat
     if (r >= U.nr || h >= U.a.Vh) return;
     if (mask && mask[U.sys[r]] == 0.0) return;
     dslash_any<PREC, RECON, DAG, EPI>(U.a, U.in[r], U.out[r], U.xin[r], h);
-}
-
-// Double-float batched launch with a lane pair per site (interleave 5): block bl
-// takes right-hand side bl % nr and the 64 sites of site block bl / nr.
-template <int RECON, bool DAG, int EPI>
-__global__ void __launch_bounds__(128, DF64P_MIN_BLOCKS) k_dslash_batch_df64p(const __grid_constant__ DslashBatchTable tab,
-                                                                              const double *mask) {
-    int u = 0;
-    while (u + 1 < tab.nunits && tab.block0[u + 1] <= (int)blockIdx.x) u++;
-    const DslashUnit &U = tab.units[u];
-    const int bl = (int)blockIdx.x - tab.block0[u];
-    const int r = bl % U.nr;
-    if (mask && mask[U.sys[r]] == 0.0) return;  // the whole block: one right-hand side
-    const int h = (bl / U.nr) * 64 + (int)(threadIdx.x >> 1);
-    const bool valid = h < U.a.Vh;
-    dslash_site_df64_pair<RECON, DAG, EPI>(U.a, U.in[r], U.out[r], U.xin[r], valid ? h : U.a.Vh - 1,
-                                           (int)(threadIdx.x & 1), valid);
 }
 
 template <int PREC>
@@ -108,26 +87,13 @@ static void launch_dslash_pr(const DslashArgs &a, bool dag, int epi, unsigned gr
     }
 }
 
-template <int RECON>
-static void launch_df64p(const DslashArgs &a, bool dag, int epi, unsigned grid, cudaStream_t s) {
-    if (dag) {
-        if (epi == EPI_PLAIN) k_dslash_df64p<RECON, true, EPI_PLAIN><<<grid, 128, 0, s>>>(a);
-        else if (epi == EPI_CLOVINV) k_dslash_df64p<RECON, true, EPI_CLOVINV><<<grid, 128, 0, s>>>(a);
-        else k_dslash_df64p<RECON, true, EPI_XPAY><<<grid, 128, 0, s>>>(a);
-    } else {
-        if (epi == EPI_PLAIN) k_dslash_df64p<RECON, false, EPI_PLAIN><<<grid, 128, 0, s>>>(a);
-        else if (epi == EPI_CLOVINV) k_dslash_df64p<RECON, false, EPI_CLOVINV><<<grid, 128, 0, s>>>(a);
-        else k_dslash_df64p<RECON, false, EPI_XPAY><<<grid, 128, 0, s>>>(a);
-    }
-}
-
 // storage of the links and clover a launch at precision prec reads
 static int field_store(const bq_ctx *c, int prec) {
     return (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) ? (int)BQ_PREC_DF64 : prec;
 }
 
 int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_parity, int dagger, int epi,
-                     const void *xin, double k) {
+                     const void *xin, double k, int fmt) {
     const int fs = field_store(c, prec);
     BQ_TRY(bq_prepare_links(c, fs));
     if (epi != EPI_PLAIN) BQ_TRY(bq_prepare_clover(c, fs));
@@ -152,6 +118,7 @@ int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_par
     a.cb = dagger ? ef : eb;
     a.bc = c->params.t_bc;
     a.k = k;
+    a.fmt = (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) ? fmt : 0;
     unsigned grid = (unsigned)((c->Vh + 127) / 128);
     int recon = c->links_recon[fs];
     int slot = -1;
@@ -167,10 +134,8 @@ int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_par
         c->ev_bucket[slot] = prec * 3 + epi;
         BQ_CUDA_TRY(bq_event_record(c, c->ev[2 * slot]));
     }
-    if (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) {  // a lane pair per site
-        const unsigned grid2 = (unsigned)((2LL * c->Vh + 127) / 128);
-        if (recon == 12) launch_df64p<12>(a, dagger, epi, grid2, c->stream);
-        else launch_df64p<18>(a, dagger, epi, grid2, c->stream);
+    if (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) {  // a lane pair per site (bq_df64.cu)
+        BQ_TRY(bq_df64p_launch(recon, a, dagger, epi, (unsigned)((2LL * c->Vh + 127) / 128), c->stream));
     } else if (prec == BQ_PREC_DOUBLE) {
         if (recon == 12) launch_dslash_pr<BQ_PREC_DOUBLE, 12>(a, dagger, epi, grid, c->stream);
         else launch_dslash_pr<BQ_PREC_DOUBLE, 18>(a, dagger, epi, grid, c->stream);
@@ -245,20 +210,6 @@ extern "C" int bq_get_counters(bq_ctx *c, bq_counters *out) {
 template <int PREC, int RECON>
 static void launch_batch_pr(const DslashBatchTable &tab, const double *mask, int nblocks, bool dag, int epi,
                             cudaStream_t s) {
-    if constexpr (PREC == BQ_PREC_DF64) {
-        if (tab.nunits > 0 && tab.units[0].interleave == 5) {  // a lane pair per site
-            if (dag) {
-                if (epi == EPI_PLAIN) k_dslash_batch_df64p<RECON, true, EPI_PLAIN><<<nblocks, 128, 0, s>>>(tab, mask);
-                else if (epi == EPI_CLOVINV) k_dslash_batch_df64p<RECON, true, EPI_CLOVINV><<<nblocks, 128, 0, s>>>(tab, mask);
-                else k_dslash_batch_df64p<RECON, true, EPI_XPAY><<<nblocks, 128, 0, s>>>(tab, mask);
-            } else {
-                if (epi == EPI_PLAIN) k_dslash_batch_df64p<RECON, false, EPI_PLAIN><<<nblocks, 128, 0, s>>>(tab, mask);
-                else if (epi == EPI_CLOVINV) k_dslash_batch_df64p<RECON, false, EPI_CLOVINV><<<nblocks, 128, 0, s>>>(tab, mask);
-                else k_dslash_batch_df64p<RECON, false, EPI_XPAY><<<nblocks, 128, 0, s>>>(tab, mask);
-            }
-            return;
-        }
-    }
     if (tab.nunits > 0 && tab.units[0].interleave == 3) {  // shared-memory tiles (bq_tile.cu)
         bq_tile_launch(PREC, RECON, tab, mask, nblocks, dag, epi, s);
         return;
@@ -300,6 +251,7 @@ int bq_dslash_unit_fill(bq_ctx *c, int prec, int out_parity, int dagger, int epi
     a->cb = dagger ? ef : eb;
     a->bc = c->params.t_bc;
     a->k = k;
+    a->fmt = 0;
     return BQ_OK;
 }
 
@@ -323,9 +275,8 @@ int bq_dslash_batch_launch(bq_ctx *c, int prec, int recon, const DslashBatchTabl
         BQ_CUDA_TRY(bq_event_record(c, c->ev[2 * slot]));
     }
     cudaStream_t s = c->stream;
-    if (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) {
-        if (recon == 12) launch_batch_pr<BQ_PREC_DF64, 12>(*tab, mask, nblocks, dagger, epi, s);
-        else launch_batch_pr<BQ_PREC_DF64, 18>(*tab, mask, nblocks, dagger, epi, s);
+    if (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) {  // lane pairs per site (bq_df64.cu)
+        BQ_TRY(bq_df64p_batch_launch(recon, *tab, mask, nblocks, dagger, epi, s));
     } else if (prec == BQ_PREC_DOUBLE) {
         if (recon == 12) launch_batch_pr<BQ_PREC_DOUBLE, 12>(*tab, mask, nblocks, dagger, epi, s);
         else launch_batch_pr<BQ_PREC_DOUBLE, 18>(*tab, mask, nblocks, dagger, epi, s);
@@ -362,16 +313,22 @@ int bq_clover_launch(bq_ctx *c, int prec, void *out, const void *in, int parity,
     return BQ_OK;
 }
 
-// Mhat in = A_ee in - kappa^2 D_eo A_oo^{-1} D_oe in (adjoint: D -> D^dagger, A Hermitian)
+// Mhat in = A_ee in - kappa^2 D_eo A_oo^{-1} D_oe in (adjoint: D -> D^dagger, A Hermitian).
+// With double-float arithmetic the odd intermediate is stored as float pairs.
 int bq_mhat_launch(bq_ctx *c, int prec, void *out, const void *in, int dagger, void *tmp_odd) {
-    BQ_TRY(bq_dslash_launch(c, prec, tmp_odd, in, 1, dagger, EPI_CLOVINV, nullptr, 0.0));
+    BQ_TRY(bq_dslash_launch(c, prec, tmp_odd, in, 1, dagger, EPI_CLOVINV, nullptr, 0.0, DF_OUT_PAIR));
     double k2 = c->params.kappa * c->params.kappa;
-    return bq_dslash_launch(c, prec, out, tmp_odd, 0, dagger, EPI_XPAY, in, k2);
+    return bq_dslash_launch(c, prec, out, tmp_odd, 0, dagger, EPI_XPAY, in, k2, DF_IN_PAIR);
 }
 
+// Mhat^dag Mhat in; with double-float arithmetic every intermediate (odd
+// vectors and Mhat in) is stored as float pairs, only in and out are FP64
 int bq_mdagm_launch(bq_ctx *c, int prec, void *out, const void *in, void *tmp_odd, void *tmp_even) {
-    BQ_TRY(bq_mhat_launch(c, prec, tmp_even, in, 0, tmp_odd));
-    return bq_mhat_launch(c, prec, out, tmp_even, 1, tmp_odd);
+    const double k2 = c->params.kappa * c->params.kappa;
+    BQ_TRY(bq_dslash_launch(c, prec, tmp_odd, in, 1, 0, EPI_CLOVINV, nullptr, 0.0, DF_OUT_PAIR));
+    BQ_TRY(bq_dslash_launch(c, prec, tmp_even, tmp_odd, 0, 0, EPI_XPAY, in, k2, DF_IN_PAIR | DF_OUT_PAIR));
+    BQ_TRY(bq_dslash_launch(c, prec, tmp_odd, tmp_even, 1, 1, EPI_CLOVINV, nullptr, 0.0, DF_IN_PAIR | DF_OUT_PAIR));
+    return bq_dslash_launch(c, prec, out, tmp_odd, 0, 1, EPI_XPAY, tmp_even, k2, DF_IN_PAIR | DF_X_PAIR);
 }
 
 int bq_workspace(bq_ctx *c, int prec) {

@@ -147,8 +147,13 @@ struct DslashBatchTable {
 };
 
 // operator launches (bq_dslash.cu)
+// fmt: DF_* storage flags of the double-float kernels (ignored by the other arithmetics)
 int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_parity, int dagger, int epi,
-                     const void *xin, double k);
+                     const void *xin, double k, int fmt = 0);
+// double-float lane-pair kernels (bq_df64.cu); BQ_ERR_ARG for a storage combination without a kernel
+int bq_df64p_launch(int recon, const DslashArgs &a, bool dag, int epi, unsigned grid, cudaStream_t s);
+int bq_df64p_batch_launch(int recon, const DslashBatchTable &tab, const double *mask, int nblocks, bool dag, int epi,
+                          cudaStream_t s);
 int bq_clover_launch(bq_ctx *c, int prec, void *out, const void *in, int parity, int inverse);
 int bq_mhat_launch(bq_ctx *c, int prec, void *out, const void *in, int dagger, void *tmp_odd);
 int bq_mdagm_launch(bq_ctx *c, int prec, void *out, const void *in, void *tmp_odd, void *tmp_even);

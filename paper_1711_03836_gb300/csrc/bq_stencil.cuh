@@ -14,9 +14,6 @@
 
 #include "bq_device.cuh"
 
-#ifndef DF64_MIN_BLOCKS
-#define DF64_MIN_BLOCKS 3
-#endif
 
 // (1 + S gamma_mu) psi = (h0, h1, ...) in the chiral basis: the projection ...
 template <int MU, int S, typename T>
@@ -221,19 +218,13 @@ __device__ __forceinline__ void dslash_site(const DslashArgs &a, const void *in,
 }
 
 
-#include "bq_df64.cuh"
-
 template <int PREC, int RECON, bool DAG, int EPI>
 __device__ __forceinline__ void dslash_any(const DslashArgs &a, const void *in, void *out, const void *xin,
                                            const int h) {
-    if (PREC == BQ_PREC_DF64)
-        dslash_site_df64<RECON, DAG, EPI>(a, in, out, xin, h);
-    else
-        dslash_site<PREC, RECON, DAG, EPI>(a, in, out, xin, h);
+    static_assert(PREC != BQ_PREC_DF64, "double-float storage runs the lane-pair kernels of bq_df64.cuh");
+    dslash_site<PREC, RECON, DAG, EPI>(a, in, out, xin, h);
 }
 
-// double-float kernels carry ~2x the live state; without a cap they sit at 255
-// registers and two resident blocks, too few warps to hide their dependent chains
 // Measured at 32^3x64: FP32 runs best at four 128-thread blocks per SM (128
 // registers, no spills; 5-10 % faster than five blocks with spilling), FP16
 // storage at five (96 registers).
@@ -255,11 +246,6 @@ template <>
 struct DslashMinBlocks<BQ_PREC_DOUBLE> {  // FP64-unit bound: no cap
     static constexpr int value = 1;
 };
-template <>
-struct DslashMinBlocks<BQ_PREC_DF64> {
-    static constexpr int value = DF64_MIN_BLOCKS;
-};
-
 template <int PREC, int RECON, bool DAG, int EPI>
 __global__ void __launch_bounds__(128, DslashMinBlocks<PREC>::value) k_dslash(const DslashArgs a) {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;

@@ -85,7 +85,9 @@ __device__ __forceinline__ void hop_link(cplx<float> acc[12], const void *in, in
         accumulate<MU, S>(acc, u0, u1);
 }
 
-// link d of the tile's site `lane`: 9 complex as 5 float4 (the last half unused), [8][5][TILE_SITES]
+// link d of the tile's site `lane`: 9 complex as 5 float4 (the last half unused),
+// [8][5][TILE_SITES]. (Keeping 12-real links as 3 float4 and rebuilding row 2 per
+// right-hand side was measured: no faster in FP32, slower in FP16.)
 __device__ __forceinline__ void tile_link(cplx<float> U[9], const float4 *sL, int d, int lane) {
     const float4 *p = sL + d * 5 * TILE_SITES + lane;
     const float4 v0 = p[0], v1 = p[TILE_SITES], v2 = p[2 * TILE_SITES], v3 = p[3 * TILE_SITES],
@@ -164,7 +166,7 @@ __device__ __forceinline__ void stage_clover(float4 *sC, const void *clov, int h
     }
 }
 
-template <int PREC, bool DAG, int EPI>
+template <int PREC, int RECON, bool DAG, int EPI>
 __device__ __forceinline__ void dslash_site_tile(const DslashArgs &a, const SiteNb &nb, const void *in, void *out,
                                                  const void *xin, int h, const float4 *sL, const float4 *sC,
                                                  int lane) {
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(128, MB) k_dslash_tile(const __grid_constant__
     const SiteNb nb = site_neighbours(U.a, h);
     for (int r = warp; r < U.nr; r += nw) {
         if (mask && mask[U.sys[r]] == 0.0) continue;
-        dslash_site_tile<PREC, DAG, EPI>(U.a, nb, U.in[r], U.out[r], U.xin[r], h, sL, sC, lane);
+        dslash_site_tile<PREC, RECON, DAG, EPI>(U.a, nb, U.in[r], U.out[r], U.xin[r], h, sL, sC, lane);
     }
 }
 
