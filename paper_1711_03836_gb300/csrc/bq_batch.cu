@@ -266,28 +266,46 @@ struct GraphRun {
 // Krylov recurrences (bodies in bq_ms.cuh), one grid row per right-hand side
 
 struct MSBArgs {
-    const MSPtrs *ptr;  // [nsys] per-shift solutions and directions
+    const MSPtrs *ptr;  // [nsys] per-shift solutions, directions and the residual ring
     double *ms;         // [nsys][M_NTOTAL]
+    double *mh;         // [nsys][MH_TOTAL] chunk history and coefficients
 };
 
 template <int PR>
-__global__ void __launch_bounds__(RED_THREADS) kbm_init(BArgs ba, MSBArgs m, int n, int base) {
+__global__ void __launch_bounds__(RED_THREADS) kbm_init(BArgs ba, MSBArgs m, int n) {
     BATCH_PROLOGUE
-    ms_init_body<PR>(sv.b, m.ptr[sy], n, base, Vh);
+    ms_init_body<PR>(sv.b, m.ptr[sy], n, Vh);
 }
 
+// residual slot src -> dst, history row t
 template <int PS, int PR>
-__global__ void __launch_bounds__(RED_THREADS) kbm_residual(BArgs ba, MSBArgs m, int n, int base) {
+__global__ void __launch_bounds__(RED_THREADS) kbm_residual(BArgs ba, MSBArgs m, int n, int base, int src, int dst,
+                                                            int t) {
     BATCH_PROLOGUE
     double *ms = m.ms + (size_t)sy * M_NTOTAL;
+    double *hist_t = m.mh + (size_t)sy * MH_TOTAL + (size_t)t * MH_N * MS_MAX;
     const RedArgs ra{part, tick, scal, Vh};
-    ms_residual_body<PS, PR>(sv.Ap, sv.rs, ra, ms, n, base, ms[M_TOL2]);
+    ms_residual_body<PS, PR>(sv.Ap, ms_slot(m.ptr[sy], src), ms_slot(m.ptr[sy], dst), ra, ms, hist_t, n, base,
+                             ms[M_TOL2]);
 }
 
 template <int PS, int PR>
-__global__ void __launch_bounds__(RED_THREADS) kbm_update(BArgs ba, MSBArgs m, int n, int base) {
+__global__ void __launch_bounds__(RED_THREADS) kbm_pupdate(BArgs ba, MSBArgs m, int dst) {
     BATCH_PROLOGUE
-    ms_update_body<PS, PR>(sv.p, sv.rs, m.ptr[sy], m.ms + (size_t)sy * M_NTOTAL, scal, n, base, Vh);
+    ms_pupdate_body<PS, PR>(sv.p, ms_slot(m.ptr[sy], dst), scal, Vh);
+}
+
+// coefficients of the chunk (T iterations) of every system: one block per system
+__global__ void kbm_coef(MSBArgs m, int n, int T) {
+    const double *mh = m.mh + (size_t)blockIdx.x * MH_TOTAL;
+    ms_coef_body(mh, m.mh + (size_t)blockIdx.x * MH_TOTAL + MH_HIST, n, T);
+}
+
+// apply the chunk to x_k and p_k of the systems flagged in ba.mask (grid row = system)
+template <int PR>
+__global__ void __launch_bounds__(RED_THREADS) kbm_flush(BArgs ba, MSBArgs m, int n, int T, int slot0) {
+    BATCH_PROLOGUE
+    ms_flush_body<PR>(m.ptr[sy], m.mh + (size_t)sy * MH_TOTAL + MH_HIST, n, T, slot0, Vh);
 }
 
 // x (FP64) = y (precision PR)
@@ -332,11 +350,13 @@ struct BatchWork {
     GraphRun graph;
     unsigned long long graph_sig;
     int graph_gen;
-    // block multishift: per (rhs, shift) vectors at precision ms_prec, device pointer tables, scalars
-    std::vector<char *> ms_vec;  // [rhs][MS_MAX][2] (x, p)
+    // block multishift: per (rhs, shift) vectors at precision ms_prec, the per-rhs residual
+    // ring, device pointer tables, scalars and chunk histories
+    std::vector<char *> ms_vec;   // [rhs][MS_MAX][2] (x, p)
+    std::vector<char *> ms_hist;  // [rhs]: MS_SLOTS residual vectors
     int ms_prec, ms_Vh;
     MSPtrs *d_msv;
-    double *d_ms, *h_ms;
+    double *d_ms, *h_ms, *d_mh;
     int ms_cap;
 };
 
@@ -374,8 +394,10 @@ void bq_batch_free(bq_ctx *c) {
     if (w->t1) cudaEventDestroy(w->t1);
     if (w->graph.exec) cudaGraphExecDestroy(w->graph.exec);
     for (char *v : w->ms_vec) cudaFree(v);
+    for (char *v : w->ms_hist) cudaFree(v);
     cudaFree(w->d_msv);
     cudaFree(w->d_ms);
+    cudaFree(w->d_mh);
     cudaFreeHost(w->h_ms);
     delete w;
     c->batch = nullptr;
@@ -1089,11 +1111,14 @@ static int ms_block_run(bq_ctx *c0, int nrhs, int n, const double *shifts, int b
     const size_t vb = spinor_bytes_per_site(PR) * (size_t)Vh;
     if (w->ms_prec != PR || w->ms_Vh != Vh) {
         for (char *v : w->ms_vec) cudaFree(v);
+        for (char *v : w->ms_hist) cudaFree(v);
         w->ms_vec.clear();
+        w->ms_hist.clear();
         w->ms_prec = PR;
         w->ms_Vh = Vh;
     }
     if ((int)w->ms_vec.size() < nrhs * MS_MAX * 2) w->ms_vec.resize((size_t)nrhs * MS_MAX * 2, nullptr);
+    if ((int)w->ms_hist.size() < nrhs) w->ms_hist.resize(nrhs, nullptr);
     std::vector<MSPtrs> hp(nrhs);
     for (int r = 0; r < nrhs; r++) {
         for (int k = 0; k < MS_MAX; k++) {
@@ -1101,22 +1126,25 @@ static int ms_block_run(bq_ctx *c0, int nrhs, int n, const double *shifts, int b
             if (k >= n) continue;
             char **xv = &w->ms_vec[((size_t)r * MS_MAX + k) * 2], **pv = xv + 1;
             BQ_TRY(bq_alloc((void **)xv, vb));
+            BQ_TRY(bq_alloc((void **)pv, vb));
             hp[r].x[k] = *xv;
-            if (k != base) {
-                BQ_TRY(bq_alloc((void **)pv, vb));
-                hp[r].p[k] = *pv;
-            }
+            hp[r].p[k] = *pv;
         }
+        BQ_TRY(bq_alloc((void **)&w->ms_hist[r], vb * MS_SLOTS));
+        hp[r].hist = w->ms_hist[r];
+        hp[r].hstride = (long long)vb;
     }
     if (w->ms_cap < nrhs) {
         cudaFree(w->d_msv);
         cudaFree(w->d_ms);
+        cudaFree(w->d_mh);
         cudaFreeHost(w->h_ms);
         w->d_msv = nullptr;
-        w->d_ms = w->h_ms = nullptr;
+        w->d_ms = w->h_ms = w->d_mh = nullptr;
         w->ms_cap = 0;
         BQ_TRY(bq_alloc((void **)&w->d_msv, sizeof(MSPtrs) * nrhs));
         BQ_TRY(bq_alloc((void **)&w->d_ms, sizeof(double) * M_NTOTAL * nrhs));
+        BQ_TRY(bq_alloc((void **)&w->d_mh, sizeof(double) * MH_TOTAL * nrhs));
         BQ_CUDA_TRY(cudaMallocHost((void **)&w->h_ms, sizeof(double) * M_NTOTAL * nrhs));
         w->ms_cap = nrhs;
     }
@@ -1127,7 +1155,8 @@ static int ms_block_run(bq_ctx *c0, int nrhs, int n, const double *shifts, int b
     memset(hms, 0, sizeof(double) * M_NTOTAL * nrhs);
     for (int r = 0; r < nrhs; r++) {
         BatchSlot *sl = &w->slot[r];
-        hs[r] = SysVec{sl->b, sl->x, sl->r, sl->t, sl->rs, sl->xs, sl->p, sl->Ap, sl->Vh};
+        // the residual lives in the ring: kb_init writes r^0 into slot 0
+        hs[r] = SysVec{sl->b, sl->x, sl->r, sl->t, hp[r].hist, sl->xs, sl->p, sl->Ap, sl->Vh};
         hscal[(size_t)r * S_NSCAL + S_SIGMA] = shifts[base];
         double *m = hms + (size_t)r * M_NTOTAL;
         for (int k = 0; k < n; k++) {
@@ -1149,10 +1178,13 @@ static int ms_block_run(bq_ctx *c0, int nrhs, int n, const double *shifts, int b
     for (int r = 0; r < nrhs; r++) active[r] = 1.0;
     BQ_CUDA_TRY(cudaMemcpyAsync(w->d_flags, active, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
     const BArgs ba{w->d_sys, w->d_scal, w->d_part, w->d_ticket, w->d_flags};
-    const MSBArgs mb{w->d_msv, w->d_ms};
+    // systems to flush at the end of a chunk: those active when it started
+    double *chunk_on = w->h_flags + nrhs;
+    const BArgs ba_chunk{w->d_sys, w->d_scal, w->d_part, w->d_ticket, w->d_flags + nrhs};
+    const MSBArgs mb{w->d_msv, w->d_ms, w->d_mh};
     kb_init<PS, PR><<<G, RED_THREADS, 0, s>>>(ba, 0);
     BQ_COUNT(c0);
-    kbm_init<PR><<<G, RED_THREADS, 0, s>>>(ba, mb, n, base);
+    kbm_init<PR><<<G, RED_THREADS, 0, s>>>(ba, mb, n);
     BQ_COUNT(c0);
     BQ_LAUNCH_CHECK();
     BQ_CUDA_TRY(cudaMemcpyAsync(w->h_scal, w->d_scal, sizeof(double) * S_NSCAL * nrhs, cudaMemcpyDeviceToHost, s));
@@ -1169,17 +1201,44 @@ static int ms_block_run(bq_ctx *c0, int nrhs, int n, const double *shifts, int b
     BQ_CUDA_TRY(cudaMemcpyAsync(w->d_flags, active, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
     const int recon_s = c0->links_recon[PS];
     const int check = sp->check_every > 0 ? sp->check_every : 1;
-    int it = 0;
+    const dim3 GF(red_grid(MsChunk<PR>::PER_SITE * Vh), nrhs);
+    int it = 0, t = 0, slot0 = 0;
+    // a new chunk: history rows cleared (a system skipped for an iteration leaves zeros), systems to flush
+    auto start_chunk = [&]() -> int {
+        BQ_CUDA_TRY(cudaMemsetAsync(w->d_mh, 0, sizeof(double) * MH_TOTAL * nrhs, s));
+        for (int r = 0; r < nrhs; r++) chunk_on[r] = active[r];
+        BQ_CUDA_TRY(cudaMemcpyAsync(w->d_flags + nrhs, chunk_on, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+        return BQ_OK;
+    };
+    // fold the chunk's T iterations into x_k and p_k; the last residual becomes slot 0 of the next chunk
+    auto flush = [&]() -> int {
+        if (t == 0) return BQ_OK;
+        kbm_coef<<<nrhs, MS_MAX, 0, s>>>(mb, n, t);
+        BQ_COUNT(c0);
+        kbm_flush<PR><<<GF, RED_THREADS, 0, s>>>(ba_chunk, mb, n, t, slot0);
+        BQ_COUNT(c0);
+        BQ_LAUNCH_CHECK();
+        slot0 = (slot0 + t) % MS_SLOTS;
+        t = 0;
+        return BQ_OK;
+    };
+    BQ_TRY(start_chunk());
     while (nactive > 0 && it < sp->max_iter) {
         BQ_TRY(mdagm_batch(c0, PS, recon_s, 0, &plan, nrhs, w->d_flags, (double)nactive / nrhs));
         kb_pap<PS><<<G, RED_THREADS, 0, s>>>(ba);
         BQ_COUNT(c0);
-        kbm_residual<PS, PR><<<G, RED_THREADS, 0, s>>>(ba, mb, n, base);
+        const int src = (slot0 + t) % MS_SLOTS, dst = (slot0 + t + 1) % MS_SLOTS;
+        kbm_residual<PS, PR><<<G, RED_THREADS, 0, s>>>(ba, mb, n, base, src, dst, t);
         BQ_COUNT(c0);
-        kbm_update<PS, PR><<<G, RED_THREADS, 0, s>>>(ba, mb, n, base);
+        kbm_pupdate<PS, PR><<<G, RED_THREADS, 0, s>>>(ba, mb, dst);
         BQ_COUNT(c0);
         BQ_LAUNCH_CHECK();
         it++;
+        t++;
+        if (t == MS_CHUNK) {
+            BQ_TRY(flush());
+            BQ_TRY(start_chunk());
+        }
         for (int r = 0; r < nrhs; r++)
             if (active[r] != 0.0) iters[r]++;
         if (it % check != 0) continue;
@@ -1202,6 +1261,7 @@ static int ms_block_run(bq_ctx *c0, int nrhs, int n, const double *shifts, int b
         if (changed)
             BQ_CUDA_TRY(cudaMemcpyAsync(w->d_flags, active, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
     }
+    BQ_TRY(flush());
     return BQ_OK;
 }
 
