@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--workload", default="32^3x64", choices=sorted(WORKLOADS))
     ap.add_argument("--inner", default="single", choices=["single", "half", "double"],
                     help="precision of the inner Krylov iteration (double = plain FP64 CG)")
-    ap.add_argument("--delta", type=float, default=None, help="reliable-update threshold (default 1e-3 FP32, 0.1 FP16)")
+    ap.add_argument("--delta", type=float, default=None, help="reliable-update threshold (default 1e-3 FP32, 3e-3 FP16)")
     ap.add_argument("--check-every", type=int, default=8, help="iterations between host residual checks")
     ap.add_argument("--fp64-arith", default="df64", choices=["native", "df64"],
                     help="arithmetic of the FP64-storage operator kernels")
@@ -285,7 +285,7 @@ def main():
     b = synth.gaussian_spinor(Vh, wl["seed"] + 1000 + rank)
     b_dev = torch.from_numpy(b).cuda()
     x_dev = torch.empty_like(b_dev)
-    delta = args.delta if args.delta is not None else {"single": 1e-3, "half": 1e-1, "double": 0.0}[args.inner]
+    delta = args.delta if args.delta is not None else {"single": 1e-3, "half": 3e-3, "double": 0.0}[args.inner]
     solve_kw = dict(tol=1e-10, precision=args.inner, delta=delta, check_every=args.check_every, max_iter=20000)
 
     bqcd.bq_set_batch_mapping(ctx, args.batch_mapping)

@@ -243,20 +243,31 @@ __device__ __forceinline__ void ms_flush_body(const MSPtrs &ptr, const double *c
                     ap[g][q] = G * pv[q];
                 }
             }
-            for (int i = 1; i <= T; i++) {
-                int sl = slot0 + i;
-                if (sl >= MS_SLOTS) sl -= MS_SLOTS;
-                TT rv[NR];
-                C::get(rv, static_cast<const V *>(ms_slot(ptr, sl))[e]);
+            // residuals four at a time: four independent loads in flight per thread
+            for (int i0 = 1; i0 <= T; i0 += 4) {
+                V raw[4];
 #pragma unroll
-                for (int g = 0; g < MS_GROUP; g++) {
-                    const int k = k0 + g;
-                    if (k >= n) continue;
-                    const TT W = (TT)sc[k * MH_COEF + 2 + (i - 1)], Cc = (TT)sc[k * MH_COEF + 2 + MS_CHUNK + (i - 1)];
+                for (int u = 0; u < 4; u++) {
+                    int sl = slot0 + i0 + u;
+                    if (sl >= MS_SLOTS) sl -= MS_SLOTS;
+                    if (i0 + u <= T) raw[u] = static_cast<const V *>(ms_slot(ptr, sl))[e];
+                }
 #pragma unroll
-                    for (int q = 0; q < NR; q++) {
-                        ax[g][q] = fma(W, rv[q], ax[g][q]);
-                        ap[g][q] = fma(Cc, rv[q], ap[g][q]);
+                for (int u = 0; u < 4; u++) {
+                    const int i = i0 + u;
+                    if (i > T) break;
+                    TT rv[NR];
+                    C::get(rv, raw[u]);
+#pragma unroll
+                    for (int g = 0; g < MS_GROUP; g++) {
+                        const int k = k0 + g;
+                        if (k >= n) continue;
+                        const TT W = (TT)sc[k * MH_COEF + 2 + (i - 1)], Cc = (TT)sc[k * MH_COEF + 2 + MS_CHUNK + (i - 1)];
+#pragma unroll
+                        for (int q = 0; q < NR; q++) {
+                            ax[g][q] = fma(W, rv[q], ax[g][q]);
+                            ap[g][q] = fma(Cc, rv[q], ap[g][q]);
+                        }
                     }
                 }
             }

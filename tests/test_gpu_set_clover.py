@@ -130,3 +130,28 @@ def test_set_clover_singular_block_falls_back(bq):
         bq._check(bq._lib_handle().bq_set_clover(lat.ctx, None, 7), "bq_set_clover")
     assert e.value.status == bq.BQ_ERR_ARG
     lat.close()
+
+
+def test_set_clover_in_batched_and_multishift_solves(bq):
+    """A caller's clover field drives the solvers too: two systems in one batched
+    mixed-precision CG (shared-memory tile mapping) and a two-shift multishift
+    solve, each to a true residual <= 1e-10 of the oracle operator on that field."""
+    dims = (6, 4, 6, 10)
+    lat, U, p = setup(bq, dims, "single", 12)
+    op = oracle.Operator(p, U)
+    rng = np.random.default_rng(5)
+    Ae, Ao = perturbed(op.Aee, rng), perturbed(op.Aoo, rng)
+    bq.bq_set_clover(lat.ctx, pack_clover(dims, Ae, Ao))
+    op.Aee, op.Aoo, op.Aoo_inv = Ae, Ao, oracle.clover_invert(Ao)
+    bq.bq_set_batch_mapping(lat.ctx, -3)
+    bs = [synth.gaussian_spinor(lat.Vh, 60 + i) for i in range(2)]
+    xs = [np.empty_like(b) for b in bs]
+    st = bq.bq_solve_cg_batch([lat.ctx] * 2, xs, bs, tol=1e-10, precision="single")
+    for b, x, s in zip(bs, xs, st):
+        assert s["converged"] and np.linalg.norm(op.mdagm(x) - b) / np.linalg.norm(b) <= 1e-10
+    shifts = [0.01, 0.2]
+    xm = [np.empty_like(bs[0]) for _ in shifts]
+    bq.bq_solve_multishift_cg(lat.ctx, xm, bs[0], shifts, tol=1e-10, precision="single")
+    for x, sh in zip(xm, shifts):
+        assert np.linalg.norm(op.mdagm(x, sh) - bs[0]) / np.linalg.norm(bs[0]) <= 1e-10
+    lat.close()
