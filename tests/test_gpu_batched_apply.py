@@ -82,3 +82,19 @@ def test_batched_mdagm_matches_single_apply_and_rejects_aliasing(bq):
         bq.bq_apply_mdagm_batch([lat.ctx, lat.ctx], [o1, src], [src, o1], "single")
     assert e.value.status == bq.BQ_ERR_ARG
     lat.close()
+
+
+@pytest.mark.parametrize("prec", ["single", "half"])
+def test_tile_unit_split_at_sixteen(bq, prec):
+    """17 right-hand sides of one lattice in the tile mapping: a unit of 16 and a
+    unit of 1, every output against the oracle."""
+    la, opa = lattice(bq, (4, 6, 4, 8), prec, 12, 0.0, 0.0, 4)
+    bq.bq_set_batch_mapping(la.ctx, -3)
+    psis = [synth.gaussian_spinor(la.Vh, 90 + i) for i in range(17)]
+    ins = [la.pack(p, prec) for p in psis]
+    outs = [la.spinor(prec) for _ in psis]
+    bq.bq_apply_mdagm_batch([la.ctx] * 17, outs, ins, prec)
+    assert bq.bq_get_batch_mapping(la.ctx) == -3
+    for p, o in zip(psis, outs):
+        assert rel(la.unpack(o, prec), opa.mdagm(p)) < TOL[prec]
+    la.close()

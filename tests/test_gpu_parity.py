@@ -596,7 +596,8 @@ def test_stout_links_parity(bq, rho, n_iter):
 
 @pytest.mark.parametrize("prec,recon,mu,charge", [("double", 18, 0.0, 0.0), ("double", 12, 0.1, 0.0),
                                                   ("single", 12, 0.0, 0.0), ("double", 18, 0.0, 2.0 / 3.0),
-                                                  ("half", 18, 0.1, -1.0 / 3.0)])
+                                                  ("half", 18, 0.1, -1.0 / 3.0), ("single", 8, 0.1, 0.0),
+                                                  ("half", 8, 0.0, 0.0)])
 def test_stout_operator_parity(bq, prec, recon, mu, charge):
     """Mhat with stout-smeared hopping links and the clover term from the thin links."""
     dims = (6, 4, 6, 10)
