@@ -56,7 +56,7 @@ WORKLOADS = {
 PREC_ID = {"double": 0, "single": 1, "half": 2}
 SPINOR_B = {0: 192, 1: 96, 2: 52}
 CLOVER_B = {0: 576, 1: 288, 2: 144}
-EPI_NAMES = ["dhop", "dhop_clovinv", "dhop_xpay"]
+EPI_NAMES = ["dhop", "dhop_clovinv", "dhop_xpay", "cg_mhat_norms", "cg_mhatdag_update"]
 
 
 def link_b(prec, recon):
@@ -153,7 +153,7 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ traffic from the committed ncu summary
 
-KERNEL_SOURCES = ("bq_device.cuh", "bq_stencil.cuh")  # the files that define k_dslash
+KERNEL_SOURCES = ("bq_device.cuh", "bq_stencil.cuh", "bq_cgfuse.cu")  # the files that define k_dslash, k_dslash_cg
 
 
 def kernel_source_hash():
@@ -323,14 +323,15 @@ def main():
     value = bytes_all / (ms_max * 1e-3) / 1e9
 
     # dominant hopping-term kernel over the timed region (CUDA events around each launch)
-    best = max(((p, e) for p in range(3) for e in range(3)), key=lambda pe: cnt["dslash_ms"][pe[0]][pe[1]])
+    best = max(((p, e) for p in range(3) for e in range(5)), key=lambda pe: cnt["dslash_ms"][pe[0]][pe[1]])
     bp, be = best
     n_l = cnt["dslash_launches"][bp][be]
-    per_launch_bytes = cnt["dslash_bytes"][bp][be] / max(n_l, 1)
+    # the CG-fused launches also move the vectors of the fused x / r update
+    per_launch_bytes = (cnt["dslash_bytes"][bp][be] + cnt["fused_bytes"][bp][be]) / max(n_l, 1)
     per_launch_ms = cnt["dslash_ms"][bp][be] / max(n_l, 1)
     peak, peak_kind = measured_peaks()
     achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
-    tag = f"k_dslash<{['double', 'single', 'half'][bp]},{EPI_NAMES[be]}>"
+    tag = f"{'k_dslash_cg' if be >= 3 else 'k_dslash'}<{['double', 'single', 'half'][bp]},{EPI_NAMES[be]}>"
     traffic = committed_traffic(tag, args.workload)
     all_ms = sum(sum(r) for r in cnt["dslash_ms"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -339,6 +340,17 @@ def main():
                 "algorithmic_bytes_per_launch": per_launch_bytes, "launches": n_l,
                 "avg_launch_us": per_launch_ms * 1e3, "share_of_dslash_time": cnt["dslash_ms"][bp][be] / all_ms,
                 "timing": "CUDA events around each launch, second timed pass of the same K steps"}
+    # every hopping-term bucket of the solve: launches, mean CUDA-event time, algorithmic GB/s
+    buckets = {}
+    for p in range(3):
+        for e in range(5):
+            n = cnt["dslash_launches"][p][e]
+            if n and cnt["dslash_ms"][p][e] > 0:
+                us = cnt["dslash_ms"][p][e] / n * 1e3
+                nbytes = (cnt["dslash_bytes"][p][e] + cnt["fused_bytes"][p][e]) / n
+                buckets[f"{'k_dslash_cg' if e >= 3 else 'k_dslash'}<{['double', 'single', 'half'][p]},{EPI_NAMES[e]}>"] = {
+                    "launches": n, "avg_us": us, "GB/s": nbytes / (us * 1e-6) / 1e9}
+    roofline["buckets"] = buckets
 
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,

@@ -97,17 +97,24 @@ typedef struct {
 
 /* Launch counters and optional device timing of the hopping-term kernels.
  * Buckets [precision][epilogue]: epilogue 0 = plain D_hop, 1 = D_hop followed
- * by A^{-1} (D_oe A_oo^{-1} step), 2 = A x - k D_hop in (D_eo step of Mhat).
+ * by A^{-1} (D_oe A_oo^{-1} step), 2 = A x - k D_hop in (D_eo step of Mhat),
+ * 3 and 4 = the two A x - k D_hop steps of a single-system CG iteration with
+ * the CG vector work fused in: 3 = t = Mhat p with |t|^2 and |p|^2 (so
+ * <p, Ap> = |t|^2 + shift |p|^2), 4 = Mhat^dag t with the x and r updates and
+ * |r|^2 (Ap itself is not stored).
  * Bytes and flops are ALGORITHMIC per launch: 8 links + 1 input + 1 output
  * spinor per output site, plus the clover blocks (and the x spinor) the fused
  * epilogue reads; 1320 flops per site for D_hop, +504 per clover apply,
- * +48 for the xpay. */
+ * +48 for the xpay. fused_bytes holds, for buckets 3 and 4, the further bytes
+ * of the fused vector work (bucket 4: p, x and r read, x and r written, minus
+ * the output spinor that is not stored). */
 typedef struct {
     long long launches;            /* every kernel the library launched since the last reset */
-    long long dslash_launches[3][3];
-    double dslash_bytes[3][3];
-    double dslash_flops[3][3];
-    double dslash_ms[3][3];        /* summed CUDA-event time per launch; 0 unless timing is on */
+    long long dslash_launches[3][5];
+    double dslash_bytes[3][5];
+    double dslash_flops[3][5];
+    double dslash_ms[3][5];        /* summed CUDA-event time per launch; 0 unless timing is on */
+    double fused_bytes[3][5];
 } bq_counters;
 
 /* ---- context ------------------------------------------------------------- */

@@ -49,9 +49,9 @@ class bq_solver_stats(ctypes.Structure):
 
 
 class bq_counters(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_longlong), ("dslash_launches", (ctypes.c_longlong * 3) * 3),
-                ("dslash_bytes", (ctypes.c_double * 3) * 3), ("dslash_flops", (ctypes.c_double * 3) * 3),
-                ("dslash_ms", (ctypes.c_double * 3) * 3)]
+    _fields_ = [("launches", ctypes.c_longlong), ("dslash_launches", (ctypes.c_longlong * 5) * 3),
+                ("dslash_bytes", (ctypes.c_double * 5) * 3), ("dslash_flops", (ctypes.c_double * 5) * 3),
+                ("dslash_ms", (ctypes.c_double * 5) * 3), ("fused_bytes", (ctypes.c_double * 5) * 3)]
 
     def as_dict(self):
         return {
@@ -60,6 +60,7 @@ class bq_counters(ctypes.Structure):
             "dslash_bytes": [list(row) for row in self.dslash_bytes],
             "dslash_flops": [list(row) for row in self.dslash_flops],
             "dslash_ms": [list(row) for row in self.dslash_ms],
+            "fused_bytes": [list(row) for row in self.fused_bytes],
         }
 
 

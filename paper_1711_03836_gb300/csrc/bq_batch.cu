@@ -358,6 +358,9 @@ struct BatchWork {
     MSPtrs *d_msv;
     double *d_ms, *h_ms, *d_mh;
     int ms_cap;
+    // per-block partial sums of the CG-fused hopping launches (one per 128 sites, two values)
+    double *d_fpart;
+    size_t fpart_n;
 };
 
 static void free_slot(BatchSlot *s) {
@@ -399,6 +402,7 @@ void bq_batch_free(bq_ctx *c) {
     cudaFree(w->d_ms);
     cudaFree(w->d_mh);
     cudaFreeHost(w->h_ms);
+    cudaFree(w->d_fpart);
     delete w;
     c->batch = nullptr;
 }
@@ -693,10 +697,11 @@ static int capture_iterations(bq_ctx *c0, int iters, Body &body, GraphRun *gr) {
     bq_counters &d = gr->per_launch;
     d.launches = c0->counters.launches - before.launches;
     for (int p = 0; p < 3; p++)
-        for (int e = 0; e < 3; e++) {
+        for (int e = 0; e < BQ_NEPI; e++) {
             d.dslash_launches[p][e] = c0->counters.dslash_launches[p][e] - before.dslash_launches[p][e];
             d.dslash_bytes[p][e] = c0->counters.dslash_bytes[p][e] - before.dslash_bytes[p][e];
             d.dslash_flops[p][e] = c0->counters.dslash_flops[p][e] - before.dslash_flops[p][e];
+            d.fused_bytes[p][e] = c0->counters.fused_bytes[p][e] - before.fused_bytes[p][e];
             d.dslash_ms[p][e] = 0;
         }
     c0->counters = before;
@@ -708,10 +713,11 @@ static int capture_iterations(bq_ctx *c0, int iters, Body &body, GraphRun *gr) {
 static void credit_replay(bq_ctx *c0, const GraphRun &gr, double frac) {
     c0->counters.launches += gr.per_launch.launches;
     for (int p = 0; p < 3; p++)
-        for (int e = 0; e < 3; e++) {
+        for (int e = 0; e < BQ_NEPI; e++) {
             c0->counters.dslash_launches[p][e] += gr.per_launch.dslash_launches[p][e];
             c0->counters.dslash_bytes[p][e] += gr.per_launch.dslash_bytes[p][e] * frac;
             c0->counters.dslash_flops[p][e] += gr.per_launch.dslash_flops[p][e] * frac;
+            c0->counters.fused_bytes[p][e] += gr.per_launch.fused_bytes[p][e] * frac;
         }
 }
 
@@ -779,6 +785,22 @@ static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double 
     };
     const BArgs ba_act{w->d_sys, w->d_scal, w->d_part, w->d_ticket, d_active};
     const BArgs ba_upd{w->d_sys, w->d_scal, w->d_part, w->d_ticket, d_update};
+    // one system with an FP32 inner iteration: the CG vector work rides on the two A x - k D
+    // launches (with FP16 storage the hopping kernels are bound by instruction issue, not by
+    // memory, and the fused vector traffic measured no faster than the separate kernels)
+    const bool fuse = nsys == 1 && PS == BQ_PREC_SINGLE;
+    CgFuse cgf{};
+    if (fuse) {
+        const size_t need = 8 * (size_t)((ctxs[0]->Vh + 127) / 128);  // two values per warp
+        if (w->fpart_n < need) {
+            cudaFree(w->d_fpart);
+            w->d_fpart = nullptr;
+            w->fpart_n = 0;
+            BQ_TRY(bq_alloc((void **)&w->d_fpart, sizeof(double) * need));
+            w->fpart_n = need;
+        }
+        cgf = CgFuse{w->slot[0].p, w->slot[0].xs, w->slot[0].rs, w->d_scal, w->d_fpart};
+    }
 
     for (int i = 0; i < nsys; i++) {
         active[i] = 1.0;
@@ -820,6 +842,15 @@ static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double 
     auto body = [&](double frac) -> int {
         kb_update_p<PS, PR><<<G, RED_THREADS, 0, c0->stream>>>(ba_act);
         BQ_COUNT(c0);
+        if (fuse) {
+            const DslashUnit *u[4];
+            for (int k = 0; k < 4; k++) u[k] = &w->tables[k][0].units[0];
+            BQ_TRY(bq_dslash_launch(c0, PS, u[0]->out[0], u[0]->in[0], 1, 0, EPI_CLOVINV, nullptr, u[0]->a.k));
+            BQ_TRY(bq_dslash_cg_launch(c0, PS, u[1]->out[0], u[1]->in[0], u[1]->xin[0], u[1]->a.k, CNT_CG_MHAT, cgf));
+            BQ_TRY(bq_dslash_launch(c0, PS, u[2]->out[0], u[2]->in[0], 1, 1, EPI_CLOVINV, nullptr, u[2]->a.k));
+            BQ_TRY(bq_dslash_cg_launch(c0, PS, nullptr, u[3]->in[0], u[3]->xin[0], u[3]->a.k, CNT_CG_MHATDAG, cgf));
+            return BQ_OK;
+        }
         BQ_TRY(mdagm_batch(c0, PS, recon_s, 0, &plan, nsys, d_active, frac));
         kb_pap<PS><<<G, RED_THREADS, 0, c0->stream>>>(ba_act);
         BQ_COUNT(c0);
@@ -838,9 +869,9 @@ static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double 
         for (int step = 0; step < 4; step++)
             sig = fnv(sig, w->tables[step].data(), sizeof(DslashBatchTable) * w->tables[step].size());
         sig = fnv(sig, hs.data(), sizeof(SysVec) * nsys);
-        const long long misc[10] = {nsys, PS, PR, check, c0->timing, (long long)(uintptr_t)w->d_sys,
+        const long long misc[11] = {nsys, PS, PR, check, c0->timing, (long long)(uintptr_t)w->d_sys,
                                     (long long)(uintptr_t)w->d_scal, (long long)(uintptr_t)w->d_flags,
-                                    (long long)(uintptr_t)w->d_part, G.x};
+                                    (long long)(uintptr_t)w->d_part, G.x, (long long)(uintptr_t)w->d_fpart};
         sig = fnv(sig, misc, sizeof misc);
         if (!(w->graph.exec && w->graph_sig == sig && w->graph_gen == c0->counter_gen)) {
             drop_graph(c0, &w->graph);

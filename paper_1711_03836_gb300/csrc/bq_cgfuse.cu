@@ -1,0 +1,182 @@
+// bq_cgfuse.cu -- one CG iteration on Mhat^dag Mhat + sigma (Section 3: cg)
+// with its vector work folded into the two hopping-term launches that end in
+// A x - k D (single system, FP32 inner iteration).
+//
+// Of the four launches of Ap = (Mhat^dag Mhat + sigma) p the second produces
+// t = Mhat p = A_ee p - k D_eo A_oo^{-1} D_oe p and the fourth Mhat^dag t. As
+// <p, Mhat^dag Mhat p> = |Mhat p|^2, the second launch sums |t|^2 and |p|^2
+// (p is its x spinor), a one-block kernel sets <p, Ap> = |t|^2 + sigma |p|^2 and
+// alpha = rr / <p, Ap>; the fourth forms q = Mhat^dag t + sigma p per site and,
+// instead of storing q, updates xs += alpha p and rs -= alpha q, sums |rs|^2
+// and a one-block kernel sets rr and beta. This removes the <p, Ap> kernel and the
+// x / r update kernel of the unfused iteration (their vector reads, the store
+// and reload of Ap) for two one-block launches.
+#include "bq_reduce.cuh"
+#include "bq_stencil.cuh"
+
+namespace {
+
+// The partial sums leave each warp as soon as its sites are done (lane 0 stores
+// them, [NV][warps of the grid]); a one-block kernel then sums them in warp
+// order. Nothing in the hopping kernel waits on another warp or block.
+template <int NV>
+__device__ __forceinline__ void warp_partials(double (&v)[NV], double *partials) {
+    const int nw = (int)(gridDim.x * blockDim.x) >> 5, w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        const double t = warp_sum(v[k]);
+        if ((threadIdx.x & 31) == 0) partials[k * nw + w] = t;
+    }
+}
+
+// the solver scalars from the warp partials of a fused launch (one block of CG_FIN_THREADS)
+constexpr int CG_FIN_THREADS = 1024;
+template <int MODE>
+__global__ void __launch_bounds__(CG_FIN_THREADS) k_cg_finish(const double *partials, int nw, double *scal) {
+    constexpr int NV = MODE == CNT_CG_MHAT ? 2 : 1;
+    double s[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) s[k] = 0.0;
+#pragma unroll 8
+    for (int i = threadIdx.x; i < nw; i += CG_FIN_THREADS)
+#pragma unroll
+        for (int k = 0; k < NV; k++) s[k] += partials[k * nw + i];
+    block_sum(s);
+    if (threadIdx.x == 0) {
+        if constexpr (MODE == CNT_CG_MHAT) {
+            const double pap = s[0] + scal[S_SIGMA] * s[1];
+            scal[S_PAP] = pap;
+            scal[S_ALPHA] = scal[S_RR] / pap;
+        } else {
+            const double rr = scal[S_RR];
+            scal[S_RRPREV] = rr;
+            scal[S_RR] = s[0];
+            scal[S_BETA] = s[0] / rr;
+        }
+    }
+}
+
+template <int PS, int RECON, int MODE>
+__global__ void __launch_bounds__(128, DslashMinBlocks<PS>::value) k_dslash_cg(const DslashArgs a, const CgFuse f) {
+    using T = typename Traits<PS>::real;
+    constexpr int NV = MODE == CNT_CG_MHAT ? 2 : 1;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = 0.0;
+    if (h < a.Vh) {
+        cplx<T> acc[12];
+        dslash_hops<PS, RECON, MODE == CNT_CG_MHATDAG>(a, a.in, h, acc);
+        if constexpr (MODE == CNT_CG_MHAT) {
+            cplx<T> xv[12], o[12];
+            xpay_site<PS>(a, a.xin, h, acc, xv, o);
+            SpinorIO<PS>::store(a.out, h, a.Vh, o);
+            v[0] = norm2_site(o);
+            v[1] = norm2_site(xv);
+        } else {
+            // q = A x - k acc + sigma p one chirality block (six components) at a time,
+            // each followed by the x / r update of its three float4 chunks
+            const float alpha = (float)f.scal[S_ALPHA];
+            const float sigma = (float)f.scal[S_SIGMA];
+            const float kk = (float)a.k;
+            const float4 *pxin = static_cast<const float4 *>(a.xin) + h;
+            const float4 *pp = static_cast<const float4 *>(f.p) + h;
+            float4 *px = static_cast<float4 *>(f.xs) + h, *pr = static_cast<float4 *>(f.rs) + h;
+            float nr = 0.f;
+#pragma unroll
+            for (int b = 0; b < 2; b++) {
+                cplx<T> o[6];
+                {
+                    cplx<T> xb[6];
+#pragma unroll
+                    for (int j = 0; j < 3; j++) {
+                        const float4 x4 = ldg(pxin + (size_t)(3 * b + j) * a.Vh);
+                        xb[2 * j] = {x4.x, x4.y};
+                        xb[2 * j + 1] = {x4.z, x4.w};
+                    }
+                    T d[6];
+                    cplx<T> od[15];
+                    CloverIO<PS>::load_block(d, od, a.clov, b, h, a.Vh);
+                    herm6_apply(d, od, xb, o);
+                }
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    const int k = 3 * b + j;
+                    const float4 p4 = ldg(pp + (size_t)k * a.Vh);
+                    float4 x4 = px[(size_t)k * a.Vh], r4 = pr[(size_t)k * a.Vh];
+                    const cplx<T> a0 = acc[2 * k], a1 = acc[2 * k + 1];
+                    const float q0r = fmaf(sigma, p4.x, fmaf(-kk, a0.re, o[2 * j].re));
+                    const float q0i = fmaf(sigma, p4.y, fmaf(-kk, a0.im, o[2 * j].im));
+                    const float q1r = fmaf(sigma, p4.z, fmaf(-kk, a1.re, o[2 * j + 1].re));
+                    const float q1i = fmaf(sigma, p4.w, fmaf(-kk, a1.im, o[2 * j + 1].im));
+                    x4.x = fmaf(alpha, p4.x, x4.x);
+                    x4.y = fmaf(alpha, p4.y, x4.y);
+                    x4.z = fmaf(alpha, p4.z, x4.z);
+                    x4.w = fmaf(alpha, p4.w, x4.w);
+                    r4.x = fmaf(-alpha, q0r, r4.x);
+                    r4.y = fmaf(-alpha, q0i, r4.y);
+                    r4.z = fmaf(-alpha, q1r, r4.z);
+                    r4.w = fmaf(-alpha, q1i, r4.w);
+                    px[(size_t)k * a.Vh] = x4;
+                    pr[(size_t)k * a.Vh] = r4;
+                    nr += r4.x * r4.x + r4.y * r4.y + r4.z * r4.z + r4.w * r4.w;
+                }
+            }
+            v[0] = (double)nr;
+        }
+    }
+    warp_partials(v, f.partials);
+}
+
+template <int PS, int RECON>
+void launch_cg(const DslashArgs &a, const CgFuse &f, int mode, unsigned grid, cudaStream_t s) {
+    if (mode == CNT_CG_MHAT) k_dslash_cg<PS, RECON, CNT_CG_MHAT><<<grid, 128, 0, s>>>(a, f);
+    else k_dslash_cg<PS, RECON, CNT_CG_MHATDAG><<<grid, 128, 0, s>>>(a, f);
+}
+
+void launch_finish(const CgFuse &f, int mode, unsigned grid, cudaStream_t s) {
+    const int nw = (int)grid * 4;
+    if (mode == CNT_CG_MHAT) k_cg_finish<CNT_CG_MHAT><<<1, CG_FIN_THREADS, 0, s>>>(f.partials, nw, f.scal);
+    else k_cg_finish<CNT_CG_MHATDAG><<<1, CG_FIN_THREADS, 0, s>>>(f.partials, nw, f.scal);
+}
+
+template <int PS>
+void launch_cg_r(int recon, const DslashArgs &a, const CgFuse &f, int mode, unsigned grid, cudaStream_t s) {
+    if (recon == 12) launch_cg<PS, 12>(a, f, mode, grid, s);
+    else if (recon == 8) launch_cg<PS, 8>(a, f, mode, grid, s);
+    else launch_cg<PS, 18>(a, f, mode, grid, s);
+}
+
+}  // namespace
+
+int bq_dslash_cg_launch(bq_ctx *c, int ps, void *out, const void *in, const void *xin, double k, int mode,
+                        const CgFuse &f) {
+    if (ps != BQ_PREC_SINGLE || !(mode == CNT_CG_MHAT || mode == CNT_CG_MHATDAG)) {
+        bq_set_error("fused CG step: FP32 inner precision only");
+        return BQ_ERR_ARG;
+    }
+    const int dagger = mode == CNT_CG_MHATDAG;
+    DslashArgs a;
+    BQ_TRY(bq_dslash_unit_fill(c, ps, 0, dagger, EPI_XPAY, k, &a));
+    a.out = out;
+    a.in = in;
+    a.xin = xin;
+    const int recon = c->links_recon[ps];
+    const unsigned grid = (unsigned)((c->Vh + 127) / 128);
+    int slot;
+    BQ_TRY(bq_time_begin(c, ps, mode, &slot));
+    launch_cg_r<BQ_PREC_SINGLE>(recon, a, f, mode, grid, c->stream);
+    BQ_LAUNCH_CHECK();
+    BQ_TRY(bq_time_end(c, slot));
+    BQ_COUNT(c);
+    launch_finish(f, mode, grid, c->stream);
+    BQ_LAUNCH_CHECK();
+    BQ_COUNT(c);
+    const double sr = spinor_bytes_per_site(BQ_PREC_SINGLE);
+    c->counters.dslash_launches[ps][mode]++;
+    c->counters.dslash_bytes[ps][mode] += dslash_site_bytes(ps, recon, EPI_XPAY) * c->Vh;
+    c->counters.dslash_flops[ps][mode] += dslash_site_flops(EPI_XPAY) * c->Vh;
+    // mode 4: p read, xs and rs read and written; the output spinor (as many bytes as p) not written
+    if (mode == CNT_CG_MHATDAG) c->counters.fused_bytes[ps][mode] += 4 * sr * c->Vh;
+    return BQ_OK;
+}

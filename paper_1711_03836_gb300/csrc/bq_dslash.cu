@@ -95,45 +95,16 @@ static int field_store(const bq_ctx *c, int prec) {
 int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_parity, int dagger, int epi,
                      const void *xin, double k, int fmt) {
     const int fs = field_store(c, prec);
-    BQ_TRY(bq_prepare_links(c, fs));
-    if (epi != EPI_PLAIN) BQ_TRY(bq_prepare_clover(c, fs));
     DslashArgs a;
+    BQ_TRY(bq_dslash_unit_fill(c, prec, out_parity, dagger, epi, k, &a));
     a.out = out;
     a.in = in;
-    a.links = links_ptr(c, fs);
-    a.lblk = links_block_bytes(c, fs);
-    a.clov = (epi == EPI_CLOVINV) ? clover_ptr(c, fs, out_parity, 1)
-           : (epi == EPI_XPAY)    ? clover_ptr(c, fs, out_parity, 0)
-                                  : nullptr;
     a.xin = xin;
-    a.L0 = c->L[0];
-    a.L1 = c->L[1];
-    a.L2 = c->L[2];
-    a.L3 = c->L[3];
-    a.Lxh = c->L[0] / 2;
-    a.Vh = c->Vh;
-    a.parity = out_parity;
-    double ef = exp(c->params.mu), eb = exp(-c->params.mu);
-    a.cf = dagger ? eb : ef;
-    a.cb = dagger ? ef : eb;
-    a.bc = c->params.t_bc;
-    a.k = k;
     a.fmt = (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) ? fmt : 0;
     unsigned grid = (unsigned)((c->Vh + 127) / 128);
     int recon = c->links_recon[fs];
     int slot = -1;
-    if (c->timing) {
-        if (c->ev_used == BQ_EV_PAIRS) {
-            if (c->capturing) {
-                bq_set_error("too many timed launches inside one captured graph");
-                return BQ_ERR_STATE;
-            }
-            BQ_TRY(bq_fold_events(c));
-        }
-        slot = c->ev_used++;
-        c->ev_bucket[slot] = prec * 3 + epi;
-        BQ_CUDA_TRY(bq_event_record(c, c->ev[2 * slot]));
-    }
+    BQ_TRY(bq_time_begin(c, prec, epi, &slot));
     if (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) {  // a lane pair per site (bq_df64.cu)
         BQ_TRY(bq_df64p_launch(recon, a, dagger, epi, (unsigned)((2LL * c->Vh + 127) / 128), c->stream));
     } else if (prec == BQ_PREC_DOUBLE) {
@@ -149,7 +120,7 @@ int bq_dslash_launch(bq_ctx *c, int prec, void *out, const void *in, int out_par
         else launch_dslash_pr<BQ_PREC_HALF, 18>(a, dagger, epi, grid, c->stream);
     }
     BQ_LAUNCH_CHECK();
-    if (slot >= 0) BQ_CUDA_TRY(bq_event_record(c, c->ev[2 * slot + 1]));
+    BQ_TRY(bq_time_end(c, slot));
     const double site_bytes = dslash_site_bytes(prec, recon, epi), site_flops = dslash_site_flops(epi);
     BQ_COUNT(c);
     c->counters.dslash_launches[prec][epi]++;
@@ -164,13 +135,35 @@ cudaError_t bq_event_record(bq_ctx *c, cudaEvent_t ev) {
     return c->capturing ? cudaEventRecordWithFlags(ev, c->stream, cudaEventRecordExternal) : cudaEventRecord(ev, c->stream);
 }
 
+// open a timed slot for a hopping-term launch in bucket [prec][epi] (no-op unless timing is on)
+int bq_time_begin(bq_ctx *c, int prec, int epi, int *slot) {
+    *slot = -1;
+    if (!c->timing) return BQ_OK;
+    if (c->ev_used == BQ_EV_PAIRS) {
+        if (c->capturing) {
+            bq_set_error("too many timed launches inside one captured graph");
+            return BQ_ERR_STATE;
+        }
+        BQ_TRY(bq_fold_events(c));
+    }
+    *slot = c->ev_used++;
+    c->ev_bucket[*slot] = prec * BQ_NEPI + epi;
+    BQ_CUDA_TRY(bq_event_record(c, c->ev[2 * *slot]));
+    return BQ_OK;
+}
+
+int bq_time_end(bq_ctx *c, int slot) {
+    if (slot >= 0) BQ_CUDA_TRY(bq_event_record(c, c->ev[2 * slot + 1]));
+    return BQ_OK;
+}
+
 // add the elapsed times of slots [a, b) to the counters (stream synchronised by the caller)
 int bq_fold_slots(bq_ctx *c, int a, int b) {
     for (int i = a; i < b; i++) {
         float ms = 0.f;
         BQ_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]));
         int k = c->ev_bucket[i];
-        c->counters.dslash_ms[k / 3][k % 3] += ms;
+        c->counters.dslash_ms[k / BQ_NEPI][k % BQ_NEPI] += ms;
     }
     return BQ_OK;
 }
@@ -262,18 +255,7 @@ int bq_dslash_batch_launch(bq_ctx *c, int prec, int recon, const DslashBatchTabl
                            int dagger, int epi, double site_bytes_total, double site_flops_total) {
     const int nblocks = tab->block0[tab->nunits];
     int slot = -1;
-    if (c->timing) {
-        if (c->ev_used == BQ_EV_PAIRS) {
-            if (c->capturing) {
-                bq_set_error("too many timed launches inside one captured graph");
-                return BQ_ERR_STATE;
-            }
-            BQ_TRY(bq_fold_events(c));
-        }
-        slot = c->ev_used++;
-        c->ev_bucket[slot] = prec * 3 + epi;
-        BQ_CUDA_TRY(bq_event_record(c, c->ev[2 * slot]));
-    }
+    BQ_TRY(bq_time_begin(c, prec, epi, &slot));
     cudaStream_t s = c->stream;
     if (prec == BQ_PREC_DOUBLE && c->fp64_arith == BQ_FP64_DF64) {  // lane pairs per site (bq_df64.cu)
         BQ_TRY(bq_df64p_batch_launch(recon, *tab, mask, nblocks, dagger, epi, s));
@@ -290,7 +272,7 @@ int bq_dslash_batch_launch(bq_ctx *c, int prec, int recon, const DslashBatchTabl
         else launch_batch_pr<BQ_PREC_HALF, 18>(*tab, mask, nblocks, dagger, epi, s);
     }
     BQ_LAUNCH_CHECK();
-    if (slot >= 0) BQ_CUDA_TRY(bq_event_record(c, c->ev[2 * slot + 1]));
+    BQ_TRY(bq_time_end(c, slot));
     BQ_COUNT(c);
     c->counters.dslash_launches[prec][epi]++;
     c->counters.dslash_bytes[prec][epi] += site_bytes_total;

@@ -98,6 +98,11 @@ enum { BQ_EV_PAIRS = 4096 };
 int bq_fold_events(bq_ctx *c);
 int bq_fold_slots(bq_ctx *c, int a, int b);
 cudaError_t bq_event_record(bq_ctx *c, cudaEvent_t ev);
+// counter buckets per precision: the kernel epilogues EPI_PLAIN, EPI_CLOVINV, EPI_XPAY
+// and the two CG-fused A x - k D steps (bq_cgfuse.cu)
+enum { CNT_CG_MHAT = 3, CNT_CG_MHATDAG = 4, BQ_NEPI = 5 };
+int bq_time_begin(bq_ctx *c, int prec, int epi, int *slot);
+int bq_time_end(bq_ctx *c, int slot);
 
 // field preparation (bq_fields.cu)
 int bq_prepare_links(bq_ctx *c, int prec);
@@ -166,6 +171,22 @@ void bq_tile_launch(int prec, int recon, const DslashBatchTable &tab, const doub
                     int epi, cudaStream_t s);
 double dslash_site_bytes(int prec, int recon, int epi);
 double dslash_site_flops(int epi);
+
+// The CG vector work fused into the two A x - k D launches of one CG iteration
+// on Mhat^dag Mhat + sigma (single system, FP32 inner iteration; bq_cgfuse.cu).
+// scal: the system's solver scalars (S_* slots of bq_reduce.cuh); partials: 2 doubles
+// per warp of the launch (8 * ceil(V/2 / 128))
+struct CgFuse {
+    const void *p;  // search direction, FP32
+    void *xs, *rs;  // iterated solution and residual, FP32
+    double *scal;
+    double *partials;
+};
+// mode CNT_CG_MHAT: out = t = A_ee p - k D_eo in (xin = p), then <p, Ap> = |t|^2 + sigma |p|^2
+//   and alpha = rr / <p, Ap>; mode CNT_CG_MHATDAG: q = A_ee^dag xin - k D_eo^dag in + sigma p
+//   (not stored), xs += alpha p, rs -= alpha q, rr_new = |rs|^2, beta = rr_new / rr
+int bq_dslash_cg_launch(bq_ctx *c, int ps, void *out, const void *in, const void *xin, double k, int mode,
+                        const CgFuse &f);
 
 // batched solver (bq_batch.cu)
 int bq_batch_prepare(int nsys, bq_ctx *const *ctxs, int ps);  // fields of every system at FP64 and ps

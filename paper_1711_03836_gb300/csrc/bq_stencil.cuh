@@ -137,9 +137,10 @@ __device__ __forceinline__ void hop(cplx<typename Traits<PREC>::real> acc[12], c
         accumulate<MU, S>(acc, u0, u1);
 }
 
-template <int PREC, int RECON, bool DAG, int EPI>
-__device__ __forceinline__ void dslash_site(const DslashArgs &a, const void *in, void *out, const void *xin,
-                                            const int h) {
+// acc = D_hop in at output site h (the eight hops, Eq. 1 / Eq. 5)
+template <int PREC, int RECON, bool DAG>
+__device__ __forceinline__ void dslash_hops(const DslashArgs &a, const void *in, const int h,
+                                            cplx<typename Traits<PREC>::real> acc[12]) {
     using T = typename Traits<PREC>::real;
     const int Lxh = a.Lxh, Vh = a.Vh;
     const int xh = h % Lxh;
@@ -155,7 +156,6 @@ __device__ __forceinline__ void dslash_site(const DslashArgs &a, const void *in,
     constexpr int SB = -SF;
     const int sy = Lxh, sz = Lxh * a.L1, st = sz * a.L2;
 
-    cplx<T> acc[12];
 #pragma unroll
     for (int c = 0; c < 12; c++) acc[c] = {T(0), T(0)};
 
@@ -196,7 +196,32 @@ __device__ __forceinline__ void dslash_site(const DslashArgs &a, const void *in,
         const T coef = (T)(wrap ? a.cb * a.bc : a.cb);
         hop<PREC, RECON, 3, SB, true, true>(acc, in, hn, Li + 3 * a.lblk, hn, Vh, coef);
     }
+}
 
+// o = A x - k acc at site h (the A_ee x - k D_eo step), x read from xin
+template <int PREC>
+__device__ __forceinline__ void xpay_site(const DslashArgs &a, const void *xin, const int h,
+                                          const cplx<typename Traits<PREC>::real> acc[12],
+                                          cplx<typename Traits<PREC>::real> xv[12],
+                                          cplx<typename Traits<PREC>::real> o[12]) {
+    using T = typename Traits<PREC>::real;
+    SpinorIO<PREC>::load(xv, xin, h, a.Vh);
+    clover_apply_site<PREC>(o, xv, a.clov, h, a.Vh);
+    const T k = (T)a.k;
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+        o[c].re = fma(-k, acc[c].re, o[c].re);
+        o[c].im = fma(-k, acc[c].im, o[c].im);
+    }
+}
+
+template <int PREC, int RECON, bool DAG, int EPI>
+__device__ __forceinline__ void dslash_site(const DslashArgs &a, const void *in, void *out, const void *xin,
+                                            const int h) {
+    using T = typename Traits<PREC>::real;
+    const int Vh = a.Vh;
+    cplx<T> acc[12];
+    dslash_hops<PREC, RECON, DAG>(a, in, h, acc);
     if (EPI == EPI_PLAIN) {
         SpinorIO<PREC>::store(out, h, Vh, acc);
     } else if (EPI == EPI_CLOVINV) {
@@ -205,14 +230,7 @@ __device__ __forceinline__ void dslash_site(const DslashArgs &a, const void *in,
         SpinorIO<PREC>::store(out, h, Vh, o);
     } else {
         cplx<T> xv[12], o[12];
-        SpinorIO<PREC>::load(xv, xin, h, Vh);
-        clover_apply_site<PREC>(o, xv, a.clov, h, Vh);
-        const T k = (T)a.k;
-#pragma unroll
-        for (int c = 0; c < 12; c++) {
-            o[c].re = fma(-k, acc[c].re, o[c].re);
-            o[c].im = fma(-k, acc[c].im, o[c].im);
-        }
+        xpay_site<PREC>(a, xin, h, acc, xv, o);
         SpinorIO<PREC>::store(out, h, Vh, o);
     }
 }
