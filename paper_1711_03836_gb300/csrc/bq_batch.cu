@@ -31,13 +31,6 @@
 #include "bq_ms.cuh"
 #include "bq_nvtx.cuh"
 
-struct SysVec {
-    void *b, *x, *r, *t;  // FP64 native
-    void *rs, *xs;        // precision pr
-    void *p, *Ap;         // precision ps
-    int Vh;
-};
-
 struct BArgs {
     const SysVec *sys;
     double *scal;          // [nsys][S_NSCAL]
@@ -578,27 +571,32 @@ static int build_units(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, int ps, int ma
     return BQ_OK;
 }
 
+// one of the eight steps (0-3 sloppy, 4-7 FP64) of the batched Mhat^dag Mhat
+static int batch_step(bq_ctx *c0, int prec, int recon, int step, const UnitPlan *plan, int nsys,
+                      const double *mask_dev, double active_fraction) {
+    BatchWork *w = c0->batch;
+    const int k = step & 3;
+    const int parity = (k == 0 || k == 2) ? 1 : 0;
+    const int dagger = k >= 2;
+    const int epi = parity == 1 ? EPI_CLOVINV : EPI_XPAY;
+    const std::vector<DslashBatchTable> &tabs = w->tables[step];
+    if (nsys == 1) {
+        // a single system: the plain kernel, no unit indirection (it is
+        // active whenever this runs: the loop stops at convergence)
+        const DslashUnit &u = tabs[0].units[0];
+        return bq_dslash_launch(c0, prec, u.out[0], u.in[0], parity, dagger, epi, u.xin[0], u.a.k, u.a.fmt);
+    }
+    for (size_t q = 0; q < tabs.size(); q++)
+        BQ_TRY(bq_dslash_batch_launch(c0, prec, recon, &tabs[q], mask_dev, dagger, epi,
+                                      plan->bytes_all[step] * active_fraction / tabs.size(),
+                                      plan->flops_all[step] * active_fraction / tabs.size()));
+    return BQ_OK;
+}
+
 static int mdagm_batch(bq_ctx *c0, int prec, int recon, int first_step, const UnitPlan *plan, int nsys,
                        const double *mask_dev, double active_fraction) {
-    BatchWork *w = c0->batch;
-    for (int k = 0; k < 4; k++) {
-        const int step = first_step + k;
-        const int parity = (k == 0 || k == 2) ? 1 : 0;
-        const int dagger = k >= 2;
-        const int epi = parity == 1 ? EPI_CLOVINV : EPI_XPAY;
-        const std::vector<DslashBatchTable> &tabs = w->tables[step];
-        if (nsys == 1) {
-            // a single system: the plain kernel, no unit indirection (it is
-            // active whenever this runs: the loop stops at convergence)
-            const DslashUnit &u = tabs[0].units[0];
-            BQ_TRY(bq_dslash_launch(c0, prec, u.out[0], u.in[0], parity, dagger, epi, u.xin[0], u.a.k, u.a.fmt));
-            continue;
-        }
-        for (size_t q = 0; q < tabs.size(); q++)
-            BQ_TRY(bq_dslash_batch_launch(c0, prec, recon, &tabs[q], mask_dev, dagger, epi,
-                                          plan->bytes_all[step] * active_fraction / tabs.size(),
-                                          plan->flops_all[step] * active_fraction / tabs.size()));
-    }
+    for (int k = 0; k < 4; k++)
+        BQ_TRY(batch_step(c0, prec, recon, first_step + k, plan, nsys, mask_dev, active_fraction));
     return BQ_OK;
 }
 
@@ -801,6 +799,23 @@ static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double 
         }
         cgf = CgFuse{w->slot[0].p, w->slot[0].xs, w->slot[0].rs, w->d_scal, w->d_fpart};
     }
+    // several FP32 systems in the shared-memory tile mapping: the same fusion inside the tile kernel
+    const bool fuse_tiles = nsys > 1 && PS == BQ_PREC_SINGLE && mapping <= -3;
+    TileCg tcg{};
+    double sum_vh = 0.0;
+    if (fuse_tiles) {
+        const int pstride = (maxVh + 31) / 32;
+        const size_t need = (size_t)nsys * 2 * pstride;
+        if (w->fpart_n < need) {
+            cudaFree(w->d_fpart);
+            w->d_fpart = nullptr;
+            w->fpart_n = 0;
+            BQ_TRY(bq_alloc((void **)&w->d_fpart, sizeof(double) * need));
+            w->fpart_n = need;
+        }
+        tcg = TileCg{w->d_sys, w->d_scal, w->d_fpart, pstride};
+        for (int i = 0; i < nsys; i++) sum_vh += ctxs[i]->Vh;
+    }
 
     for (int i = 0; i < nsys; i++) {
         active[i] = 1.0;
@@ -849,6 +864,24 @@ static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double 
             BQ_TRY(bq_dslash_cg_launch(c0, PS, u[1]->out[0], u[1]->in[0], u[1]->xin[0], u[1]->a.k, CNT_CG_MHAT, cgf));
             BQ_TRY(bq_dslash_launch(c0, PS, u[2]->out[0], u[2]->in[0], 1, 1, EPI_CLOVINV, nullptr, u[2]->a.k));
             BQ_TRY(bq_dslash_cg_launch(c0, PS, nullptr, u[3]->in[0], u[3]->xin[0], u[3]->a.k, CNT_CG_MHATDAG, cgf));
+            return BQ_OK;
+        }
+        if (fuse_tiles) {
+            for (int k = 0; k < 4; k++) {
+                if (k == 0 || k == 2) {
+                    BQ_TRY(batch_step(c0, PS, recon_s, k, &plan, nsys, d_active, frac));
+                    continue;
+                }
+                const int mode = k == 1 ? CNT_CG_MHAT : CNT_CG_MHATDAG;
+                const std::vector<DslashBatchTable> &tabs = w->tables[k];
+                const double nt = (double)tabs.size();
+                // step 3 moves p, x and r (x and r twice) in place of its output: 4 FP32 spinors per site
+                const double fused = mode == CNT_CG_MHATDAG ? 4.0 * spinor_bytes_per_site(PS) * sum_vh * frac / nt : 0.0;
+                for (size_t q = 0; q < tabs.size(); q++)
+                    BQ_TRY(bq_tile_cg_launch(c0, recon_s, &tabs[q], d_active, mode, tcg,
+                                             plan.bytes_all[k] * frac / nt, plan.flops_all[k] * frac / nt, fused));
+                BQ_TRY(bq_cg_finish_batch(c0, mode, tcg, d_active, nsys));
+            }
             return BQ_OK;
         }
         BQ_TRY(mdagm_batch(c0, PS, recon_s, 0, &plan, nsys, d_active, frac));

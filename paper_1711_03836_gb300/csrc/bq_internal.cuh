@@ -172,6 +172,28 @@ void bq_tile_launch(int prec, int recon, const DslashBatchTable &tab, const doub
 double dslash_site_bytes(int prec, int recon, int epi);
 double dslash_site_flops(int epi);
 
+// the vectors of one system of the batched solvers (device table, bq_batch.cu)
+struct SysVec {
+    void *b, *x, *r, *t;  // FP64 native
+    void *rs, *xs;        // precision pr
+    void *p, *Ap;         // precision ps
+    int Vh;
+};
+
+// The same fusion for a batch of FP32 systems in the shared-memory tile mapping
+// (bq_tile.cu): per system and tile of 32 sites one partial per value, [nsys][2][pstride]
+// with pstride >= the tiles of the largest lattice; scal [nsys][S_NSCAL]
+struct TileCg {
+    const SysVec *sys;
+    double *scal;
+    double *partials;
+    int pstride;
+};
+int bq_tile_cg_launch(bq_ctx *c, int recon, const DslashBatchTable *tab, const double *mask, int mode,
+                      const TileCg &cg, double site_bytes_total, double site_flops_total, double fused_bytes_total);
+// the solver scalars of every unmasked system from the tile partials of a fused launch
+int bq_cg_finish_batch(bq_ctx *c, int mode, const TileCg &cg, const double *mask, int nsys);
+
 // The CG vector work fused into the two A x - k D launches of one CG iteration
 // on Mhat^dag Mhat + sigma (single system, FP32 inner iteration; bq_cgfuse.cu).
 // scal: the system's solver scalars (S_* slots of bq_reduce.cuh); partials: 2 doubles

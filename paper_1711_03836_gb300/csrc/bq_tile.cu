@@ -2,7 +2,7 @@
 // the clover term of a tile of sites staged in shared memory once for all
 // right-hand sides of a unit (the block solvers of Section 3 apply one operator
 // to many right-hand sides), FP32 and FP16 storage.
-#include "bq_internal.cuh"
+#include "bq_reduce.cuh"
 #include "bq_stencil.cuh"
 
 // --------------------------------------------------------------------------
@@ -166,10 +166,21 @@ __device__ __forceinline__ void stage_clover(float4 *sC, const void *clov, int h
     }
 }
 
-template <int PREC, int RECON, bool DAG, int EPI>
+// sum over a warp in FP32 (the per-site terms are FP32 already; an FP64 shuffle-add
+// chain per right-hand side and tile runs on GB300's narrow FP64 pipe)
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// CGM: 0, or the CG-fused A x - k D steps of an FP32 batch (CNT_CG_MHAT: store t and
+// return |t|^2, |x|^2 in v; CNT_CG_MHATDAG: q = A x - k D in + sigma p of system sys,
+// xs += alpha p, rs -= alpha q, return |rs|^2 in v[0]; nothing stored to out)
+template <int PREC, int RECON, bool DAG, int EPI, int CGM>
 __device__ __forceinline__ void dslash_site_tile(const DslashArgs &a, const SiteNb &nb, const void *in, void *out,
                                                  const void *xin, int h, const float4 *sL, const float4 *sC,
-                                                 int lane) {
+                                                 int lane, const TileCg &cg, int sys, float (&v)[2]) {
     const int Vh = a.Vh;
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
@@ -200,6 +211,97 @@ __device__ __forceinline__ void dslash_site_tile(const DslashArgs &a, const Site
         SpinorIO<PREC>::store(out, h, Vh, acc);
         return;
     }
+    if constexpr (CGM == CNT_CG_MHATDAG) {
+        // one chirality block (six components) at a time, each followed by the update of
+        // its three float4 chunks of x and r
+        static_assert(PREC == BQ_PREC_SINGLE && EPI == EPI_XPAY, "fused CG update: FP32 xpay step");
+        const SysVec &sv = cg.sys[sys];
+        const double *sc = cg.scal + (size_t)sys * S_NSCAL;
+        const float alpha = (float)sc[S_ALPHA], sigma = (float)sc[S_SIGMA], kk = (float)a.k;
+        const float4 *pxin = static_cast<const float4 *>(xin) + h, *pp = static_cast<const float4 *>(sv.p) + h;
+        float4 *px = static_cast<float4 *>(sv.xs) + h, *pr = static_cast<float4 *>(sv.rs) + h;
+        float nr = 0.f;
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            cplx<float> ob[6];
+            {
+                cplx<float> xb[6];
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    const float4 x4 = ldg(pxin + (size_t)(3 * b + j) * Vh);
+                    xb[2 * j] = {x4.x, x4.y};
+                    xb[2 * j + 1] = {x4.z, x4.w};
+                }
+                float d[6];
+                cplx<float> od[15];
+                tile_clover_block(d, od, sC, b, lane);
+                herm6_apply(d, od, xb, ob);
+            }
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                const int k = 3 * b + j;
+                const float4 p4 = ldg(pp + (size_t)k * Vh);
+                float4 x4 = px[(size_t)k * Vh], r4 = pr[(size_t)k * Vh];
+                const float q0r = fmaf(sigma, p4.x, fmaf(-kk, acc[2 * k].re, ob[2 * j].re));
+                const float q0i = fmaf(sigma, p4.y, fmaf(-kk, acc[2 * k].im, ob[2 * j].im));
+                const float q1r = fmaf(sigma, p4.z, fmaf(-kk, acc[2 * k + 1].re, ob[2 * j + 1].re));
+                const float q1i = fmaf(sigma, p4.w, fmaf(-kk, acc[2 * k + 1].im, ob[2 * j + 1].im));
+                x4.x = fmaf(alpha, p4.x, x4.x);
+                x4.y = fmaf(alpha, p4.y, x4.y);
+                x4.z = fmaf(alpha, p4.z, x4.z);
+                x4.w = fmaf(alpha, p4.w, x4.w);
+                r4.x = fmaf(-alpha, q0r, r4.x);
+                r4.y = fmaf(-alpha, q0i, r4.y);
+                r4.z = fmaf(-alpha, q1r, r4.z);
+                r4.w = fmaf(-alpha, q1i, r4.w);
+                px[(size_t)k * Vh] = x4;
+                pr[(size_t)k * Vh] = r4;
+                nr += r4.x * r4.x + r4.y * r4.y + r4.z * r4.z + r4.w * r4.w;
+            }
+        }
+        v[0] = nr;
+        return;
+    }
+    if constexpr (CGM == CNT_CG_MHAT) {
+        // t = A x - k D in one chirality block at a time, stored as it is formed, with |t|^2 and |x|^2
+        static_assert(PREC == BQ_PREC_SINGLE && EPI == EPI_XPAY, "fused CG norms: FP32 xpay step");
+        const float kk = (float)a.k;
+        const float4 *pxin = static_cast<const float4 *>(xin) + h;
+        float4 *po = static_cast<float4 *>(out) + h;
+        float n0 = 0.f, n1 = 0.f;
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            cplx<float> ob[6];
+            {
+                cplx<float> xb[6];
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    const float4 x4 = ldg(pxin + (size_t)(3 * b + j) * Vh);
+                    xb[2 * j] = {x4.x, x4.y};
+                    xb[2 * j + 1] = {x4.z, x4.w};
+                    n1 += x4.x * x4.x + x4.y * x4.y + x4.z * x4.z + x4.w * x4.w;
+                }
+                float d[6];
+                cplx<float> od[15];
+                tile_clover_block(d, od, sC, b, lane);
+                herm6_apply(d, od, xb, ob);
+            }
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                const int k = 3 * b + j;
+                float4 t4;
+                t4.x = fmaf(-kk, acc[2 * k].re, ob[2 * j].re);
+                t4.y = fmaf(-kk, acc[2 * k].im, ob[2 * j].im);
+                t4.z = fmaf(-kk, acc[2 * k + 1].re, ob[2 * j + 1].re);
+                t4.w = fmaf(-kk, acc[2 * k + 1].im, ob[2 * j + 1].im);
+                po[(size_t)k * Vh] = t4;
+                n0 += t4.x * t4.x + t4.y * t4.y + t4.z * t4.z + t4.w * t4.w;
+            }
+        }
+        v[0] = n0;
+        v[1] = n1;
+        return;
+    }
     cplx<float> src[12], o[12];
     if (EPI == EPI_CLOVINV) {
 #pragma unroll
@@ -227,9 +329,9 @@ __device__ __forceinline__ void dslash_site_tile(const DslashArgs &a, const Site
 
 // MB: resident 128-thread blocks per SM the kernel is compiled for (registers
 // per thread 128, 96 or 80); the autotuner picks among the variants
-template <int PREC, int RECON, bool DAG, int EPI, int MB>
+template <int PREC, int RECON, bool DAG, int EPI, int MB, int CGM = 0>
 __global__ void __launch_bounds__(128, MB) k_dslash_tile(const __grid_constant__ DslashBatchTable tab,
-                                                         const double *mask) {
+                                                         const double *mask, const TileCg cg) {
     __shared__ float4 sL[8 * 5 * TILE_SITES];
     __shared__ float4 sC[EPI != EPI_PLAIN ? 18 * TILE_SITES : 1];
     int u = 0;
@@ -248,23 +350,39 @@ __global__ void __launch_bounds__(128, MB) k_dslash_tile(const __grid_constant__
     __syncthreads();
     const int lane = (int)(threadIdx.x & 31), warp = (int)(threadIdx.x >> 5), nw = (int)(blockDim.x >> 5);
     const int h = h0 + lane;
-    if (h >= U.a.Vh) return;
-    const SiteNb nb = site_neighbours(U.a, h);
+    const bool valid = h < U.a.Vh;
+    // the CG-fused steps keep every lane of the warp for the per-warp sums
+    if (CGM == 0 && !valid) return;
+    const SiteNb nb = site_neighbours(U.a, valid ? h : h0);
     for (int r = warp; r < U.nr; r += nw) {
         if (mask && mask[U.sys[r]] == 0.0) continue;
-        dslash_site_tile<PREC, RECON, DAG, EPI>(U.a, nb, U.in[r], U.out[r], U.xin[r], h, sL, sC, lane);
+        float v[2] = {0.f, 0.f};
+        if (valid)
+            dslash_site_tile<PREC, RECON, DAG, EPI, CGM>(U.a, nb, U.in[r], U.out[r], U.xin[r], h, sL, sC, lane, cg,
+                                                         U.sys[r], v);
+        if constexpr (CGM != 0) {
+            const int tile = (int)blockIdx.x - tab.block0[u];
+            double *pt = cg.partials + (size_t)U.sys[r] * 2 * cg.pstride + tile;
+            const float t0 = warp_sum_f(v[0]);
+            if (lane == 0) pt[0] = (double)t0;
+            if constexpr (CGM == CNT_CG_MHAT) {
+                const float t1 = warp_sum_f(v[1]);
+                if (lane == 0) pt[cg.pstride] = (double)t1;
+            }
+        }
     }
 }
 
 template <int PREC, int RECON, int MB>
 static void launch_tile_mb(const DslashBatchTable &tab, const double *mask, int nblocks, bool dag, int epi,
                            cudaStream_t s) {
+    const TileCg none{};
     if (dag) {
-        if (epi == EPI_CLOVINV) k_dslash_tile<PREC, RECON, true, EPI_CLOVINV, MB><<<nblocks, 128, 0, s>>>(tab, mask);
-        else k_dslash_tile<PREC, RECON, true, EPI_XPAY, MB><<<nblocks, 128, 0, s>>>(tab, mask);
+        if (epi == EPI_CLOVINV) k_dslash_tile<PREC, RECON, true, EPI_CLOVINV, MB><<<nblocks, 128, 0, s>>>(tab, mask, none);
+        else k_dslash_tile<PREC, RECON, true, EPI_XPAY, MB><<<nblocks, 128, 0, s>>>(tab, mask, none);
     } else {
-        if (epi == EPI_CLOVINV) k_dslash_tile<PREC, RECON, false, EPI_CLOVINV, MB><<<nblocks, 128, 0, s>>>(tab, mask);
-        else k_dslash_tile<PREC, RECON, false, EPI_XPAY, MB><<<nblocks, 128, 0, s>>>(tab, mask);
+        if (epi == EPI_CLOVINV) k_dslash_tile<PREC, RECON, false, EPI_CLOVINV, MB><<<nblocks, 128, 0, s>>>(tab, mask, none);
+        else k_dslash_tile<PREC, RECON, false, EPI_XPAY, MB><<<nblocks, 128, 0, s>>>(tab, mask, none);
     }
 }
 
@@ -289,4 +407,88 @@ void bq_tile_launch(int prec, int recon, const DslashBatchTable &tab, const doub
         else if (recon == 8) launch_tile_pr<BQ_PREC_HALF, 8>(tab, mask, nblocks, dag, epi, s);
         else launch_tile_pr<BQ_PREC_HALF, 18>(tab, mask, nblocks, dag, epi, s);
     }
+}
+
+// --------------------------------------------------------------------------
+// CG-fused A x - k D steps of an FP32 batch in the tile mapping
+
+template <int RECON, int MB>
+static void launch_tile_cg_mb(const DslashBatchTable &tab, const double *mask, int nblocks, int mode,
+                              const TileCg &cg, cudaStream_t s) {
+    if (mode == CNT_CG_MHAT)
+        k_dslash_tile<BQ_PREC_SINGLE, RECON, false, EPI_XPAY, MB, CNT_CG_MHAT><<<nblocks, 128, 0, s>>>(tab, mask, cg);
+    else
+        k_dslash_tile<BQ_PREC_SINGLE, RECON, true, EPI_XPAY, MB, CNT_CG_MHATDAG><<<nblocks, 128, 0, s>>>(tab, mask, cg);
+}
+
+template <int RECON>
+static void launch_tile_cg_r(const DslashBatchTable &tab, const double *mask, int nblocks, int mode, const TileCg &cg,
+                             cudaStream_t s) {
+    if (tab.variant == 6) launch_tile_cg_mb<RECON, 6>(tab, mask, nblocks, mode, cg, s);
+    else if (tab.variant == 5) launch_tile_cg_mb<RECON, 5>(tab, mask, nblocks, mode, cg, s);
+    else launch_tile_cg_mb<RECON, 4>(tab, mask, nblocks, mode, cg, s);
+}
+
+int bq_tile_cg_launch(bq_ctx *c, int recon, const DslashBatchTable *tab, const double *mask, int mode,
+                      const TileCg &cg, double site_bytes_total, double site_flops_total, double fused_bytes_total) {
+    if (tab->nunits < 1 || tab->units[0].interleave != 3 || !(mode == CNT_CG_MHAT || mode == CNT_CG_MHATDAG)) {
+        bq_set_error("fused CG step: units must take the shared-memory tile mapping");
+        return BQ_ERR_ARG;
+    }
+    const int nblocks = tab->block0[tab->nunits];
+    int slot;
+    BQ_TRY(bq_time_begin(c, BQ_PREC_SINGLE, mode, &slot));
+    if (recon == 12) launch_tile_cg_r<12>(*tab, mask, nblocks, mode, cg, c->stream);
+    else if (recon == 8) launch_tile_cg_r<8>(*tab, mask, nblocks, mode, cg, c->stream);
+    else launch_tile_cg_r<18>(*tab, mask, nblocks, mode, cg, c->stream);
+    BQ_LAUNCH_CHECK();
+    BQ_TRY(bq_time_end(c, slot));
+    BQ_COUNT(c);
+    c->counters.dslash_launches[BQ_PREC_SINGLE][mode]++;
+    c->counters.dslash_bytes[BQ_PREC_SINGLE][mode] += site_bytes_total;
+    c->counters.dslash_flops[BQ_PREC_SINGLE][mode] += site_flops_total;
+    c->counters.fused_bytes[BQ_PREC_SINGLE][mode] += fused_bytes_total;
+    return BQ_OK;
+}
+
+// the solver scalars of each system from the tile partials of a fused launch (one block
+// per system, tiles summed in order)
+template <int MODE>
+__global__ void __launch_bounds__(256) k_cg_finish_batch(const SysVec *sys, const double *partials, int pstride,
+                                                         double *scal_all, const double *mask) {
+    constexpr int NV = MODE == CNT_CG_MHAT ? 2 : 1;
+    const int sy = blockIdx.x;
+    if (mask && mask[sy] == 0.0) return;
+    const int nt = (sys[sy].Vh + 31) / 32;
+    const double *pt = partials + (size_t)sy * 2 * pstride;
+    double s[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) s[k] = 0.0;
+    for (int i = threadIdx.x; i < nt; i += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; k++) s[k] += pt[k * pstride + i];
+    block_sum(s);
+    if (threadIdx.x == 0) {
+        double *scal = scal_all + (size_t)sy * S_NSCAL;
+        if constexpr (MODE == CNT_CG_MHAT) {
+            const double pap = s[0] + scal[S_SIGMA] * s[1];
+            scal[S_PAP] = pap;
+            scal[S_ALPHA] = scal[S_RR] / pap;
+        } else {
+            const double rr = scal[S_RR];
+            scal[S_RRPREV] = rr;
+            scal[S_RR] = s[0];
+            scal[S_BETA] = s[0] / rr;
+        }
+    }
+}
+
+int bq_cg_finish_batch(bq_ctx *c, int mode, const TileCg &cg, const double *mask, int nsys) {
+    if (mode == CNT_CG_MHAT)
+        k_cg_finish_batch<CNT_CG_MHAT><<<nsys, 256, 0, c->stream>>>(cg.sys, cg.partials, cg.pstride, cg.scal, mask);
+    else
+        k_cg_finish_batch<CNT_CG_MHATDAG><<<nsys, 256, 0, c->stream>>>(cg.sys, cg.partials, cg.pstride, cg.scal, mask);
+    BQ_LAUNCH_CHECK();
+    BQ_COUNT(c);
+    return BQ_OK;
 }

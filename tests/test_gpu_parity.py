@@ -798,6 +798,28 @@ def test_batched_rhs_mappings(bq, mapping, prec):
     lat.close()
 
 
+@pytest.mark.parametrize("mapping", [-3, -5, -1])
+def test_batched_cg_shift_fused_tiles(bq, mapping):
+    """FP32 batched CG with a shift: in the tile mappings the x / r update and
+    <p, Ap> = |Mhat p|^2 + shift |p|^2 ride on the tile launches (the block-
+    interleaved mapping runs the separate kernels); every system against the oracle."""
+    dims = (6, 4, 6, 10)
+    lat, U, A, p = make(bq, dims, kappa=0.1350, csw=1.7, eps=0.2, mu=0.1, recon=12, precision="single")
+    bq.bq_set_batch_mapping(lat.ctx, mapping)
+    op = oracle.Operator(p, U)
+    bs = [synth.gaussian_spinor(lat.Vh, 340 + i) for i in range(3)]
+    xs = [np.empty_like(b) for b in bs]
+    bq.bq_reset_counters(lat.ctx)
+    stats = bq.bq_solve_cg_batch([lat.ctx] * 3, xs, bs, tol=1e-10, precision="single", shift=0.05)
+    c = bq.bq_get_counters(lat.ctx)
+    fused = c["dslash_launches"][1][3] > 0 and c["dslash_launches"][1][4] > 0
+    assert fused == (mapping <= -3) and (c["dslash_launches"][1][2] == 0) == fused
+    for b, x, st in zip(bs, xs, stats):
+        res = np.linalg.norm(op.mdagm(x, 0.05) - b) / np.linalg.norm(b)
+        assert st["converged"] and res <= 1e-10, res
+    lat.close()
+
+
 def test_next_rows_error_codes(bq):
     """Argument and state errors of the full-system, block multishift, stout,
     log det and trace entry points come back as status codes."""
