@@ -16,16 +16,19 @@
 
 namespace {
 
-// The partial sums leave each warp as soon as its sites are done (lane 0 stores
-// them, [NV][warps of the grid]); a one-block kernel then sums them in warp
-// order. Nothing in the hopping kernel waits on another warp or block.
+// The partial sums leave each warp as soon as its sites are done (summed over the
+// warp in FP32, like the per-site terms; lane 0 stores them in FP64, [NV][warps of
+// the grid]); a one-block kernel then sums them in warp order. Nothing in the
+// hopping kernel waits on another warp or block, and no FP64 arithmetic runs in it.
 template <int NV>
-__device__ __forceinline__ void warp_partials(double (&v)[NV], double *partials) {
+__device__ __forceinline__ void warp_partials(float (&v)[NV], double *partials) {
     const int nw = (int)(gridDim.x * blockDim.x) >> 5, w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
 #pragma unroll
     for (int k = 0; k < NV; k++) {
-        const double t = warp_sum(v[k]);
-        if ((threadIdx.x & 31) == 0) partials[k * nw + w] = t;
+        float t = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) partials[k * nw + w] = (double)t;
     }
 }
 
@@ -61,18 +64,49 @@ __global__ void __launch_bounds__(128, DslashMinBlocks<PS>::value) k_dslash_cg(c
     using T = typename Traits<PS>::real;
     constexpr int NV = MODE == CNT_CG_MHAT ? 2 : 1;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
-    double v[NV];
+    float v[NV];
 #pragma unroll
-    for (int k = 0; k < NV; k++) v[k] = 0.0;
+    for (int k = 0; k < NV; k++) v[k] = 0.f;
     if (h < a.Vh) {
         cplx<T> acc[12];
         dslash_hops<PS, RECON, MODE == CNT_CG_MHATDAG>(a, a.in, h, acc);
         if constexpr (MODE == CNT_CG_MHAT) {
-            cplx<T> xv[12], o[12];
-            xpay_site<PS>(a, a.xin, h, acc, xv, o);
-            SpinorIO<PS>::store(a.out, h, a.Vh, o);
-            v[0] = norm2_site(o);
-            v[1] = norm2_site(xv);
+            // t = A x - k acc one chirality block at a time, stored as it is formed
+            const float kk = (float)a.k;
+            const float4 *pxin = static_cast<const float4 *>(a.xin) + h;
+            float4 *po = static_cast<float4 *>(a.out) + h;
+            float n0 = 0.f, n1 = 0.f;
+#pragma unroll
+            for (int b = 0; b < 2; b++) {
+                cplx<T> o[6];
+                {
+                    cplx<T> xb[6];
+#pragma unroll
+                    for (int j = 0; j < 3; j++) {
+                        const float4 x4 = ldg(pxin + (size_t)(3 * b + j) * a.Vh);
+                        xb[2 * j] = {x4.x, x4.y};
+                        xb[2 * j + 1] = {x4.z, x4.w};
+                        n1 += x4.x * x4.x + x4.y * x4.y + x4.z * x4.z + x4.w * x4.w;
+                    }
+                    T d[6];
+                    cplx<T> od[15];
+                    CloverIO<PS>::load_block(d, od, a.clov, b, h, a.Vh);
+                    herm6_apply(d, od, xb, o);
+                }
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    const int k = 3 * b + j;
+                    float4 t4;
+                    t4.x = fmaf(-kk, acc[2 * k].re, o[2 * j].re);
+                    t4.y = fmaf(-kk, acc[2 * k].im, o[2 * j].im);
+                    t4.z = fmaf(-kk, acc[2 * k + 1].re, o[2 * j + 1].re);
+                    t4.w = fmaf(-kk, acc[2 * k + 1].im, o[2 * j + 1].im);
+                    po[(size_t)k * a.Vh] = t4;
+                    n0 += t4.x * t4.x + t4.y * t4.y + t4.z * t4.z + t4.w * t4.w;
+                }
+            }
+            v[0] = n0;
+            v[1] = n1;
         } else {
             // q = A x - k acc + sigma p one chirality block (six components) at a time,
             // each followed by the x / r update of its three float4 chunks
@@ -122,7 +156,7 @@ __global__ void __launch_bounds__(128, DslashMinBlocks<PS>::value) k_dslash_cg(c
                     nr += r4.x * r4.x + r4.y * r4.y + r4.z * r4.z + r4.w * r4.w;
                 }
             }
-            v[0] = (double)nr;
+            v[0] = nr;
         }
     }
     warp_partials(v, f.partials);
