@@ -15,6 +15,9 @@
 
 __device__ __forceinline__ df dneg(df x, bool n) { return n ? df(-x.hi, -x.lo) : x; }
 
+// hint: bring the line holding p into L1 (no register is written; p is a valid address)
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 // z * i^k, k in 0..3
 __device__ __forceinline__ cplx<df> mul_ipow(cplx<df> z, int k) {
     const bool sw = k & 1, nre = (k == 1 || k == 2), nim = (k >= 2);
@@ -70,22 +73,43 @@ __device__ __forceinline__ void dslash_site_df64_pair(const DslashArgs &a, const
 #pragma unroll
     for (int c = 0; c < 3; c++) up[c] = p2[c] = p3[c] = {T(0), T(0)};
 
+    // neighbour of h in direction d = 2 mu + back
+    auto neighbour = [&](int d) -> int {
+        switch (d) {
+            case 0: return h - xh + (((x + 1 == a.L0) ? 0 : x + 1) >> 1);
+            case 1: return h - xh + (((x == 0) ? a.L0 - 1 : x - 1) >> 1);
+            case 2: return (y + 1 == a.L1) ? h - (a.L1 - 1) * sy : h + sy;
+            case 3: return (y == 0) ? h + (a.L1 - 1) * sy : h - sy;
+            case 4: return (z + 1 == a.L2) ? h - (a.L2 - 1) * sz : h + sz;
+            case 5: return (z == 0) ? h + (a.L2 - 1) * sz : h - sz;
+            case 6: return (t + 1 == a.L3) ? h - (a.L3 - 1) * st : h + st;
+            default: return (t == 0) ? h + (a.L3 - 1) * st : h - st;
+        }
+    };
+    // the next hop's two spinor components (16-byte entries in either storage) and
+    // link entries are requested into L1 while this hop computes: the loop is rolled,
+    // so the compiler does not hoist those loads itself
+    auto prefetch_hop = [&](int d) {
+        const int mu = d >> 1, hn = neighbour(d);
+        const int jq = mu < 2 ? (q ? 2 : 3) : (q ? 3 : 2);
+        const float4 *pp = static_cast<const float4 *>(in) + hn;
+        const float4 *pl = reinterpret_cast<const float4 *>(((d & 1) ? Li : Lo) + (size_t)mu * a.lblk) + ((d & 1) ? hn : h);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            prefetch_l1(pp + (size_t)(3 * q + c) * Vh);
+            prefetch_l1(pp + (size_t)(3 * jq + c) * Vh);
+        }
+#pragma unroll
+        for (int e = 0; e < (RECON == 12 ? 6 : 9); e++) prefetch_l1(pl + (size_t)e * Vh);
+    };
+    prefetch_hop(0);
 #pragma unroll 1
     for (int d = 0; d < 8; d++) {
         const int mu = d >> 1;
         const bool back = d & 1;
         const int S = back ? -SF : SF;
-        int hn;
-        switch (d) {
-            case 0: hn = h - xh + (((x + 1 == a.L0) ? 0 : x + 1) >> 1); break;
-            case 1: hn = h - xh + (((x == 0) ? a.L0 - 1 : x - 1) >> 1); break;
-            case 2: hn = (y + 1 == a.L1) ? h - (a.L1 - 1) * sy : h + sy; break;
-            case 3: hn = (y == 0) ? h + (a.L1 - 1) * sy : h - sy; break;
-            case 4: hn = (z + 1 == a.L2) ? h - (a.L2 - 1) * sz : h + sz; break;
-            case 5: hn = (z == 0) ? h + (a.L2 - 1) * sz : h - sz; break;
-            case 6: hn = (t + 1 == a.L3) ? h - (a.L3 - 1) * st : h + st; break;
-            default: hn = (t == 0) ? h + (a.L3 - 1) * st : h - st; break;
-        }
+        const int hn = neighbour(d);
+        if (d < 7) prefetch_hop(d + 1);
         const char *lb = (back ? Li : Lo) + (size_t)mu * a.lblk;
         const int hl = back ? hn : h;
         // projector data (see dslash_site_df64): h_q = psi_q + i^kq psi_jq; this lane's
