@@ -49,7 +49,7 @@ __device__ __forceinline__ df dshfl(df v) {
 
 // FMT: DF_IN_PAIR / DF_X_PAIR / DF_OUT_PAIR select float-pair storage for the
 // hopped spinor, the xpay spinor and the output (FP64 otherwise)
-template <int RECON, bool DAG, int EPI, int FMT>
+template <int RECON, bool DAG, int EPI, int FMT, bool PREFETCH = true>
 __device__ __forceinline__ void dslash_site_df64_pair(const DslashArgs &a, const void *in, void *out, const void *xin,
                                                       const int h, const int q, const bool valid) {
     using T = df;
@@ -102,14 +102,14 @@ __device__ __forceinline__ void dslash_site_df64_pair(const DslashArgs &a, const
 #pragma unroll
         for (int e = 0; e < (RECON == 12 ? 6 : 9); e++) prefetch_l1(pl + (size_t)e * Vh);
     };
-    prefetch_hop(0);
+    if (PREFETCH) prefetch_hop(0);
 #pragma unroll 1
     for (int d = 0; d < 8; d++) {
         const int mu = d >> 1;
         const bool back = d & 1;
         const int S = back ? -SF : SF;
         const int hn = neighbour(d);
-        if (d < 7) prefetch_hop(d + 1);
+        if (PREFETCH && d < 7) prefetch_hop(d + 1);
         const char *lb = (back ? Li : Lo) + (size_t)mu * a.lblk;
         const int hl = back ? hn : h;
         // projector data (see dslash_site_df64): h_q = psi_q + i^kq psi_jq; this lane's
@@ -293,6 +293,8 @@ __global__ void __launch_bounds__(128, DF64P_MIN_BLOCKS) k_dslash_batch_df64p(co
     if (mask && mask[U.sys[r]] == 0.0) return;  // the whole block: one right-hand side
     const int h = (bl / U.nr) * 64 + (int)(threadIdx.x >> 1);
     const bool valid = h < U.a.Vh;
-    dslash_site_df64_pair<RECON, DAG, EPI, FMT>(U.a, U.in[r], U.out[r], U.xin[r], valid ? h : U.a.Vh - 1,
+    // no L1 prefetch here: with the unit indirection it costs registers (spills) and
+    // measured slower (12-rhs batch, 24^3x48: 2.8 -> 3.1 ms per launch)
+    dslash_site_df64_pair<RECON, DAG, EPI, FMT, false>(U.a, U.in[r], U.out[r], U.xin[r], valid ? h : U.a.Vh - 1,
                                                 (int)(threadIdx.x & 1), valid);
 }

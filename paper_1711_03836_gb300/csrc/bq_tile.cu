@@ -184,6 +184,24 @@ __device__ __forceinline__ void dslash_site_tile(const DslashArgs &a, const Site
     const int Vh = a.Vh;
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
+    if constexpr (CGM != 0) {
+        // the epilogue's vectors at this site (x, and for the update p, xs, rs) from DRAM into
+        // L2 while the eight hops run, so that their traffic overlaps the latency-bound hops
+        const float4 *px = static_cast<const float4 *>(xin) + h;
+#pragma unroll
+        for (int k = 0; k < 6; k++) asm volatile("prefetch.global.L2 [%0];" ::"l"(px + (size_t)k * Vh));
+        if constexpr (CGM == CNT_CG_MHATDAG) {
+            const SysVec &sv = cg.sys[sys];
+            const float4 *q0 = static_cast<const float4 *>(sv.p) + h, *q1 = static_cast<const float4 *>(sv.xs) + h,
+                         *q2 = static_cast<const float4 *>(sv.rs) + h;
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(q0 + (size_t)k * Vh));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(q1 + (size_t)k * Vh));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(q2 + (size_t)k * Vh));
+            }
+        }
+    }
     cplx<float> acc[12];
 #pragma unroll
     for (int c = 0; c < 12; c++) acc[c] = {0.f, 0.f};
