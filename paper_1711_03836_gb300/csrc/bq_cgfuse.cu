@@ -68,6 +68,17 @@ __global__ void __launch_bounds__(128, DslashMinBlocks<PS>::value) k_dslash_cg(c
 #pragma unroll
     for (int k = 0; k < NV; k++) v[k] = 0.f;
     if (h < a.Vh) {
+        if constexpr (MODE == CNT_CG_MHATDAG) {
+            // the update's vectors at h from DRAM into L2 while the eight hops run
+            const float4 *q0 = static_cast<const float4 *>(f.p) + h, *q1 = static_cast<const float4 *>(f.xs) + h,
+                         *q2 = static_cast<const float4 *>(f.rs) + h;
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(q0 + (size_t)k * a.Vh));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(q1 + (size_t)k * a.Vh));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(q2 + (size_t)k * a.Vh));
+            }
+        }
         cplx<T> acc[12];
         dslash_hops<PS, RECON, MODE == CNT_CG_MHATDAG>(a, a.in, h, acc);
         if constexpr (MODE == CNT_CG_MHAT) {
