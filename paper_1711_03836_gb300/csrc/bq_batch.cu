@@ -783,10 +783,9 @@ static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double 
     };
     const BArgs ba_act{w->d_sys, w->d_scal, w->d_part, w->d_ticket, d_active};
     const BArgs ba_upd{w->d_sys, w->d_scal, w->d_part, w->d_ticket, d_update};
-    // one system with an FP32 inner iteration: the CG vector work rides on the two A x - k D
-    // launches (with FP16 storage the hopping kernels are bound by instruction issue, not by
-    // memory, and the fused vector traffic measured no faster than the separate kernels)
-    const bool fuse = nsys == 1 && PS == BQ_PREC_SINGLE;
+    // one system with an FP32 or FP16-storage inner iteration: the CG vector work rides on
+    // the two A x - k D launches
+    const bool fuse = nsys == 1 && PS != BQ_PREC_DOUBLE;
     CgFuse cgf{};
     if (fuse) {
         const size_t need = 8 * (size_t)((ctxs[0]->Vh + 127) / 128);  // two values per warp
@@ -797,7 +796,8 @@ static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double 
             BQ_TRY(bq_alloc((void **)&w->d_fpart, sizeof(double) * need));
             w->fpart_n = need;
         }
-        cgf = CgFuse{w->slot[0].p, w->slot[0].xs, w->slot[0].rs, w->d_scal, w->d_fpart};
+        const double sigma0 = shifts ? shifts[0] : sp->shift;
+        cgf = CgFuse{w->slot[0].p, w->slot[0].xs, w->slot[0].rs, w->d_scal, w->d_fpart, sigma0 != 0.0};
     }
     // several FP32 systems in the shared-memory tile mapping: the same fusion inside the tile kernel
     const bool fuse_tiles = nsys > 1 && PS == BQ_PREC_SINGLE && mapping <= -3;

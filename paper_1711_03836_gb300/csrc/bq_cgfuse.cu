@@ -1,11 +1,11 @@
 // bq_cgfuse.cu -- one CG iteration on Mhat^dag Mhat + sigma (Section 3: cg)
 // with its vector work folded into the two hopping-term launches that end in
-// A x - k D (single system, FP32 inner iteration).
+// A x - k D (single system, FP32 or FP16-storage inner iteration).
 //
 // Of the four launches of Ap = (Mhat^dag Mhat + sigma) p the second produces
 // t = Mhat p = A_ee p - k D_eo A_oo^{-1} D_oe p and the fourth Mhat^dag t. As
-// <p, Mhat^dag Mhat p> = |Mhat p|^2, the second launch sums |t|^2 and |p|^2
-// (p is its x spinor), a one-block kernel sets <p, Ap> = |t|^2 + sigma |p|^2 and
+// <p, Mhat^dag Mhat p> = |Mhat p|^2, the second launch sums |t|^2 and, with a
+// shift, |p|^2 (p is its x spinor), a one-block kernel sets <p, Ap> = |t|^2 + sigma |p|^2 and
 // alpha = rr / <p, Ap>; the fourth forms q = Mhat^dag t + sigma p per site and,
 // instead of storing q, updates xs += alpha p and rs -= alpha q, sums |rs|^2
 // and a one-block kernel sets rr and beta. This removes the <p, Ap> kernel and the
@@ -59,7 +59,35 @@ __global__ void __launch_bounds__(CG_FIN_THREADS) k_cg_finish(const double *part
     }
 }
 
-template <int PS, int RECON, int MODE>
+// the six components of chirality block b (0: spins 0, 1; 1: spins 2, 3) of the
+// spinor at h: FP32 [6][V/2] float4, or FP16 [3][V/2] uint4 with the site's scale
+// after them (block 0 is uint4 0 and half of uint4 1, block 1 the rest)
+template <int PS>
+__device__ __forceinline__ void load_block6(cplx<float> out[6], const void *base, int h, int Vh, int b) {
+    if constexpr (PS == BQ_PREC_SINGLE) {
+        const float4 *p = static_cast<const float4 *>(base) + h;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const float4 v = ldg(p + (size_t)(3 * b + j) * Vh);
+            out[2 * j] = {v.x, v.y};
+            out[2 * j + 1] = {v.z, v.w};
+        }
+    } else {
+        const uint4 *p = static_cast<const uint4 *>(base);
+        const float n = ldg(reinterpret_cast<const float *>(p + (size_t)3 * Vh) + h);
+        const uint4 u0 = ldg(p + (size_t)(b == 0 ? 0 : 1) * Vh + h), u1 = ldg(p + (size_t)(b == 0 ? 1 : 2) * Vh + h);
+        const unsigned w[6] = {b == 0 ? u0.x : u0.z, b == 0 ? u0.y : u0.w, b == 0 ? u0.z : u1.x,
+                               b == 0 ? u0.w : u1.y, b == 0 ? u1.x : u1.z, b == 0 ? u1.y : u1.w};
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+            const float2 c = h2f(w[j]);
+            out[j] = {c.x * n, c.y * n};
+        }
+    }
+}
+
+// PN: sum |p|^2 in the Mhat step (a nonzero shift)
+template <int PS, int RECON, int MODE, bool PN>
 __global__ void __launch_bounds__(128, DslashMinBlocks<PS>::value) k_dslash_cg(const DslashArgs a, const CgFuse f) {
     using T = typename Traits<PS>::real;
     constexpr int NV = MODE == CNT_CG_MHAT ? 2 : 1;
@@ -70,21 +98,34 @@ __global__ void __launch_bounds__(128, DslashMinBlocks<PS>::value) k_dslash_cg(c
     if (h < a.Vh) {
         if constexpr (MODE == CNT_CG_MHATDAG) {
             // the update's vectors at h from DRAM into L2 while the eight hops run
+            // (FP16 p: its three uint4 words; the scale shares a line with its neighbours')
             const float4 *q0 = static_cast<const float4 *>(f.p) + h, *q1 = static_cast<const float4 *>(f.xs) + h,
                          *q2 = static_cast<const float4 *>(f.rs) + h;
 #pragma unroll
             for (int k = 0; k < 6; k++) {
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(q0 + (size_t)k * a.Vh));
+                if (PS == BQ_PREC_SINGLE || k < 3) asm volatile("prefetch.global.L2 [%0];" ::"l"(q0 + (size_t)k * a.Vh));
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(q1 + (size_t)k * a.Vh));
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(q2 + (size_t)k * a.Vh));
             }
         }
         cplx<T> acc[12];
         dslash_hops<PS, RECON, MODE == CNT_CG_MHATDAG>(a, a.in, h, acc);
-        if constexpr (MODE == CNT_CG_MHAT) {
+        if constexpr (MODE == CNT_CG_MHAT && PS == BQ_PREC_HALF) {
+            // FP16 t: the site's scale needs all twelve components before the store
+            cplx<T> xv[12], o[12];
+            xpay_site<PS>(a, a.xin, h, acc, xv, o);
+            SpinorIO<PS>::store(a.out, h, a.Vh, o);
+            float n0 = 0.f, n1 = 0.f;
+#pragma unroll
+            for (int c = 0; c < 12; c++) n0 += o[c].re * o[c].re + o[c].im * o[c].im;
+            if (PN)
+#pragma unroll
+                for (int c = 0; c < 12; c++) n1 += xv[c].re * xv[c].re + xv[c].im * xv[c].im;
+            v[0] = n0;
+            v[1] = n1;
+        } else if constexpr (MODE == CNT_CG_MHAT) {
             // t = A x - k acc one chirality block at a time, stored as it is formed
             const float kk = (float)a.k;
-            const float4 *pxin = static_cast<const float4 *>(a.xin) + h;
             float4 *po = static_cast<float4 *>(a.out) + h;
             float n0 = 0.f, n1 = 0.f;
 #pragma unroll
@@ -92,13 +133,10 @@ __global__ void __launch_bounds__(128, DslashMinBlocks<PS>::value) k_dslash_cg(c
                 cplx<T> o[6];
                 {
                     cplx<T> xb[6];
+                    load_block6<PS>(xb, a.xin, h, a.Vh, b);
+                    if (PN)
 #pragma unroll
-                    for (int j = 0; j < 3; j++) {
-                        const float4 x4 = ldg(pxin + (size_t)(3 * b + j) * a.Vh);
-                        xb[2 * j] = {x4.x, x4.y};
-                        xb[2 * j + 1] = {x4.z, x4.w};
-                        n1 += x4.x * x4.x + x4.y * x4.y + x4.z * x4.z + x4.w * x4.w;
-                    }
+                        for (int j = 0; j < 6; j++) n1 += xb[j].re * xb[j].re + xb[j].im * xb[j].im;
                     T d[6];
                     cplx<T> od[15];
                     CloverIO<PS>::load_block(d, od, a.clov, b, h, a.Vh);
@@ -120,12 +158,10 @@ __global__ void __launch_bounds__(128, DslashMinBlocks<PS>::value) k_dslash_cg(c
             v[1] = n1;
         } else {
             // q = A x - k acc + sigma p one chirality block (six components) at a time,
-            // each followed by the x / r update of its three float4 chunks
+            // each followed by the x / r update of its three float4 chunks (x, r in FP32)
             const float alpha = (float)f.scal[S_ALPHA];
             const float sigma = (float)f.scal[S_SIGMA];
             const float kk = (float)a.k;
-            const float4 *pxin = static_cast<const float4 *>(a.xin) + h;
-            const float4 *pp = static_cast<const float4 *>(f.p) + h;
             float4 *px = static_cast<float4 *>(f.xs) + h, *pr = static_cast<float4 *>(f.rs) + h;
             float nr = 0.f;
 #pragma unroll
@@ -133,21 +169,23 @@ __global__ void __launch_bounds__(128, DslashMinBlocks<PS>::value) k_dslash_cg(c
                 cplx<T> o[6];
                 {
                     cplx<T> xb[6];
-#pragma unroll
-                    for (int j = 0; j < 3; j++) {
-                        const float4 x4 = ldg(pxin + (size_t)(3 * b + j) * a.Vh);
-                        xb[2 * j] = {x4.x, x4.y};
-                        xb[2 * j + 1] = {x4.z, x4.w};
-                    }
+                    load_block6<PS>(xb, a.xin, h, a.Vh, b);
                     T d[6];
                     cplx<T> od[15];
                     CloverIO<PS>::load_block(d, od, a.clov, b, h, a.Vh);
                     herm6_apply(d, od, xb, o);
                 }
+                // FP32 p one float4 at a time; FP16 p a block at a time (its words hold four components)
+                cplx<float> pb[PS == BQ_PREC_HALF ? 6 : 1];
+                if constexpr (PS == BQ_PREC_HALF) load_block6<PS>(pb, f.p, h, a.Vh, b);
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
                     const int k = 3 * b + j;
-                    const float4 p4 = ldg(pp + (size_t)k * a.Vh);
+                    float4 p4;
+                    if constexpr (PS == BQ_PREC_HALF)
+                        p4 = make_float4(pb[2 * j].re, pb[2 * j].im, pb[2 * j + 1].re, pb[2 * j + 1].im);
+                    else
+                        p4 = ldg(static_cast<const float4 *>(f.p) + h + (size_t)k * a.Vh);
                     float4 x4 = px[(size_t)k * a.Vh], r4 = pr[(size_t)k * a.Vh];
                     const cplx<T> a0 = acc[2 * k], a1 = acc[2 * k + 1];
                     const float q0r = fmaf(sigma, p4.x, fmaf(-kk, a0.re, o[2 * j].re));
@@ -175,8 +213,9 @@ __global__ void __launch_bounds__(128, DslashMinBlocks<PS>::value) k_dslash_cg(c
 
 template <int PS, int RECON>
 void launch_cg(const DslashArgs &a, const CgFuse &f, int mode, unsigned grid, cudaStream_t s) {
-    if (mode == CNT_CG_MHAT) k_dslash_cg<PS, RECON, CNT_CG_MHAT><<<grid, 128, 0, s>>>(a, f);
-    else k_dslash_cg<PS, RECON, CNT_CG_MHATDAG><<<grid, 128, 0, s>>>(a, f);
+    if (mode == CNT_CG_MHAT && f.with_pnorm) k_dslash_cg<PS, RECON, CNT_CG_MHAT, true><<<grid, 128, 0, s>>>(a, f);
+    else if (mode == CNT_CG_MHAT) k_dslash_cg<PS, RECON, CNT_CG_MHAT, false><<<grid, 128, 0, s>>>(a, f);
+    else k_dslash_cg<PS, RECON, CNT_CG_MHATDAG, false><<<grid, 128, 0, s>>>(a, f);
 }
 
 void launch_finish(const CgFuse &f, int mode, unsigned grid, cudaStream_t s) {
@@ -196,8 +235,8 @@ void launch_cg_r(int recon, const DslashArgs &a, const CgFuse &f, int mode, unsi
 
 int bq_dslash_cg_launch(bq_ctx *c, int ps, void *out, const void *in, const void *xin, double k, int mode,
                         const CgFuse &f) {
-    if (ps != BQ_PREC_SINGLE || !(mode == CNT_CG_MHAT || mode == CNT_CG_MHATDAG)) {
-        bq_set_error("fused CG step: FP32 inner precision only");
+    if (!(ps == BQ_PREC_SINGLE || ps == BQ_PREC_HALF) || !(mode == CNT_CG_MHAT || mode == CNT_CG_MHATDAG)) {
+        bq_set_error("fused CG step: FP32 or FP16 inner precision only");
         return BQ_ERR_ARG;
     }
     const int dagger = mode == CNT_CG_MHATDAG;
@@ -210,7 +249,8 @@ int bq_dslash_cg_launch(bq_ctx *c, int ps, void *out, const void *in, const void
     const unsigned grid = (unsigned)((c->Vh + 127) / 128);
     int slot;
     BQ_TRY(bq_time_begin(c, ps, mode, &slot));
-    launch_cg_r<BQ_PREC_SINGLE>(recon, a, f, mode, grid, c->stream);
+    if (ps == BQ_PREC_SINGLE) launch_cg_r<BQ_PREC_SINGLE>(recon, a, f, mode, grid, c->stream);
+    else launch_cg_r<BQ_PREC_HALF>(recon, a, f, mode, grid, c->stream);
     BQ_LAUNCH_CHECK();
     BQ_TRY(bq_time_end(c, slot));
     BQ_COUNT(c);

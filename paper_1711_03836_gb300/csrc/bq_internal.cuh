@@ -195,14 +195,15 @@ int bq_tile_cg_launch(bq_ctx *c, int recon, const DslashBatchTable *tab, const d
 int bq_cg_finish_batch(bq_ctx *c, int mode, const TileCg &cg, const double *mask, int nsys);
 
 // The CG vector work fused into the two A x - k D launches of one CG iteration
-// on Mhat^dag Mhat + sigma (single system, FP32 inner iteration; bq_cgfuse.cu).
+// on Mhat^dag Mhat + sigma (single system, FP32 or FP16-storage inner iteration; bq_cgfuse.cu).
 // scal: the system's solver scalars (S_* slots of bq_reduce.cuh); partials: 2 doubles
 // per warp of the launch (8 * ceil(V/2 / 128))
 struct CgFuse {
-    const void *p;  // search direction, FP32
+    const void *p;  // search direction, precision ps
     void *xs, *rs;  // iterated solution and residual, FP32
     double *scal;
     double *partials;
+    int with_pnorm;  // sum |p|^2 too (the shift is nonzero)
 };
 // mode CNT_CG_MHAT: out = t = A_ee p - k D_eo in (xin = p), then <p, Ap> = |t|^2 + sigma |p|^2
 //   and alpha = rr / <p, Ap>; mode CNT_CG_MHATDAG: q = A_ee^dag xin - k D_eo^dag in + sigma p
