@@ -153,7 +153,7 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ traffic from the committed ncu summary
 
-KERNEL_SOURCES = ("bq_device.cuh", "bq_stencil.cuh", "bq_cgfuse.cu")  # the files that define k_dslash, k_dslash_cg
+KERNEL_SOURCES = ("bq_device.cuh", "bq_stencil.cuh", "bq_cgfuse.cuh", "bq_cgfuse.cu")  # the files that define k_dslash, k_dslash_cg
 
 
 def kernel_source_hash():

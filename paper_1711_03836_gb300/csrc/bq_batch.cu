@@ -799,8 +799,8 @@ static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double 
         const double sigma0 = shifts ? shifts[0] : sp->shift;
         cgf = CgFuse{w->slot[0].p, w->slot[0].xs, w->slot[0].rs, w->d_scal, w->d_fpart, sigma0 != 0.0};
     }
-    // several FP32 systems in the shared-memory tile mapping: the same fusion inside the tile kernel
-    const bool fuse_tiles = nsys > 1 && PS == BQ_PREC_SINGLE && mapping <= -3;
+    // several FP32 / FP16 systems in the shared-memory tile mapping: the same fusion inside the tile kernel
+    const bool fuse_tiles = nsys > 1 && PS != BQ_PREC_DOUBLE && mapping <= -3;
     TileCg tcg{};
     double sum_vh = 0.0;
     if (fuse_tiles) {
@@ -875,10 +875,10 @@ static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double 
                 const int mode = k == 1 ? CNT_CG_MHAT : CNT_CG_MHATDAG;
                 const std::vector<DslashBatchTable> &tabs = w->tables[k];
                 const double nt = (double)tabs.size();
-                // step 3 moves p, x and r (x and r twice) in place of its output: 4 FP32 spinors per site
-                const double fused = mode == CNT_CG_MHATDAG ? 4.0 * spinor_bytes_per_site(PS) * sum_vh * frac / nt : 0.0;
+                // step 3 moves p, x and r (x and r twice) in place of its output: 4 spinors of x's precision
+                const double fused = mode == CNT_CG_MHATDAG ? 4.0 * spinor_bytes_per_site(PR) * sum_vh * frac / nt : 0.0;
                 for (size_t q = 0; q < tabs.size(); q++)
-                    BQ_TRY(bq_tile_cg_launch(c0, recon_s, &tabs[q], d_active, mode, tcg,
+                    BQ_TRY(bq_tile_cg_launch(c0, PS, recon_s, &tabs[q], d_active, mode, tcg,
                                              plan.bytes_all[k] * frac / nt, plan.flops_all[k] * frac / nt, fused));
                 BQ_TRY(bq_cg_finish_batch(c0, mode, tcg, d_active, nsys));
             }

@@ -180,7 +180,7 @@ struct SysVec {
     int Vh;
 };
 
-// The same fusion for a batch of FP32 systems in the shared-memory tile mapping
+// The same fusion for a batch of FP32 / FP16-storage systems in the shared-memory tile mapping
 // (bq_tile.cu): per system and tile of 32 sites one partial per value, [nsys][2][pstride]
 // with pstride >= the tiles of the largest lattice; scal [nsys][S_NSCAL]
 struct TileCg {
@@ -189,7 +189,7 @@ struct TileCg {
     double *partials;
     int pstride;
 };
-int bq_tile_cg_launch(bq_ctx *c, int recon, const DslashBatchTable *tab, const double *mask, int mode,
+int bq_tile_cg_launch(bq_ctx *c, int prec, int recon, const DslashBatchTable *tab, const double *mask, int mode,
                       const TileCg &cg, double site_bytes_total, double site_flops_total, double fused_bytes_total);
 // the solver scalars of every unmasked system from the tile partials of a fused launch
 int bq_cg_finish_batch(bq_ctx *c, int mode, const TileCg &cg, const double *mask, int nsys);

@@ -2,6 +2,7 @@
 // the clover term of a tile of sites staged in shared memory once for all
 // right-hand sides of a unit (the block solvers of Section 3 apply one operator
 // to many right-hand sides), FP32 and FP16 storage.
+#include "bq_cgfuse.cuh"
 #include "bq_reduce.cuh"
 #include "bq_stencil.cuh"
 
@@ -174,7 +175,7 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     return v;
 }
 
-// CGM: 0, or the CG-fused A x - k D steps of an FP32 batch (CNT_CG_MHAT: store t and
+// CGM: 0, or the CG-fused A x - k D steps of a batch (CNT_CG_MHAT: store t and
 // return |t|^2, |x|^2 in v; CNT_CG_MHATDAG: q = A x - k D in + sigma p of system sys,
 // xs += alpha p, rs -= alpha q, return |rs|^2 in v[0]; nothing stored to out)
 template <int PREC, int RECON, bool DAG, int EPI, int CGM>
@@ -187,16 +188,18 @@ __device__ __forceinline__ void dslash_site_tile(const DslashArgs &a, const Site
     if constexpr (CGM != 0) {
         // the epilogue's vectors at this site (x, and for the update p, xs, rs) from DRAM into
         // L2 while the eight hops run, so that their traffic overlaps the latency-bound hops
+        // (FP16 spinors: their three uint4 words; x and r are FP32 in either case)
+        constexpr int NW = PREC == BQ_PREC_SINGLE ? 6 : 3;
         const float4 *px = static_cast<const float4 *>(xin) + h;
 #pragma unroll
-        for (int k = 0; k < 6; k++) asm volatile("prefetch.global.L2 [%0];" ::"l"(px + (size_t)k * Vh));
+        for (int k = 0; k < NW; k++) asm volatile("prefetch.global.L2 [%0];" ::"l"(px + (size_t)k * Vh));
         if constexpr (CGM == CNT_CG_MHATDAG) {
             const SysVec &sv = cg.sys[sys];
             const float4 *q0 = static_cast<const float4 *>(sv.p) + h, *q1 = static_cast<const float4 *>(sv.xs) + h,
                          *q2 = static_cast<const float4 *>(sv.rs) + h;
 #pragma unroll
             for (int k = 0; k < 6; k++) {
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(q0 + (size_t)k * Vh));
+                if (k < NW) asm volatile("prefetch.global.L2 [%0];" ::"l"(q0 + (size_t)k * Vh));
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(q1 + (size_t)k * Vh));
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(q2 + (size_t)k * Vh));
             }
@@ -232,11 +235,11 @@ __device__ __forceinline__ void dslash_site_tile(const DslashArgs &a, const Site
     if constexpr (CGM == CNT_CG_MHATDAG) {
         // one chirality block (six components) at a time, each followed by the update of
         // its three float4 chunks of x and r
-        static_assert(PREC == BQ_PREC_SINGLE && EPI == EPI_XPAY, "fused CG update: FP32 xpay step");
+        static_assert(EPI == EPI_XPAY, "fused CG update: xpay step");
         const SysVec &sv = cg.sys[sys];
         const double *sc = cg.scal + (size_t)sys * S_NSCAL;
         const float alpha = (float)sc[S_ALPHA], sigma = (float)sc[S_SIGMA], kk = (float)a.k;
-        const float4 *pxin = static_cast<const float4 *>(xin) + h, *pp = static_cast<const float4 *>(sv.p) + h;
+        const float4 *pp = static_cast<const float4 *>(sv.p) + h;
         float4 *px = static_cast<float4 *>(sv.xs) + h, *pr = static_cast<float4 *>(sv.rs) + h;
         float nr = 0.f;
 #pragma unroll
@@ -244,21 +247,23 @@ __device__ __forceinline__ void dslash_site_tile(const DslashArgs &a, const Site
             cplx<float> ob[6];
             {
                 cplx<float> xb[6];
-#pragma unroll
-                for (int j = 0; j < 3; j++) {
-                    const float4 x4 = ldg(pxin + (size_t)(3 * b + j) * Vh);
-                    xb[2 * j] = {x4.x, x4.y};
-                    xb[2 * j + 1] = {x4.z, x4.w};
-                }
+                load_block6<PREC>(xb, xin, h, Vh, b);
                 float d[6];
                 cplx<float> od[15];
                 tile_clover_block(d, od, sC, b, lane);
                 herm6_apply(d, od, xb, ob);
             }
+            // FP32 p one float4 at a time; FP16 p a block at a time
+            cplx<float> pb[PREC == BQ_PREC_HALF ? 6 : 1];
+            if constexpr (PREC == BQ_PREC_HALF) load_block6<PREC>(pb, sv.p, h, Vh, b);
 #pragma unroll
             for (int j = 0; j < 3; j++) {
                 const int k = 3 * b + j;
-                const float4 p4 = ldg(pp + (size_t)k * Vh);
+                float4 p4;
+                if constexpr (PREC == BQ_PREC_HALF)
+                    p4 = make_float4(pb[2 * j].re, pb[2 * j].im, pb[2 * j + 1].re, pb[2 * j + 1].im);
+                else
+                    p4 = ldg(pp + (size_t)k * Vh);
                 float4 x4 = px[(size_t)k * Vh], r4 = pr[(size_t)k * Vh];
                 const float q0r = fmaf(sigma, p4.x, fmaf(-kk, acc[2 * k].re, ob[2 * j].re));
                 const float q0i = fmaf(sigma, p4.y, fmaf(-kk, acc[2 * k].im, ob[2 * j].im));
@@ -280,9 +285,9 @@ __device__ __forceinline__ void dslash_site_tile(const DslashArgs &a, const Site
         v[0] = nr;
         return;
     }
-    if constexpr (CGM == CNT_CG_MHAT) {
+    if constexpr (CGM == CNT_CG_MHAT && PREC == BQ_PREC_SINGLE) {
         // t = A x - k D in one chirality block at a time, stored as it is formed, with |t|^2 and |x|^2
-        static_assert(PREC == BQ_PREC_SINGLE && EPI == EPI_XPAY, "fused CG norms: FP32 xpay step");
+        static_assert(EPI == EPI_XPAY, "fused CG norms: xpay step");
         const float kk = (float)a.k;
         const float4 *pxin = static_cast<const float4 *>(xin) + h;
         float4 *po = static_cast<float4 *>(out) + h;
@@ -343,6 +348,16 @@ __device__ __forceinline__ void dslash_site_tile(const DslashArgs &a, const Site
         }
     }
     SpinorIO<PREC>::store(out, h, Vh, o);
+    if constexpr (CGM == CNT_CG_MHAT) {  // FP16 t: its scale needs all twelve components first
+        float n0 = 0.f, n1 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            n0 += o[c].re * o[c].re + o[c].im * o[c].im;
+            n1 += src[c].re * src[c].re + src[c].im * src[c].im;
+        }
+        v[0] = n0;
+        v[1] = n1;
+    }
 }
 
 // MB: resident 128-thread blocks per SM the kernel is compiled for (registers
@@ -430,42 +445,53 @@ void bq_tile_launch(int prec, int recon, const DslashBatchTable &tab, const doub
 // --------------------------------------------------------------------------
 // CG-fused A x - k D steps of an FP32 batch in the tile mapping
 
-template <int RECON, int MB>
+template <int PREC, int RECON, int MB>
 static void launch_tile_cg_mb(const DslashBatchTable &tab, const double *mask, int nblocks, int mode,
                               const TileCg &cg, cudaStream_t s) {
     if (mode == CNT_CG_MHAT)
-        k_dslash_tile<BQ_PREC_SINGLE, RECON, false, EPI_XPAY, MB, CNT_CG_MHAT><<<nblocks, 128, 0, s>>>(tab, mask, cg);
+        k_dslash_tile<PREC, RECON, false, EPI_XPAY, MB, CNT_CG_MHAT><<<nblocks, 128, 0, s>>>(tab, mask, cg);
     else
-        k_dslash_tile<BQ_PREC_SINGLE, RECON, true, EPI_XPAY, MB, CNT_CG_MHATDAG><<<nblocks, 128, 0, s>>>(tab, mask, cg);
+        k_dslash_tile<PREC, RECON, true, EPI_XPAY, MB, CNT_CG_MHATDAG><<<nblocks, 128, 0, s>>>(tab, mask, cg);
 }
 
-template <int RECON>
+template <int PREC, int RECON>
 static void launch_tile_cg_r(const DslashBatchTable &tab, const double *mask, int nblocks, int mode, const TileCg &cg,
                              cudaStream_t s) {
-    if (tab.variant == 6) launch_tile_cg_mb<RECON, 6>(tab, mask, nblocks, mode, cg, s);
-    else if (tab.variant == 5) launch_tile_cg_mb<RECON, 5>(tab, mask, nblocks, mode, cg, s);
-    else launch_tile_cg_mb<RECON, 4>(tab, mask, nblocks, mode, cg, s);
+    // FP16 t with its norms needs the whole site in registers: at 80 registers (six blocks)
+    // it spills about 200 bytes, so that step runs with five at most
+    const int mb = (PREC == BQ_PREC_HALF && mode == CNT_CG_MHAT && tab.variant == 6) ? 5 : tab.variant;
+    if (mb == 6) launch_tile_cg_mb<PREC, RECON, 6>(tab, mask, nblocks, mode, cg, s);
+    else if (mb == 5) launch_tile_cg_mb<PREC, RECON, 5>(tab, mask, nblocks, mode, cg, s);
+    else launch_tile_cg_mb<PREC, RECON, 4>(tab, mask, nblocks, mode, cg, s);
 }
 
-int bq_tile_cg_launch(bq_ctx *c, int recon, const DslashBatchTable *tab, const double *mask, int mode,
+template <int PREC>
+static void launch_tile_cg_p(int recon, const DslashBatchTable &tab, const double *mask, int nblocks, int mode,
+                             const TileCg &cg, cudaStream_t s) {
+    if (recon == 12) launch_tile_cg_r<PREC, 12>(tab, mask, nblocks, mode, cg, s);
+    else if (recon == 8) launch_tile_cg_r<PREC, 8>(tab, mask, nblocks, mode, cg, s);
+    else launch_tile_cg_r<PREC, 18>(tab, mask, nblocks, mode, cg, s);
+}
+
+int bq_tile_cg_launch(bq_ctx *c, int prec, int recon, const DslashBatchTable *tab, const double *mask, int mode,
                       const TileCg &cg, double site_bytes_total, double site_flops_total, double fused_bytes_total) {
-    if (tab->nunits < 1 || tab->units[0].interleave != 3 || !(mode == CNT_CG_MHAT || mode == CNT_CG_MHATDAG)) {
-        bq_set_error("fused CG step: units must take the shared-memory tile mapping");
+    if (tab->nunits < 1 || tab->units[0].interleave != 3 || !(mode == CNT_CG_MHAT || mode == CNT_CG_MHATDAG) ||
+        !(prec == BQ_PREC_SINGLE || prec == BQ_PREC_HALF)) {
+        bq_set_error("fused CG step: FP32 / FP16 units in the shared-memory tile mapping only");
         return BQ_ERR_ARG;
     }
     const int nblocks = tab->block0[tab->nunits];
     int slot;
-    BQ_TRY(bq_time_begin(c, BQ_PREC_SINGLE, mode, &slot));
-    if (recon == 12) launch_tile_cg_r<12>(*tab, mask, nblocks, mode, cg, c->stream);
-    else if (recon == 8) launch_tile_cg_r<8>(*tab, mask, nblocks, mode, cg, c->stream);
-    else launch_tile_cg_r<18>(*tab, mask, nblocks, mode, cg, c->stream);
+    BQ_TRY(bq_time_begin(c, prec, mode, &slot));
+    if (prec == BQ_PREC_SINGLE) launch_tile_cg_p<BQ_PREC_SINGLE>(recon, *tab, mask, nblocks, mode, cg, c->stream);
+    else launch_tile_cg_p<BQ_PREC_HALF>(recon, *tab, mask, nblocks, mode, cg, c->stream);
     BQ_LAUNCH_CHECK();
     BQ_TRY(bq_time_end(c, slot));
     BQ_COUNT(c);
-    c->counters.dslash_launches[BQ_PREC_SINGLE][mode]++;
-    c->counters.dslash_bytes[BQ_PREC_SINGLE][mode] += site_bytes_total;
-    c->counters.dslash_flops[BQ_PREC_SINGLE][mode] += site_flops_total;
-    c->counters.fused_bytes[BQ_PREC_SINGLE][mode] += fused_bytes_total;
+    c->counters.dslash_launches[prec][mode]++;
+    c->counters.dslash_bytes[prec][mode] += site_bytes_total;
+    c->counters.dslash_flops[prec][mode] += site_flops_total;
+    c->counters.fused_bytes[prec][mode] += fused_bytes_total;
     return BQ_OK;
 }
 

@@ -177,10 +177,13 @@ def test_cg_shift_and_device_buffers(bq):
     b = synth.gaussian_spinor(lat.Vh, 77)
     bd = torch.from_numpy(b).cuda()
     xd = torch.empty_like(bd)
-    st = bq.bq_solve_cg(lat.ctx, xd, bd, tol=1e-10, precision="single", shift=0.05)
-    x = xd.cpu().numpy()
-    res = np.linalg.norm(op.mdagm(x, 0.05) - b) / np.linalg.norm(b)
-    assert res <= 1e-10 and st["converged"]
+    # FP32 and FP16-storage inner iterations (the shifted <p, Ap> sums |p|^2 inside the fused launch)
+    for prec, delta in (("single", 1e-3), ("half", 1e-1)):
+        bq.bq_set_recon(lat.ctx, prec, 12)
+        st = bq.bq_solve_cg(lat.ctx, xd, bd, tol=1e-10, precision=prec, shift=0.05, delta=delta)
+        x = xd.cpu().numpy()
+        res = np.linalg.norm(op.mdagm(x, 0.05) - b) / np.linalg.norm(b)
+        assert res <= 1e-10 and st["converged"], (prec, res)
     lat.close()
 
 
@@ -798,22 +801,26 @@ def test_batched_rhs_mappings(bq, mapping, prec):
     lat.close()
 
 
+@pytest.mark.parametrize("prec", ["single", "half"])
 @pytest.mark.parametrize("mapping", [-3, -5, -1])
-def test_batched_cg_shift_fused_tiles(bq, mapping):
-    """FP32 batched CG with a shift: in the tile mappings the x / r update and
-    <p, Ap> = |Mhat p|^2 + shift |p|^2 ride on the tile launches (the block-
-    interleaved mapping runs the separate kernels); every system against the oracle."""
+def test_batched_cg_shift_fused_tiles(bq, mapping, prec):
+    """Batched CG with a shift (FP32 and FP16-storage inner iteration): in the
+    tile mappings the x / r update and <p, Ap> = |Mhat p|^2 + shift |p|^2 ride on
+    the tile launches (the block-interleaved mapping runs the separate kernels);
+    every system against the oracle."""
     dims = (6, 4, 6, 10)
-    lat, U, A, p = make(bq, dims, kappa=0.1350, csw=1.7, eps=0.2, mu=0.1, recon=12, precision="single")
+    lat, U, A, p = make(bq, dims, kappa=0.1350, csw=1.7, eps=0.2, mu=0.1, recon=12, precision=prec)
     bq.bq_set_batch_mapping(lat.ctx, mapping)
     op = oracle.Operator(p, U)
     bs = [synth.gaussian_spinor(lat.Vh, 340 + i) for i in range(3)]
     xs = [np.empty_like(b) for b in bs]
     bq.bq_reset_counters(lat.ctx)
-    stats = bq.bq_solve_cg_batch([lat.ctx] * 3, xs, bs, tol=1e-10, precision="single", shift=0.05)
+    stats = bq.bq_solve_cg_batch([lat.ctx] * 3, xs, bs, tol=1e-10, precision=prec, shift=0.05,
+                                 delta=1e-3 if prec == "single" else 1e-1)
     c = bq.bq_get_counters(lat.ctx)
-    fused = c["dslash_launches"][1][3] > 0 and c["dslash_launches"][1][4] > 0
-    assert fused == (mapping <= -3) and (c["dslash_launches"][1][2] == 0) == fused
+    pi = 1 if prec == "single" else 2
+    fused = c["dslash_launches"][pi][3] > 0 and c["dslash_launches"][pi][4] > 0
+    assert fused == (mapping <= -3) and (c["dslash_launches"][pi][2] == 0) == fused
     for b, x, st in zip(bs, xs, stats):
         res = np.linalg.norm(op.mdagm(x, 0.05) - b) / np.linalg.norm(b)
         assert st["converged"] and res <= 1e-10, res
