@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--workload", default="32^3x64", choices=sorted(WORKLOADS))
     ap.add_argument("--inner", default="single", choices=["single", "half", "double"],
                     help="precision of the inner Krylov iteration (double = plain FP64 CG)")
-    ap.add_argument("--delta", type=float, default=None, help="reliable-update threshold (default 1e-3 FP32, 3e-3 FP16)")
+    ap.add_argument("--delta", type=float, default=None, help="reliable-update threshold (default 1e-3)")
     ap.add_argument("--check-every", type=int, default=8, help="iterations between host residual checks")
     ap.add_argument("--fp64-arith", default="df64", choices=["native", "df64"],
                     help="arithmetic of the FP64-storage operator kernels")
@@ -285,7 +285,7 @@ def main():
     b = synth.gaussian_spinor(Vh, wl["seed"] + 1000 + rank)
     b_dev = torch.from_numpy(b).cuda()
     x_dev = torch.empty_like(b_dev)
-    delta = args.delta if args.delta is not None else {"single": 1e-3, "half": 3e-3, "double": 0.0}[args.inner]
+    delta = args.delta if args.delta is not None else {"single": 1e-3, "half": 1e-3, "double": 0.0}[args.inner]
     solve_kw = dict(tol=1e-10, precision=args.inner, delta=delta, check_every=args.check_every, max_iter=20000)
 
     bqcd.bq_set_batch_mapping(ctx, args.batch_mapping)
@@ -680,13 +680,13 @@ def extras(args, ctx, lat, b, b_dev, x_dev, solve_kw, mixed_ms, torch, bqcd):
         fp64[mode] = (e0.elapsed_time(e1), st64)
     bqcd.bq_set_fp64_arith(ctx, args.fp64_arith)
     # the same solve with FP16 storage in the inner iteration (12-real links, per-site FP32 scale)
-    half_kw = dict(tol=1e-10, precision="half", delta=3e-3, check_every=args.check_every, max_iter=20000)
+    half_kw = dict(tol=1e-10, precision="half", delta=1e-3, check_every=args.check_every, max_iter=20000)
     bqcd.bq_solve_cg(ctx, x_dev, b_dev, **half_kw)
     e0.record()
     st_h = bqcd.bq_solve_cg(ctx, x_dev, b_dev, **half_kw)
     e1.record()
     torch.cuda.synchronize()
-    out["cg_fp16_inner"] = {"ms": e0.elapsed_time(e1), "delta": 3e-3, "iterations": st_h["iterations"],
+    out["cg_fp16_inner"] = {"ms": e0.elapsed_time(e1), "delta": 1e-3, "iterations": st_h["iterations"],
                             "reliable_updates": st_h["reliable_updates"], "true_residual": st_h["true_residual"]}
     out["cg"] = {"fp64_native_ms": fp64["native"][0], "fp64_df64_ms": fp64["df64"][0], "mixed_ms": mixed_ms,
                  "speedup_mixed_vs_fp64_native": fp64["native"][0] / mixed_ms,
