@@ -788,7 +788,7 @@ static int cg_batch_run(bq_ctx *c0, int nsys, bq_ctx *const *ctxs, const double 
     const bool fuse = nsys == 1 && PS != BQ_PREC_DOUBLE;
     CgFuse cgf{};
     if (fuse) {
-        const size_t need = 8 * (size_t)((ctxs[0]->Vh + 127) / 128);  // two values per warp
+        const size_t need = 2 * (size_t)((ctxs[0]->Vh + 127) / 128);  // two values per 128-site block
         if (w->fpart_n < need) {
             cudaFree(w->d_fpart);
             w->d_fpart = nullptr;

@@ -17,23 +17,30 @@
 
 namespace {
 
-// The partial sums leave each warp as soon as its sites are done (summed over the
-// warp in FP32, like the per-site terms; lane 0 stores them in FP64, [NV][warps of
-// the grid]); a one-block kernel then sums them in warp order. Nothing in the
-// hopping kernel waits on another warp or block, and no FP64 arithmetic runs in it.
+// The partial sums: each warp sums its threads' values in FP32 (the per-site terms
+// are FP32 already) and the block's four warp sums are added in warp order; thread 0
+// stores the block's sum in FP64, [NV][blocks of the grid], and a one-block kernel
+// then sums those in block order. The only wait is the block's own barrier at its
+// end (no fence, no ticket), and no FP64 arithmetic runs in the hopping kernel.
 template <int NV>
-__device__ __forceinline__ void warp_partials(float (&v)[NV], double *partials) {
-    const int nw = (int)(gridDim.x * blockDim.x) >> 5, w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+__device__ __forceinline__ void block_partials(float (&v)[NV], double *partials) {
+    __shared__ float ws[NV][4];
+    const int lane = (int)(threadIdx.x & 31), wid = (int)(threadIdx.x >> 5);
 #pragma unroll
     for (int k = 0; k < NV; k++) {
         float t = v[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if ((threadIdx.x & 31) == 0) partials[k * nw + w] = (double)t;
+        if (lane == 0) ws[k][wid] = t;
     }
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; k++)
+            partials[k * gridDim.x + blockIdx.x] = (double)(((ws[k][0] + ws[k][1]) + ws[k][2]) + ws[k][3]);
 }
 
-// the solver scalars from the warp partials of a fused launch (one block of CG_FIN_THREADS)
+// the solver scalars from the block partials of a fused launch (one block of CG_FIN_THREADS)
 constexpr int CG_FIN_THREADS = 1024;
 template <int MODE>
 __global__ void __launch_bounds__(CG_FIN_THREADS) k_cg_finish(const double *partials, int nw, double *scal) {
@@ -182,7 +189,7 @@ __global__ void __launch_bounds__(128, DslashMinBlocks<PS>::value) k_dslash_cg(c
             v[0] = nr;
         }
     }
-    warp_partials(v, f.partials);
+    block_partials(v, f.partials);
 }
 
 template <int PS, int RECON>
@@ -193,7 +200,7 @@ void launch_cg(const DslashArgs &a, const CgFuse &f, int mode, unsigned grid, cu
 }
 
 void launch_finish(const CgFuse &f, int mode, unsigned grid, cudaStream_t s) {
-    const int nw = (int)grid * 4;
+    const int nw = (int)grid;
     if (mode == CNT_CG_MHAT) k_cg_finish<CNT_CG_MHAT><<<1, CG_FIN_THREADS, 0, s>>>(f.partials, nw, f.scal);
     else k_cg_finish<CNT_CG_MHATDAG><<<1, CG_FIN_THREADS, 0, s>>>(f.partials, nw, f.scal);
 }

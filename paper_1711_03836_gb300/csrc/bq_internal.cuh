@@ -197,7 +197,7 @@ int bq_cg_finish_batch(bq_ctx *c, int mode, const TileCg &cg, const double *mask
 // The CG vector work fused into the two A x - k D launches of one CG iteration
 // on Mhat^dag Mhat + sigma (single system, FP32 or FP16-storage inner iteration; bq_cgfuse.cu).
 // scal: the system's solver scalars (S_* slots of bq_reduce.cuh); partials: 2 doubles
-// per warp of the launch (8 * ceil(V/2 / 128))
+// per 128-site block of the launch (2 * ceil(V/2 / 128))
 struct CgFuse {
     const void *p;  // search direction, precision ps
     void *xs, *rs;  // iterated solution and residual, FP32

@@ -497,9 +497,11 @@ int bq_tile_cg_launch(bq_ctx *c, int prec, int recon, const DslashBatchTable *ta
 
 // the solver scalars of each system from the tile partials of a fused launch (one block
 // per system, tiles summed in order)
+constexpr int CG_FIN_BATCH_THREADS = 1024;
 template <int MODE>
-__global__ void __launch_bounds__(256) k_cg_finish_batch(const SysVec *sys, const double *partials, int pstride,
-                                                         double *scal_all, const double *mask) {
+__global__ void __launch_bounds__(CG_FIN_BATCH_THREADS) k_cg_finish_batch(const SysVec *sys, const double *partials,
+                                                                          int pstride, double *scal_all,
+                                                                          const double *mask) {
     constexpr int NV = MODE == CNT_CG_MHAT ? 2 : 1;
     const int sy = blockIdx.x;
     if (mask && mask[sy] == 0.0) return;
@@ -508,6 +510,7 @@ __global__ void __launch_bounds__(256) k_cg_finish_batch(const SysVec *sys, cons
     double s[NV];
 #pragma unroll
     for (int k = 0; k < NV; k++) s[k] = 0.0;
+#pragma unroll 8
     for (int i = threadIdx.x; i < nt; i += blockDim.x)
 #pragma unroll
         for (int k = 0; k < NV; k++) s[k] += pt[k * pstride + i];
@@ -529,9 +532,11 @@ __global__ void __launch_bounds__(256) k_cg_finish_batch(const SysVec *sys, cons
 
 int bq_cg_finish_batch(bq_ctx *c, int mode, const TileCg &cg, const double *mask, int nsys) {
     if (mode == CNT_CG_MHAT)
-        k_cg_finish_batch<CNT_CG_MHAT><<<nsys, 256, 0, c->stream>>>(cg.sys, cg.partials, cg.pstride, cg.scal, mask);
+        k_cg_finish_batch<CNT_CG_MHAT><<<nsys, CG_FIN_BATCH_THREADS, 0, c->stream>>>(cg.sys, cg.partials, cg.pstride,
+                                                                                  cg.scal, mask);
     else
-        k_cg_finish_batch<CNT_CG_MHATDAG><<<nsys, 256, 0, c->stream>>>(cg.sys, cg.partials, cg.pstride, cg.scal, mask);
+        k_cg_finish_batch<CNT_CG_MHATDAG><<<nsys, CG_FIN_BATCH_THREADS, 0, c->stream>>>(cg.sys, cg.partials, cg.pstride,
+                                                                                     cg.scal, mask);
     BQ_LAUNCH_CHECK();
     BQ_COUNT(c);
     return BQ_OK;
