@@ -39,6 +39,33 @@ __device__ __forceinline__ cplx<df> mul_ipow(cplx<df> z, int k) {
 // and stores its six components. Half the live state of a one-lane site, so
 // about twice the resident warps to hide the dependent double-float chains.
 
+// Lazy double-float sums of products on (real, imaginary) pairs with the packed
+// FP32 instructions of the sm_100 family (one instruction for both lanes): lane x
+// and lane y take exactly the operations of two scalar dfsum chains.
+struct dfsum2 {
+    float2 s, c;
+};
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ dfsum2 dfs2_prod(float2 ah, float2 al, float2 bh, float2 bl) {
+    const float2 p = __fmul2_rn(ah, bh);
+    float2 e = __ffma2_rn(ah, bh, f2neg(p));
+    e = __ffma2_rn(ah, bl, e);
+    e = __ffma2_rn(al, bh, e);
+    return {p, e};
+}
+__device__ __forceinline__ void dfs2_add_prod(dfsum2 &z, float2 ah, float2 al, float2 bh, float2 bl) {
+    const float2 p = __fmul2_rn(ah, bh);
+    float2 e = __ffma2_rn(ah, bh, f2neg(p));
+    e = __ffma2_rn(ah, bl, e);
+    e = __ffma2_rn(al, bh, e);
+    // two-sum of z.s and p
+    const float2 t = __fadd2_rn(z.s, p);
+    const float2 bb = __fadd2_rn(t, f2neg(z.s));
+    const float2 te = __fadd2_rn(__fadd2_rn(z.s, f2neg(__fadd2_rn(t, f2neg(bb)))), __fadd2_rn(p, f2neg(bb)));
+    z.s = t;
+    z.c = __fadd2_rn(z.c, __fadd2_rn(e, te));
+}
+
 #ifndef DF64P_MIN_BLOCKS
 #define DF64P_MIN_BLOCKS 4
 #endif
@@ -172,17 +199,20 @@ __device__ __forceinline__ void dslash_site_df64_pair(const DslashArgs &a, const
                     w[b] = {df(v.x, v.y), back ? df(-v.z, -v.w) : df(v.z, v.w)};
                 }
             }
-            dfsum re = dfs_prod(w[0].re, hq[0].re), im = dfs_prod(w[0].re, hq[0].im);
-            dfs_add_prod(re, -w[0].im, hq[0].im);
-            dfs_add_prod(im, w[0].im, hq[0].re);
+            // (re, im) += (w.re, w.re) (h.re, h.im) + (-w.im, w.im) (h.im, h.re), in the
+            // order of the scalar chains re = w.re h.re - w.im h.im, im = w.re h.im + w.im h.re
+            dfsum2 z = dfs2_prod(make_float2(w[0].re.hi, w[0].re.hi), make_float2(w[0].re.lo, w[0].re.lo),
+                                 make_float2(hq[0].re.hi, hq[0].im.hi), make_float2(hq[0].re.lo, hq[0].im.lo));
+            dfs2_add_prod(z, make_float2(-w[0].im.hi, w[0].im.hi), make_float2(-w[0].im.lo, w[0].im.lo),
+                          make_float2(hq[0].im.hi, hq[0].re.hi), make_float2(hq[0].im.lo, hq[0].re.lo));
 #pragma unroll
             for (int b = 1; b < 3; b++) {
-                dfs_add_prod(re, w[b].re, hq[b].re);
-                dfs_add_prod(re, -w[b].im, hq[b].im);
-                dfs_add_prod(im, w[b].re, hq[b].im);
-                dfs_add_prod(im, w[b].im, hq[b].re);
+                dfs2_add_prod(z, make_float2(w[b].re.hi, w[b].re.hi), make_float2(w[b].re.lo, w[b].re.lo),
+                              make_float2(hq[b].re.hi, hq[b].im.hi), make_float2(hq[b].re.lo, hq[b].im.lo));
+                dfs2_add_prod(z, make_float2(-w[b].im.hi, w[b].im.hi), make_float2(-w[b].im.lo, w[b].im.lo),
+                              make_float2(hq[b].im.hi, hq[b].re.hi), make_float2(hq[b].im.lo, hq[b].re.lo));
             }
-            u[aa] = {dfs_done(re), dfs_done(im)};
+            u[aa] = {dfs_done(dfsum{z.s.x, z.c.x}), dfs_done(dfsum{z.s.y, z.c.y})};
         }
         if (mu == 3) {
             const T coef = back ? cb : cf;
