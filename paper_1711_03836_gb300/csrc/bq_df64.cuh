@@ -66,6 +66,17 @@ __device__ __forceinline__ void dfs2_add_prod(dfsum2 &z, float2 ah, float2 al, f
     z.c = __fadd2_rn(z.c, __fadd2_rn(e, te));
 }
 
+// a + b for complex double-float values without the final normalisation (add_lazy
+// on the real and the imaginary part as one pair)
+__device__ __forceinline__ cplx<df> cadd_lazy2(cplx<df> a, cplx<df> b) {
+    const float2 ah = make_float2(a.re.hi, a.im.hi), bh = make_float2(b.re.hi, b.im.hi);
+    const float2 t = __fadd2_rn(ah, bh);
+    const float2 bb = __fadd2_rn(t, f2neg(ah));
+    const float2 te = __fadd2_rn(__fadd2_rn(ah, f2neg(__fadd2_rn(t, f2neg(bb)))), __fadd2_rn(bh, f2neg(bb)));
+    const float2 lo = __fadd2_rn(te, __fadd2_rn(make_float2(a.re.lo, a.im.lo), make_float2(b.re.lo, b.im.lo)));
+    return {df(t.x, lo.x), df(t.y, lo.y)};
+}
+
 #ifndef DF64P_MIN_BLOCKS
 #define DF64P_MIN_BLOCKS 4
 #endif
@@ -178,7 +189,7 @@ __device__ __forceinline__ void dslash_site_df64_pair(const DslashArgs &a, const
                 pj = {df_from_double(vj.x), df_from_double(vj.y)};
             }
             pj = mul_ipow(pj, kq);
-            hq[c] = {add_lazy(pq.re, pj.re), add_lazy(pq.im, pj.im)};
+            hq[c] = cadd_lazy2(pq, pj);
         }
         // U h_q (or U^dag h_q): 18-real links one row (or column) at a time; 12-real
         // links whole, the third row rebuilt
@@ -221,10 +232,10 @@ __device__ __forceinline__ void dslash_site_df64_pair(const DslashArgs &a, const
         }
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            up[c] = {add_lazy(up[c].re, u[c].re), add_lazy(up[c].im, u[c].im)};
+            up[c] = cadd_lazy2(up[c], u[c]);
             const cplx<T> l = mul_ipow(u[c], kl);
-            if (lo == 2) p2[c] = {add_lazy(p2[c].re, l.re), add_lazy(p2[c].im, l.im)};
-            else p3[c] = {add_lazy(p3[c].re, l.re), add_lazy(p3[c].im, l.im)};
+            if (lo == 2) p2[c] = cadd_lazy2(p2[c], l);
+            else p3[c] = cadd_lazy2(p3[c], l);
         }
     }
     // exchange: lane 1 collects spins 2 and 3, lane 0 receives spin 1
