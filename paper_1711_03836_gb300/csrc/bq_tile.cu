@@ -1,7 +1,10 @@
 // bq_tile.cu -- the batched hopping term (Eq. 1 / Eq. 5) with the links and
 // the clover term of a tile of sites staged in shared memory once for all
 // right-hand sides of a unit (the block solvers of Section 3 apply one operator
-// to many right-hand sides), FP32 and FP16 storage.
+// to many right-hand sides), FP32 and FP16 storage; and the two A x - k D steps
+// of a batched CG iteration with each system's CG vector work fused in (as in
+// bq_cgfuse.cu for one system: |Mhat p|^2 and |p|^2, or the x / r update and
+// |r|^2, one partial per tile and system, summed by one block per system).
 #include "bq_cgfuse.cuh"
 #include "bq_reduce.cuh"
 #include "bq_stencil.cuh"
